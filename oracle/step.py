@@ -1,0 +1,77 @@
+"""One implicit imaginary-time step and evolution over a tau grid (oracle).
+Test infrastructure only.
+
+Schemes (H' = H - s):
+* 'tr' -- implicit trapezoid rule, Eq. 4: (I + c H') psi_k = (I - c H') psi_{k-1}
+          with c = dtau/2.  The right-hand side MPS b is a two-site fit of
+          (I - c H') psi_{k-1} and is also the initial guess (App. B).
+* 'be' -- backward Euler: (I + c H') psi_k = psi_{k-1} with c = dtau; b = psi_{k-1}
+          and the initial guess is psi_{k-1}.
+After the solve the state is normalised (Heisenberg section, App. D).  The
+shift s is either fixed or, in 'energy' mode, the energy of the current state
+(App. D: shift the spectrum by the energy of the new time-evolved state).
+"""
+import numpy as np
+
+from . import linsolve as ls
+from . import mps as mpsmod
+
+
+class StepInfo:
+    def __init__(self):
+        self.energy = 0.0
+        self.norm_before = 0.0
+        self.max_discarded = 0.0
+        self.max_local_residual = 0.0
+        self.max_chi = 0
+        self.gmres_steps = 0
+        self.shift = 0.0
+
+
+def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
+                  local_tol=0.0, sweeps=1, sweep_tol=0.0, fit_sweeps=1):
+    """Advance the MPS psi (assumed normalised) by one step of size dtau.
+    Returns (new normalised MPS, StepInfo)."""
+    info = StepInfo()
+    info.shift = shift
+    if scheme == "be":
+        c = dtau
+        b = mpsmod.copy(psi)
+        x0 = mpsmod.copy(psi)
+    elif scheme == "tr":
+        c = 0.5 * dtau
+        b, finfo = ls.fit_affine(Ws, psi, 1.0 + c * shift, -c, chi_max, cutoff, fit_sweeps)
+        info.max_discarded = finfo.max_discarded
+        x0 = mpsmod.copy(b)
+    else:
+        raise ValueError(scheme)
+    x, sinfo = ls.linsolve(Ws, x0, b, c, shift, chi_max, cutoff, krylov_dim,
+                           local_tol, sweeps, sweep_tol)
+    nrm = float(np.linalg.norm(x[0]))          # centre on site 1, the rest right-orthonormal
+    x[0] = x[0] / nrm
+    info.norm_before = nrm
+    info.max_discarded = max(info.max_discarded, sinfo.max_discarded)
+    info.max_local_residual = sinfo.max_local_residual
+    info.gmres_steps = sinfo.gmres_steps
+    info.max_chi = max(mpsmod.bond_dims(x) + [1])
+    info.energy = mpsmod.expect_mpo(x, Ws)
+    return x, info
+
+
+def evolve(Ws, psi0, nodes, scheme, chi_max, cutoff, shift_mode="fixed", shift=0.0,
+           **kw):
+    """Evolve psi0 over the grid `nodes` (t_0 = 0 < t_1 < ...).  Returns
+    (list of MPS after each step, list of StepInfo)."""
+    psi = mpsmod.copy(psi0)
+    nrm = mpsmod.norm(psi)
+    psi[0] = psi[0] / nrm
+    s = mpsmod.expect_mpo(psi, Ws) if shift_mode == "energy" else shift
+    states, infos = [], []
+    for k in range(1, len(nodes)):
+        psi, info = implicit_step(Ws, psi, nodes[k] - nodes[k - 1], scheme, s, chi_max,
+                                  cutoff, **kw)
+        states.append(psi)
+        infos.append(info)
+        if shift_mode == "energy":
+            s = info.energy
+    return states, infos
