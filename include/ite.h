@@ -1,0 +1,187 @@
+/*
+ * ite.h -- C ABI of the GB300 (sm_103a) library for imaginary-time evolution
+ * of matrix product states by A-stable implicit steps on logarithmic tau grids.
+ *
+ * The method (paper: "Fast Tensor Network Imaginary Time Evolution by Implicit
+ * Stepping on Logarithmic Grids"): evolve |psi(tau)> = e^{-H tau}|psi(0)>
+ * (Method, Eq. 1) on a grid whose steps grow geometrically (Method, log-grid
+ * and panel paragraphs), each step being the implicit linear solve
+ *
+ *     (I + c (H - s)) |psi_k> = |b>                                   (Eq. 4)
+ *
+ * with c = dtau/2, b = (I - c (H - s)) psi_{k-1} for the trapezoid rule
+ * (Eq. 4, App. A), or c = dtau, b = psi_{k-1} for backward Euler.  The solve is
+ * an MPO-MPS linear system done by a two-site DMRG-style sweep with GMRES
+ * local solves (Method, "two operations"; App. B, App. D).
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im) doubles, i.e. the memory layout
+ *     of C99 double complex / numpy complex128.
+ *   - MPS site tensor i: A_i[a][s][b], shape (chi_i, d, chi_{i+1}), row-major,
+ *     chi_0 = chi_N = 1.  Bond index b = 0..N (bond b sits left of site b).
+ *   - MPO site tensor i: W_i[w][s'][s][w'], shape (D_i, d, d, D_{i+1}),
+ *     D_0 = D_N = 1; s' is the output (bra) index.  The operator is the
+ *     product of the W_i over the channel indices.
+ *   - Heisenberg local basis: 0 = spin up.  Anderson local basis:
+ *     {|0>, |up>, |down>, |up down>} (index n_up + 2 n_down), impurity on site
+ *     0, bath j on site j (star geometry), Jordan-Wigner order up before down.
+ *
+ * Ownership and memory
+ *   - Handles are library-owned and released by the matching *_destroy.
+ *   - Host arrays passed in are copied before the call returns; outputs go to
+ *     caller buffers whose capacity is passed alongside.
+ *   - Every device allocation goes through the allocator given to
+ *     ite_ctx_create (NULL = cudaMalloc/cudaFree).  All device work is
+ *     enqueued on the context stream; calls that return host values
+ *     synchronise that stream before returning.
+ *
+ * Errors
+ *   - Every call returns an ite_status; ite_last_error(ctx) gives a message.
+ *     No call aborts the process.  ITE_ESINGULAR flags non-finite values;
+ *     ITE_ENOTCONV is informational (a fixed-effort GMRES is not an error).
+ *   - A handle of NULL, a negative size or a bond dimension above the
+ *     object's capacity gives ITE_EINVAL and leaves all state unchanged.
+ */
+#ifndef ITE_H
+#define ITE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ite_ctx_s* ite_ctx;
+typedef struct ite_mpo_s* ite_mpo;
+typedef struct ite_mps_s* ite_mps;
+
+typedef enum {
+  ITE_OK = 0,
+  ITE_EINVAL = 1,
+  ITE_ENOMEM = 2,
+  ITE_ESINGULAR = 3,
+  ITE_ENOTCONV = 4,
+  ITE_ETIMEOUT = 5,
+  ITE_ECUDA = 6
+} ite_status;
+
+/* Time stepper.  Trapezoid: Eq. 4 (A-stable, App. A).  Backward Euler: the
+ * first-order A-stable (and L-stable) implicit step, R(z) = 1/(1+z). */
+typedef enum { ITE_BACKWARD_EULER = 0, ITE_TRAPEZOID = 1 } ite_scheme;
+
+/* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere. */
+typedef enum { ITE_FP64 = 0 } ite_precision;
+
+/* Spectrum shift s of each step.  FIXED: the caller's value.  CURRENT_ENERGY:
+ * s_k = <psi_{k-1}|H|psi_{k-1}> (App. D: shift by the energy of the new
+ * time-evolved state to limit norm drift). */
+typedef enum { ITE_SHIFT_FIXED = 0, ITE_SHIFT_CURRENT_ENERGY = 1 } ite_shift_mode;
+
+/* Device allocator hooks: alloc returns a device pointer (NULL on failure). */
+typedef void* (*ite_alloc_fn)(size_t bytes, void* user);
+typedef void (*ite_free_fn)(void* ptr, size_t bytes, void* user);
+
+/* Solver effort (App. D: one sweep, one GMRES cycle of Krylov dimension 10). */
+typedef struct {
+  int krylov_dim;     /* Arnoldi steps per local solve (default 10)            */
+  int sweeps;         /* maximum sweeps per solve (default 1)                  */
+  double local_tol;   /* stop GMRES at |r|/|B| <= local_tol (0: fixed effort)  */
+  double sweep_tol;   /* stop sweeping at 1-|<x_s|x_{s-1}>| < tol (0: fixed)   */
+  int fit_sweeps;     /* sweeps of the trapezoid right-hand-side fit (1)       */
+  int precision;      /* ite_precision (ITE_FP64)                              */
+} ite_solver_opts;
+
+/* Per-step report. */
+typedef struct {
+  double energy;               /* <psi_k|H|psi_k> after normalisation          */
+  double norm_before;          /* |x| before normalisation                     */
+  double max_discarded_weight; /* largest relative discarded weight of a bond  */
+  double max_local_residual;   /* largest GMRES relative residual estimate     */
+  double shift;                /* shift s used by this step                    */
+  int max_chi;                 /* largest bond dimension after the step        */
+  int gmres_steps;             /* Arnoldi steps summed over all local solves   */
+  int status;                  /* ite_status of this step                      */
+} ite_step_info;
+
+void ite_solver_opts_default(ite_solver_opts* opts);
+
+/* Context: one device, one stream (cudaStream_t or NULL for the legacy
+ * default stream), optional allocator hooks with a user pointer. */
+ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free_fn release,
+                          void* alloc_user, ite_ctx* out);
+ite_status ite_ctx_set_stream(ite_ctx ctx, void* stream);
+void ite_ctx_destroy(ite_ctx ctx);
+const char* ite_last_error(ite_ctx ctx);
+/* Bytes currently held through the allocator by this context and its objects. */
+size_t ite_ctx_device_bytes(ite_ctx ctx);
+
+/* MPO from explicit site tensors: d[N] site dimensions (all equal), D[N+1]
+ * bond dimensions with D[0] = D[N] = 1, W the concatenated W_i (interleaved
+ * complex), sum_i D_i d^2 D_{i+1} complex numbers. */
+ite_status ite_mpo_create(ite_ctx ctx, int N, const int* d, const int* D, const double* W,
+                          ite_mpo* out);
+/* Heisenberg chain J sum (SxSx + SySy) + Jz sum SzSz, open boundaries, D = 5
+ * (Heisenberg-chain section; Jz = J is the isotropic chain). */
+ite_status ite_mpo_create_heisenberg(ite_ctx ctx, int N, double J, double Jz, ite_mpo* out);
+/* Single-impurity Anderson model (Anderson-impurity section):
+ * eps_d n_d + U n_up n_down + sum_j eps_j n_j + sum_{j,s} V_j (d^dag_s c_js + h.c.),
+ * star geometry, d = 4, D = 6. */
+ite_status ite_mpo_create_anderson(ite_ctx ctx, int n_bath, const double* eps, const double* V,
+                                   double U, double eps_d, ite_mpo* out);
+int ite_mpo_length(ite_mpo mpo);
+void ite_mpo_destroy(ite_mpo mpo);
+
+/* MPS with bond-dimension capacity chi_cap (bond b holds at most
+ * min(d^b, d^(N-b), chi_cap)).  chi[N+1] are the initial bond dimensions and
+ * A the concatenated site tensors (interleaved complex). */
+ite_status ite_mps_create(ite_ctx ctx, int N, int d, const int* chi, const double* A,
+                          int chi_cap, ite_mps* out);
+/* Product state from site_vecs[N][d] (interleaved complex). */
+ite_status ite_mps_create_product(ite_ctx ctx, int N, int d, const double* site_vecs,
+                                  int chi_cap, ite_mps* out);
+/* Replace the tensors of an existing MPS (same N, d; chi within capacity). */
+ite_status ite_mps_set(ite_ctx ctx, ite_mps mps, const int* chi, const double* A);
+ite_status ite_mps_copy(ite_ctx ctx, ite_mps src, ite_mps dst);
+/* Bond dimensions chi[N+1] and the number of doubles ite_mps_get writes. */
+ite_status ite_mps_bond_dims(ite_mps mps, int* chi, size_t* n_doubles);
+ite_status ite_mps_get(ite_ctx ctx, ite_mps mps, double* A, size_t cap_doubles);
+void ite_mps_destroy(ite_mps mps);
+
+/* One implicit step of size dtau with shift s (Eq. 4 / backward Euler), in
+ * place.  The state is normalised afterwards (Heisenberg section, App. D). */
+ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int scheme,
+                             double shift, int chi_max, double cutoff,
+                             const ite_solver_opts* opts, ite_step_info* info);
+
+/* Geometric grid t_0 = 0, t_k = tau0 (tau_max/tau0)^((k-1)/(n_steps-1)),
+ * k = 1..n_steps, and evolution over it.  per_step[n_steps], nodes[n_steps+1]
+ * may be NULL. */
+ite_status ite_grid_geometric(double tau0, double tau_max, int n_steps, double* nodes);
+ite_status ite_evolve_loggrid(ite_ctx ctx, ite_mpo H, ite_mps psi, double tau0, double tau_max,
+                              int n_steps, int scheme, int shift_mode, double shift0,
+                              int chi_max, double cutoff, const ite_solver_opts* opts,
+                              ite_step_info* per_step, double* nodes);
+
+/* The paper's panel grid (Method): P panels with endpoints
+ * {0, tau_max/2^(P-j), j = 1..P} and n uniform steps per panel; P*n steps. */
+ite_status ite_grid_panels(double tau_max, int P, int n, double* nodes);
+ite_status ite_evolve_panels(ite_ctx ctx, ite_mpo H, ite_mps psi, double tau_max, int P, int n,
+                             int scheme, int shift_mode, double shift0, int chi_max,
+                             double cutoff, const ite_solver_opts* opts,
+                             ite_step_info* per_step, double* nodes);
+
+/* Measurements (Heisenberg section: overlaps; Anderson section: double
+ * occupancy <n_up n_down> as a one-site correlator). */
+ite_status ite_energy(ite_ctx ctx, ite_mpo H, ite_mps psi, double* energy);
+ite_status ite_overlap(ite_ctx ctx, ite_mps bra, ite_mps ket, double out[2]);
+/* <psi| O_i S_{i+1}..S_{j-1} P_j |psi> / <psi|psi>, i <= j, O, P, S d x d
+ * interleaved complex (S may be NULL: identity; for i == j the operator is
+ * O P on site i). */
+ite_status ite_correlator(ite_ctx ctx, ite_mps psi, const double* O, int i, const double* P,
+                          int j, const double* string_op, double out[2]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITE_H */

@@ -1,0 +1,72 @@
+/*
+ * ite_kernels.h -- kernel-level entry points of the GB300 library, one per
+ * step of the two-site linear-solve sweep (Method, "two operations"; App. B).
+ * They exist so that each step can be driven and checked on its own; the
+ * sweep in ite_implicit_step runs exactly these kernels.
+ *
+ * All array arguments are DEVICE pointers to interleaved complex doubles,
+ * owned by the caller, row-major, not aliasing each other unless stated.
+ * Work is enqueued on the context stream; entry points that return host
+ * values synchronise it.  Errors: ITE_EINVAL for bad sizes or an MPO bond /
+ * site out of range, ITE_ECUDA for a failed launch (message in ite_last_error).
+ */
+#ifndef ITE_KERNELS_H
+#define ITE_KERNELS_H
+
+#include "ite.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Two-site effective Hamiltonian on sites (i, i+1) of the MPO (the dominant
+ * operation of the local solves, App. B):
+ *   Y[a,s',t',b] = alpha * sum L[w,a,a'] W_i[w,s',s,v] W_{i+1}[v,t',t,w'']
+ *                              R[w'',b',b] X[a',s,t,b']  +  gamma * Z[a,s',t',b]
+ * L: (D_i, chl_bra, chl_ket); R: (D_{i+2}, chr_ket, chr_bra) (ket index before
+ * bra index); X: (chl_ket, d, d, chr_ket); Y, Z: (chl_bra, d, d, chr_bra).
+ * Z may be NULL; Z may equal X when the bra and ket dimensions agree.
+ * alpha and gamma are complex (re, im). */
+ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_ket,
+                      int chr_bra, const double* L, const double* R, const double* X, double* Y,
+                      const double alpha[2], const double* Z, const double gamma[2]);
+
+/* Environment updates (App. B: the projected operator of the two-site solve).
+ * Left:  Lout[w',b,b'] = sum conj(bra[a,s',b]) Lin[w,a,a'] W_i[w,s',s,w'] ket[a',s,b']
+ *        Lin (D_i, chl_bra, chl_ket), bra (chl_bra, d, chr_bra), ket (chl_ket, d, chr_ket),
+ *        Lout (D_{i+1}, chr_bra, chr_ket).
+ * Right: Rout[w,a',a] = sum ket[a',s,b'] Rin[w',b',b] W_i[w,s',s,w'] conj(bra[a,s',b])
+ *        Rin (D_{i+1}, chr_ket, chr_bra), Rout (D_i, chl_ket, chl_bra). */
+ite_status ite_k_env_left(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
+                          int chr_ket, const double* Lin, const double* bra, const double* ket,
+                          double* Lout);
+ite_status ite_k_env_right(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
+                           int chr_ket, const double* Rin, const double* bra, const double* ket,
+                           double* Rout);
+
+/* Local solve of one bond (App. B, App. D): one GMRES cycle of at most
+ * krylov_dim Arnoldi steps on  (alpha I + c H_eff) X = B,  starting from the X
+ * passed in, which is overwritten with the result.  L, R as in ite_k_heff with
+ * bra = ket dimensions (chl, chr).  steps / rel_res (host, may be NULL) receive
+ * the Arnoldi steps taken and the residual estimate |r|/|B|. */
+ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const double* L,
+                             const double* R, const double* B, double* X, double alpha, double c,
+                             int krylov_dim, double local_tol, int* steps, double* rel_res);
+
+/* Truncated SVD split of X viewed as an m x n matrix (Heisenberg section: the
+ * truncation keeps the discarded squared Schmidt weight below cutoff):
+ * X = U S V^dag, kept rank r by the library's truncation rule (chi_max, cutoff,
+ * weight floor 1e-24, near-degenerate groups kept whole).  centre_right != 0
+ * writes left = U_r (m x r) and right = S_r V_r^dag (r x n); otherwise
+ * left = U_r S_r and right = V_r^dag.  left needs m*min(m,n) and right
+ * min(m,n)*n complex entries of room.  sigma (device, may be NULL) receives
+ * the min(m,n) singular values in descending order. */
+ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
+                       int centre_right, double* left, double* right, double* sigma, int* rank,
+                       double* discarded);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITE_KERNELS_H */

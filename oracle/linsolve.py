@@ -77,6 +77,16 @@ def heff_apply(L, W1, W2, R, X):
     return np.tensordot(T, R, axes=([1, 4], [2, 1]))           # (a, s', t', b)
 
 
+def heff_entry(L, W1, W2, R, X, a, b):
+    """Y[a, :, :, b] of ``heff_apply`` for one pair (a, b), from the same sum
+    restricted to that output row/column (for sampled checks at sizes where
+    the whole contraction is too slow)."""
+    T = np.tensordot(L[a], X, axes=([1], [0]))                 # (w, s, t, b')
+    T = np.tensordot(T, W1, axes=([0, 1], [0, 2]))             # (t, b', s', v)
+    T = np.tensordot(T, W2, axes=([3, 0], [0, 2]))             # (b', s', t', w')
+    return np.tensordot(T, R[b], axes=([0, 3], [1, 0]))        # (s', t')
+
+
 def project_two_site(Lo, A1, A2, Ro):
     """B[a,s,t,b] = sum Lo[a,a'] A1[a',s,c] A2[c,t,b'] Ro[b,b']: the two-site
     block of the MPS (A1, A2) seen in the bra basis of the environments."""
@@ -125,11 +135,11 @@ def choose_rank(S, chi_max, cutoff):
     """Kept rank for descending singular values S (see module docstring)."""
     n = len(S)
     w = S.astype(float) ** 2
-    total = w.sum()
+    tail = np.concatenate([np.cumsum(w[::-1])[::-1], [0.0]])  # tail[r] = sum_{k>=r} w_k
+    total = tail[0]
     if total == 0.0:
         return 1, 0.0
     tol = max(cutoff, WEIGHT_FLOOR) * total
-    tail = np.concatenate([np.cumsum(w[::-1])[::-1], [0.0]])  # tail[r] = sum_{k>=r} w_k
     r = n
     for cand in range(1, n + 1):
         if tail[cand] <= tol:
@@ -157,6 +167,22 @@ def split_two_site(X, chi_max, cutoff, centre_right):
     else:
         A1, A2 = U * S[None, :], Vh
     return A1.reshape(chl, d1, r), A2.reshape(r, d2, chr_), disc, S
+
+
+def right_canonicalize_svd(mps_in):
+    """Gauge move before a sweep: from the last site to the second, split
+    A_i = (U S) V^dag by an SVD that keeps every singular value above the
+    weight floor, keep V^dag on site i and absorb U S into site i-1.  Dropping
+    only numerically zero singular values makes the bond spaces (and hence
+    the projected local problems) independent of the decomposition used."""
+    out = mpsmod.copy(mps_in)
+    for i in range(len(out) - 1, 0, -1):
+        chl, d, chr_ = out[i].shape
+        U, S, Vh = np.linalg.svd(out[i].reshape(chl, d * chr_), full_matrices=False)
+        r, _ = choose_rank(S, len(S), 0.0)
+        out[i] = Vh[:r].reshape(r, d, chr_)
+        out[i - 1] = np.tensordot(out[i - 1], U[:, :r] * S[None, :r], axes=([2], [0]))
+    return out
 
 
 # ------------------------------------------------------------- sweeps
@@ -218,7 +244,7 @@ def linsolve(Ws, x0, b, c, s, chi_max, cutoff, krylov_dim=10, local_tol=0.0,
              sweeps=1, sweep_tol=0.0):
     """Solve (I + c (H - s)) x = b for MPS x, starting from x0 (App. B).
     Returns (x, info); x has its orthogonality centre on site 1."""
-    x = mpsmod.right_canonicalize(x0)
+    x = right_canonicalize_svd(x0)
     info = SweepInfo()
     alpha = 1.0 - c * s
 
@@ -252,7 +278,7 @@ def fit_affine(Ws, psi, alpha, beta, chi_max, cutoff, sweeps=1):
     of Eq. 4 (Method, operation (i)); App. B notes b is also the initial guess
     of the solve.  Each local block is the exact projection of the target onto
     the current environments of f."""
-    f = mpsmod.right_canonicalize(psi)
+    f = right_canonicalize_svd(psi)
     info = SweepInfo()
 
     def local_block(i, EL, ER, X0):

@@ -1,0 +1,104 @@
+"""ctypes declarations of the C ABI in include/ite.h and include/ite_kernels.h.
+
+Argument marshalling only: every computation happens in libite.so.  Importing
+this module loads the library and fails loudly if it has not been built
+(``python -m paper_2606_02930_gb300.build`` or ``__graft_entry__.build()``).
+"""
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libite.so")
+
+ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA = range(7)
+ITE_BACKWARD_EULER, ITE_TRAPEZOID = 0, 1
+ITE_FP64 = 0
+ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
+STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",
+                4: "ITE_ENOTCONV", 5: "ITE_ETIMEOUT", 6: "ITE_ECUDA"}
+
+
+class ite_solver_opts(C.Structure):
+    _fields_ = [("krylov_dim", C.c_int), ("sweeps", C.c_int), ("local_tol", C.c_double),
+                ("sweep_tol", C.c_double), ("fit_sweeps", C.c_int), ("precision", C.c_int)]
+
+
+class ite_step_info(C.Structure):
+    _fields_ = [("energy", C.c_double), ("norm_before", C.c_double),
+                ("max_discarded_weight", C.c_double), ("max_local_residual", C.c_double),
+                ("shift", C.c_double), ("max_chi", C.c_int), ("gmres_steps", C.c_int),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ite_alloc_fn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+ite_free_fn = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+_vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+_pi, _pd = C.POINTER(C.c_int), C.POINTER(C.c_double)
+
+# name: (restype, argtypes)
+SIGNATURES = {
+    "ite_solver_opts_default": (None, [C.POINTER(ite_solver_opts)]),
+    "ite_ctx_create": (_i, [_i, _vp, ite_alloc_fn, ite_free_fn, _vp, C.POINTER(_vp)]),
+    "ite_ctx_set_stream": (_i, [_vp, _vp]),
+    "ite_ctx_destroy": (None, [_vp]),
+    "ite_last_error": (C.c_char_p, [_vp]),
+    "ite_ctx_device_bytes": (_sz, [_vp]),
+    "ite_mpo_create": (_i, [_vp, _i, _pi, _pi, _pd, C.POINTER(_vp)]),
+    "ite_mpo_create_heisenberg": (_i, [_vp, _i, _d, _d, C.POINTER(_vp)]),
+    "ite_mpo_create_anderson": (_i, [_vp, _i, _pd, _pd, _d, _d, C.POINTER(_vp)]),
+    "ite_mpo_length": (_i, [_vp]),
+    "ite_mpo_destroy": (None, [_vp]),
+    "ite_mps_create": (_i, [_vp, _i, _i, _pi, _pd, _i, C.POINTER(_vp)]),
+    "ite_mps_create_product": (_i, [_vp, _i, _i, _pd, _i, C.POINTER(_vp)]),
+    "ite_mps_set": (_i, [_vp, _vp, _pi, _pd]),
+    "ite_mps_copy": (_i, [_vp, _vp, _vp]),
+    "ite_mps_bond_dims": (_i, [_vp, _pi, C.POINTER(_sz)]),
+    "ite_mps_get": (_i, [_vp, _vp, _pd, _sz]),
+    "ite_mps_destroy": (None, [_vp]),
+    "ite_implicit_step": (_i, [_vp, _vp, _vp, _d, _i, _d, _i, _d, C.POINTER(ite_solver_opts),
+                               C.POINTER(ite_step_info)]),
+    "ite_grid_geometric": (_i, [_d, _d, _i, _pd]),
+    "ite_evolve_loggrid": (_i, [_vp, _vp, _vp, _d, _d, _i, _i, _i, _d, _i, _d,
+                                C.POINTER(ite_solver_opts), C.POINTER(ite_step_info), _pd]),
+    "ite_grid_panels": (_i, [_d, _i, _i, _pd]),
+    "ite_evolve_panels": (_i, [_vp, _vp, _vp, _d, _i, _i, _i, _i, _d, _i, _d,
+                               C.POINTER(ite_solver_opts), C.POINTER(ite_step_info), _pd]),
+    "ite_energy": (_i, [_vp, _vp, _vp, _pd]),
+    "ite_overlap": (_i, [_vp, _vp, _vp, _pd]),
+    "ite_correlator": (_i, [_vp, _vp, _pd, _i, _pd, _i, _pd, _pd]),
+    "ite_k_heff": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _pd, _vp, _pd]),
+    "ite_k_env_left": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "ite_k_env_right": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "ite_k_local_solve": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _d, _d, _i, _d, _pi, _pd]),
+    "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd]),
+}
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libite.so not built at {path}: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+class IteError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, ctx=None):
+    if status != ITE_OK:
+        msg = lib.ite_last_error(ctx).decode() if ctx else ""
+        raise IteError(status, msg)

@@ -1,0 +1,299 @@
+"""Python binding of the library: thin wrappers with the names of the C calls
+(ctx_create, mpo_create, mps_create, implicit_step, evolve_loggrid,
+evolve_panels, energy, overlap, correlator, and the kernel-level k_* calls).
+
+Argument marshalling only.  PyTorch supplies the CUDA stream and, by default,
+device memory (through the caching allocator); every computation runs in
+libite.so.  Host arrays are numpy complex128, device arrays torch complex128
+CUDA tensors.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import lib, check
+
+BACKWARD_EULER, TRAPEZOID = L.ITE_BACKWARD_EULER, L.ITE_TRAPEZOID
+SHIFT_FIXED, SHIFT_CURRENT_ENERGY = L.ITE_SHIFT_FIXED, L.ITE_SHIFT_CURRENT_ENERGY
+SCHEMES = {"be": BACKWARD_EULER, "tr": TRAPEZOID}
+
+
+def _scheme(s):
+    return SCHEMES[s] if isinstance(s, str) else int(s)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def solver_opts(krylov_dim=10, sweeps=1, local_tol=0.0, sweep_tol=0.0, fit_sweeps=1):
+    o = L.ite_solver_opts()
+    lib.ite_solver_opts_default(C.byref(o))
+    o.krylov_dim, o.sweeps, o.local_tol = krylov_dim, sweeps, local_tol
+    o.sweep_tol, o.fit_sweeps = sweep_tol, fit_sweeps
+    return o
+
+
+class Context:
+    """One device and one stream (torch's current stream by default)."""
+
+    def __init__(self, device=0, stream=None, torch_allocator=True):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._keep = []
+        alloc_cb = L.ite_alloc_fn()
+        free_cb = L.ite_free_fn()
+        if torch_allocator:
+            dev, st = device, stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except RuntimeError:
+                    return None
+
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            alloc_cb, free_cb = L.ite_alloc_fn(_alloc), L.ite_free_fn(_free)
+            self._keep += [alloc_cb, free_cb]
+        h = C.c_void_p()
+        check(lib.ite_ctx_create(device, C.c_void_p(stream), alloc_cb, free_cb, None, C.byref(h)))
+        self.h = h
+
+    def error(self):
+        return lib.ite_last_error(self.h).decode()
+
+    def device_bytes(self):
+        return lib.ite_ctx_device_bytes(self.h)
+
+    def close(self):
+        if self.h:
+            lib.ite_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctx_create(device=0, stream=None, torch_allocator=True):
+    return Context(device, stream, torch_allocator)
+
+
+class MPO:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+        self.N = lib.ite_mpo_length(h)
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.ite_mpo_destroy(self.h)
+        except Exception:
+            pass
+
+
+def mpo_create(ctx, Ws):
+    """MPO from site tensors W_i[w, s', s, w'] (numpy arrays)."""
+    N = len(Ws)
+    d = np.array([W.shape[1] for W in Ws], np.int32)
+    D = np.array([Ws[0].shape[0]] + [W.shape[3] for W in Ws], np.int32)
+    flat = np.concatenate([_c128(W).ravel() for W in Ws]).view(np.float64)
+    h = C.c_void_p()
+    check(lib.ite_mpo_create(ctx.h, N, d.ctypes.data_as(C.POINTER(C.c_int)),
+                             D.ctypes.data_as(C.POINTER(C.c_int)), _dptr(flat), C.byref(h)), ctx.h)
+    return MPO(ctx, h)
+
+
+def mpo_create_heisenberg(ctx, N, J=1.0, Jz=None):
+    h = C.c_void_p()
+    check(lib.ite_mpo_create_heisenberg(ctx.h, N, J, J if Jz is None else Jz, C.byref(h)), ctx.h)
+    return MPO(ctx, h)
+
+
+def mpo_create_anderson(ctx, eps, V, U, eps_d):
+    eps = np.ascontiguousarray(eps, np.float64)
+    V = np.ascontiguousarray(V, np.float64)
+    h = C.c_void_p()
+    check(lib.ite_mpo_create_anderson(ctx.h, len(eps), _dptr(eps), _dptr(V), U, eps_d,
+                                      C.byref(h)), ctx.h)
+    return MPO(ctx, h)
+
+
+class MPS:
+    def __init__(self, ctx, h, N, d):
+        self.ctx, self.h, self.N, self.d = ctx, h, N, d
+
+    def bond_dims(self):
+        chi = np.zeros(self.N + 1, np.int32)
+        n = C.c_size_t()
+        check(lib.ite_mps_bond_dims(self.h, chi.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
+        return chi, n.value
+
+    def tensors(self):
+        """Site tensors as numpy complex128 arrays (chi_i, d, chi_{i+1})."""
+        chi, n = self.bond_dims()
+        buf = np.empty(n, np.float64)
+        check(lib.ite_mps_get(self.ctx.h, self.h, _dptr(buf), n), self.ctx.h)
+        z = buf.view(np.complex128)
+        out, pos = [], 0
+        for i in range(self.N):
+            cnt = chi[i] * self.d * chi[i + 1]
+            out.append(z[pos:pos + cnt].reshape(chi[i], self.d, chi[i + 1]).copy())
+            pos += cnt
+        return out
+
+    def set(self, tensors):
+        chi = np.array([1] + [T.shape[2] for T in tensors], np.int32)
+        flat = np.concatenate([_c128(T).ravel() for T in tensors]).view(np.float64)
+        check(lib.ite_mps_set(self.ctx.h, self.h, chi.ctypes.data_as(C.POINTER(C.c_int)),
+                              _dptr(flat)), self.ctx.h)
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.ite_mps_destroy(self.h)
+        except Exception:
+            pass
+
+
+def mps_create(ctx, tensors, chi_cap):
+    N, d = len(tensors), tensors[0].shape[1]
+    chi = np.array([1] + [T.shape[2] for T in tensors], np.int32)
+    flat = np.concatenate([_c128(T).ravel() for T in tensors]).view(np.float64)
+    h = C.c_void_p()
+    check(lib.ite_mps_create(ctx.h, N, d, chi.ctypes.data_as(C.POINTER(C.c_int)), _dptr(flat),
+                             chi_cap, C.byref(h)), ctx.h)
+    return MPS(ctx, h, N, d)
+
+
+def mps_create_product(ctx, site_vecs, chi_cap):
+    v = _c128(site_vecs)
+    N, d = v.shape
+    h = C.c_void_p()
+    check(lib.ite_mps_create_product(ctx.h, N, d, _dptr(v.view(np.float64)), chi_cap,
+                                     C.byref(h)), ctx.h)
+    return MPS(ctx, h, N, d)
+
+
+def mps_copy(ctx, src, dst):
+    check(lib.ite_mps_copy(ctx.h, src.h, dst.h), ctx.h)
+
+
+def implicit_step(ctx, H, psi, dtau, scheme, shift, chi_max, cutoff, opts=None):
+    info = L.ite_step_info()
+    o = opts if opts is not None else solver_opts()
+    check(lib.ite_implicit_step(ctx.h, H.h, psi.h, dtau, _scheme(scheme), shift, chi_max, cutoff,
+                                C.byref(o), C.byref(info)), ctx.h)
+    return info.as_dict()
+
+
+def _evolve(fn, ctx, H, psi, grid_args, n_steps, scheme, shift_mode, shift0, chi_max, cutoff,
+            opts):
+    infos = (L.ite_step_info * n_steps)()
+    nodes = np.zeros(n_steps + 1)
+    o = opts if opts is not None else solver_opts()
+    st = fn(ctx.h, H.h, psi.h, *grid_args, _scheme(scheme), shift_mode, shift0, chi_max, cutoff,
+            C.byref(o), infos, _dptr(nodes))
+    check(st, ctx.h)
+    return nodes, [i.as_dict() for i in infos]
+
+
+def evolve_loggrid(ctx, H, psi, tau0, tau_max, n_steps, scheme, chi_max, cutoff,
+                   shift_mode=SHIFT_FIXED, shift0=0.0, opts=None):
+    return _evolve(lib.ite_evolve_loggrid, ctx, H, psi, (tau0, tau_max, n_steps), n_steps, scheme,
+                   shift_mode, shift0, chi_max, cutoff, opts)
+
+
+def evolve_panels(ctx, H, psi, tau_max, P, n, scheme, chi_max, cutoff, shift_mode=SHIFT_FIXED,
+                  shift0=0.0, opts=None):
+    return _evolve(lib.ite_evolve_panels, ctx, H, psi, (tau_max, P, n), P * n, scheme, shift_mode,
+                   shift0, chi_max, cutoff, opts)
+
+
+def grid_geometric(tau0, tau_max, n_steps):
+    out = np.zeros(n_steps + 1)
+    check(lib.ite_grid_geometric(tau0, tau_max, n_steps, _dptr(out)))
+    return out
+
+
+def grid_panels(tau_max, P, n):
+    out = np.zeros(P * n + 1)
+    check(lib.ite_grid_panels(tau_max, P, n, _dptr(out)))
+    return out
+
+
+def energy(ctx, H, psi):
+    e = C.c_double()
+    check(lib.ite_energy(ctx.h, H.h, psi.h, C.byref(e)), ctx.h)
+    return e.value
+
+
+def overlap(ctx, bra, ket):
+    out = np.zeros(2)
+    check(lib.ite_overlap(ctx.h, bra.h, ket.h, _dptr(out)), ctx.h)
+    return complex(out[0], out[1])
+
+
+def correlator(ctx, psi, O, i, P, j, string_op=None):
+    o = _c128(O).view(np.float64)
+    p = _c128(P).view(np.float64)
+    s = _c128(string_op).view(np.float64) if string_op is not None else None
+    out = np.zeros(2)
+    check(lib.ite_correlator(ctx.h, psi.h, _dptr(o), i, _dptr(p), j,
+                             _dptr(s) if s is not None else None, _dptr(out)), ctx.h)
+    return complex(out[0], out[1])
+
+
+# ------------------------------------------------------------------ kernel level
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cpair(z):
+    a = np.array([complex(z).real, complex(z).imag])
+    return a
+
+
+def k_heff(ctx, H, i, L_env, R_env, X, Y, alpha=1.0, Z=None, gamma=0.0):
+    """Device tensors (torch complex128): L (D, chl_bra, chl_ket), R (D, chr_ket,
+    chr_bra), X (chl_ket, d, d, chr_ket), Y/Z (chl_bra, d, d, chr_bra)."""
+    a, g = _cpair(alpha), _cpair(gamma)
+    check(lib.ite_k_heff(ctx.h, H.h, i, L_env.shape[1], L_env.shape[2], R_env.shape[1],
+                         R_env.shape[2], _p(L_env), _p(R_env), _p(X), _p(Y), _dptr(a), _p(Z),
+                         _dptr(g)), ctx.h)
+
+
+def k_env_left(ctx, H, i, Lin, bra, ket, Lout):
+    check(lib.ite_k_env_left(ctx.h, H.h, i, bra.shape[0], ket.shape[0], bra.shape[2], ket.shape[2],
+                             _p(Lin), _p(bra), _p(ket), _p(Lout)), ctx.h)
+
+
+def k_env_right(ctx, H, i, Rin, bra, ket, Rout):
+    check(lib.ite_k_env_right(ctx.h, H.h, i, bra.shape[0], ket.shape[0], bra.shape[2],
+                              ket.shape[2], _p(Rin), _p(bra), _p(ket), _p(Rout)), ctx.h)
+
+
+def k_local_solve(ctx, H, i, L_env, R_env, B, X, alpha, c, krylov_dim=10, local_tol=0.0):
+    steps, res = C.c_int(), C.c_double()
+    check(lib.ite_k_local_solve(ctx.h, H.h, i, X.shape[0], X.shape[3], _p(L_env), _p(R_env),
+                                _p(B), _p(X), alpha, c, krylov_dim, local_tol, C.byref(steps),
+                                C.byref(res)), ctx.h)
+    return steps.value, res.value
+
+
+def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None):
+    r, disc = C.c_int(), C.c_double()
+    check(lib.ite_k_split(ctx.h, _p(X), m, n, chi_max, cutoff, 1 if centre_right else 0, _p(left),
+                          _p(right), _p(sigma), C.byref(r), C.byref(disc)), ctx.h)
+    return r.value, disc.value

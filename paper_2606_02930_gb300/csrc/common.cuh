@@ -1,0 +1,146 @@
+// Shared device/host helpers of the CUDA library: complex arithmetic on
+// double2 (interleaved re, im), launch checks and the internal API between the
+// translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+typedef double2 cplx;
+
+__host__ __device__ __forceinline__ cplx cmake(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ cplx cconj(cplx a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ cplx cscale(cplx a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(cplx& acc, cplx a, cplx b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfma_conj(cplx& acc, cplx a, cplx b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+namespace ite {
+
+// ---------------------------------------------------------------- GEMM (FP64)
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] (+ gamma * Z[b] if Z), complex.
+// Element (i, k) of A is at A[b*sAb + i*sAm + k*sAk] (conjugated if conjA);
+// element (k, j) of B at B[b*sBb + k*sBk + j*sBn]; C and Z are row-major with
+// leading dimension ldc and batch stride sCb.  Strides are in complex units.
+struct GemmArgs {
+  int M, N, K, batch;
+  const cplx* A; long long sAm, sAk, sAb; bool conjA;
+  const cplx* B; long long sBk, sBn, sBb; bool conjB;
+  cplx* C; long long ldc, sCb;
+  cplx alpha, beta;
+  const cplx* Z; cplx gamma;   // optional: C = alpha*AB + beta*C + gamma*Z
+};
+cudaError_t zgemm(const GemmArgs& g, cudaStream_t st);
+
+// ---------------------------------------------------------------- MPO mixing
+// Sparse "gather - small matrix - scatter" along the MPO channel and physical
+// indices.  Row k and column j of the small matrix decompose into up to three
+// digits (k0,k1,k2) / (j0,j1,j2) with sizes rdim / cdim (row-major digit
+// order).  For every outer pair (p, q), p < P, q < Q:
+//   out[p*oP + q*oQ + sum_i k_i*oc[i]] = sum_e val[e] * in[p*iP + q*iQ + sum_i j_i*ic[i]]
+// over the CSR entries e of row k (rows without entries write zero).
+struct MixPlan {
+  int nrows, ncols, nnz;
+  int rdim[3], cdim[3];
+  int* row_ptr;  // device, nrows+1
+  int* col;      // device, nnz
+  cplx* val;     // device, nnz
+};
+struct MixStrides {
+  long long ic[3], oc[3];
+};
+cudaError_t mix_apply(const MixPlan& plan, const MixStrides& s, int P, int Q, const cplx* in,
+                      long long iP, long long iQ, cplx* out, long long oP, long long oQ,
+                      cudaStream_t st);
+
+// ---------------------------------------------------------------- vectors
+// Krylov and reduction kernels.  Partial sums are reduced in a fixed order,
+// so every reduction is deterministic for a given launch shape.
+cudaError_t vec_copy(cplx* y, const cplx* x, long long n, cudaStream_t st);
+cudaError_t vec_zero(cplx* y, long long n, cudaStream_t st);
+// y = a*x + b*y  (a, b complex scalars given on the host)
+cudaError_t vec_axpby(cplx* y, const cplx* x, cplx a, cplx b, long long n, cudaStream_t st);
+// out[i] = sum_e conj(V[i*ldv + e]) * w[e], i < nv  (device output); skips if *active == 0
+cudaError_t vec_block_dot(const cplx* V, long long ldv, int nv, const cplx* w, long long n,
+                          cplx* out, cplx* partial, const int* active, cudaStream_t st);
+// w += sign * sum_i h[i] * V[i*ldv + .]  (h on device); skips if *active == 0
+// (if nv_dev is given, only the first min(nv, *nv_dev) vectors are used)
+cudaError_t vec_block_axpy(const cplx* V, long long ldv, int nv, const int* nv_dev,
+                           const cplx* h, double sign, cplx* w, long long n, const int* active,
+                           cudaStream_t st);
+// out = sum |x|^2 (device double); skips if *active == 0
+cudaError_t vec_norm2(const cplx* x, long long n, double* out, double* partial,
+                      const int* active, cudaStream_t st);
+// y *= *scale (device double); skips if *active == 0
+cudaError_t vec_scale_dev(cplx* y, const double* scale, long long n, const int* active,
+                          cudaStream_t st);
+// out = sum_{w,b,b'} L[w][b][b'] * R[w][b'][b]  (device complex)
+cudaError_t env_trace(const cplx* L, const cplx* R, int D, int m, int n, cplx* out,
+                      cplx* partial, cudaStream_t st);
+// K'[a][s'][b] = sum_s O[s'][s] K[a][s][b] (O on device, d x d)
+cudaError_t apply_site_op(const cplx* O, const cplx* K, cplx* Kout, int chl, int d, int chr,
+                          cudaStream_t st);
+
+// ---------------------------------------------------------------- GMRES control
+// Device-side state of one GMRES cycle (Givens QR of the Hessenberg matrix).
+struct GmresState {
+  cplx H[(32 + 1) * 32];  // column-major (m+1) x m, m <= 32
+  cplx cs[32], sn[32];
+  cplx g[33];
+  cplx y[32];
+  cplx h[64];             // scratch: this step's projections (two passes)
+  double beta, bnorm, wnorm2, inv_h, res;
+  int steps, active, breakdown;
+};
+// r0 = B - AX0 is in V0 with |r0|^2 in *norm2: set beta, scale factor, g.
+cudaError_t gmres_start(GmresState* s, const double* r0norm2, const double* bnorm2,
+                        cudaStream_t st);
+// after Arnoldi step j (h1, h2 in s->h, |w|^2 in s->wnorm2): Givens update,
+// breakdown/convergence test, 1/h_{j+1,j} for the next basis vector.
+cudaError_t gmres_step(GmresState* s, int j, int m, double breakdown_rel, double local_tol,
+                       cudaStream_t st);
+// solve the triangular system for y (k = s->steps) and write y into s->y
+cudaError_t gmres_finish(GmresState* s, cudaStream_t st);
+// add the projections of the two Gram-Schmidt passes into column j of H
+cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cplx* h2,
+                          cudaStream_t st);
+
+// ---------------------------------------------------------------- SVD (FP64)
+// One-sided Jacobi SVD of a p x q complex matrix stored row-major in A (rows
+// are the rotated vectors, p <= q expected).  Q (p x p) receives the
+// accumulated row rotations: on return Q A_in = A_out with orthogonal rows.
+cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
+                        int* sweeps_done, int* host_counter, int* dev_counter,
+                        cudaStream_t st);
+// row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
+// by index), and the kept rank by the truncation rule (see engine).
+cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
+                     int chi_max, double cutoff, double weight_floor, double tie_rel,
+                     int* rank_out, double* discarded_out, cudaStream_t st);
+// write the two factors of a split (see engine for the four cases)
+cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma,
+                     const int* perm, int r, int p, int q, bool transposed, bool centre_right,
+                     cplx* left, cplx* right, cudaStream_t st);
+// out = A^H for a row-major m x n matrix A (out is n x m)
+cudaError_t conj_transpose(const cplx* A, int m, int n, cplx* out, cudaStream_t st);
+// Q = identity (p x p)
+cudaError_t set_identity(cplx* Q, int p, cudaStream_t st);
+
+}  // namespace ite

@@ -1,0 +1,1379 @@
+// Host orchestration and the C ABI (include/ite.h, include/ite_kernels.h).
+//
+// One implicit step (Eq. 4 or backward Euler) runs, in this order:
+//   1. right-hand side MPS b: psi itself (backward Euler) or a two-site fit of
+//      (I - c (H - s)) psi (trapezoid rule, Method operation (i));
+//   2. x <- b (trapezoid) or psi (backward Euler) as the initial guess (App. B);
+//   3. gauge move: x right-canonical by SVDs from the last site to the second;
+//   4. right environments of <x|H|x> and <x|b>;
+//   5. two-site sweep L->R then R->L (App. B, App. D): at each bond the local
+//      right-hand side (projection of b), GMRES on (1 - c s) X + c H_eff X = B,
+//      truncated SVD split, environment update;
+//   6. normalisation of the centre tensor and the energy.
+// Every numerical step is a CUDA kernel of this library; the host only
+// sequences launches and reads back the kept rank of each split.
+#include "common.cuh"
+#include "ite.h"
+#include "ite_kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace ite;
+
+namespace {
+
+constexpr double kWeightFloor = 1e-24;   // relative squared weight treated as zero
+constexpr double kTieRel = 1e-10;        // near-degenerate singular values
+constexpr double kBreakdownRel = 1e-14;  // GMRES breakdown threshold (relative to |r0|)
+constexpr double kJacobiTol = 1e-14;     // one-sided Jacobi orthogonality tolerance
+constexpr int kJacobiSweeps = 40;
+constexpr int kMaxKrylov = 32;
+constexpr int kPartialSlots = 608 * kMaxKrylov;
+
+struct HostRead {
+  int rank;
+  int steps;
+  int counter;
+  int pad;
+  double disc;
+  double res;
+  double d[4];
+  cplx z[4];
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct ite_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ite_alloc_fn alloc = nullptr;
+  ite_free_fn release = nullptr;
+  void* user = nullptr;
+  std::string err;
+  size_t bytes = 0;
+  // workspace
+  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env;
+  GmresState* gm = nullptr;
+  double* dscal = nullptr;     // device scalars
+  cplx* dcplx = nullptr;       // device complex scalars
+  cplx* partial = nullptr;     // reduction partials
+  int* dcounter = nullptr;
+  HostRead* hr = nullptr;      // pinned
+};
+
+struct ite_mpo_s {
+  ite_ctx ctx = nullptr;
+  int N = 0, d = 0;
+  std::vector<int> D;                      // N+1
+  std::vector<std::vector<cplx>> Wh;       // host copies, W_i[w][s'][s][w']
+  Buf Wdev;
+  std::vector<cplx*> W;                    // device pointers per site
+  Buf plan_mem;
+  std::vector<MixPlan> planL, planR, plan2;
+  int Dmax = 1;
+};
+
+struct ite_mps_s {
+  ite_ctx ctx = nullptr;
+  int N = 0, d = 0, chi_cap = 0;
+  std::vector<int> chi, cap;               // N+1
+  Buf mem;
+  std::vector<cplx*> site;
+  ite_mps work_x = nullptr, work_b = nullptr, work_p = nullptr;  // internal copies for the step
+};
+
+// ------------------------------------------------------------------ memory
+namespace {
+
+ite_status fail(ite_ctx ctx, ite_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(ctx, ITE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CS(call)                          \
+  do {                                    \
+    ite_status s_ = (call);               \
+    if (s_ != ITE_OK) return s_;          \
+  } while (0)
+
+void* dev_alloc(ite_ctx ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, ctx->user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) ctx->bytes += bytes;
+  return p;
+}
+
+void dev_free(ite_ctx ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (ctx->release) ctx->release(p, bytes, ctx->user);
+  else cudaFree(p);
+  ctx->bytes -= bytes;
+}
+
+void buf_free(ite_ctx ctx, Buf& b) {
+  dev_free(ctx, b.p, b.n);
+  b.p = nullptr;
+  b.n = 0;
+}
+
+ite_status buf_ensure(ite_ctx ctx, Buf& b, size_t bytes) {
+  if (b.n >= bytes && b.p) return ITE_OK;
+  buf_free(ctx, b);
+  b.p = dev_alloc(ctx, bytes);
+  if (!b.p) return fail(ctx, ITE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  b.n = bytes;
+  return ITE_OK;
+}
+
+template <typename T>
+T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+cplx C(double r, double i = 0.0) { return cmake(r, i); }
+
+ite_status sync(ite_ctx ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ITE_OK;
+}
+
+// ------------------------------------------------------------------ contractions
+// Plain GEMM helpers.  Row-major matrices; strides in complex units.
+ite_status gemm(ite_ctx ctx, int M, int N, int K, const cplx* A, long long sAm, long long sAk,
+                bool conjA, const cplx* B, long long sBk, long long sBn, bool conjB, cplx* Cm,
+                long long ldc, cplx alpha = C(1), cplx beta = C(0), const cplx* Z = nullptr,
+                cplx gamma = C(0), int batch = 1, long long sAb = 0, long long sBb = 0,
+                long long sCb = 0) {
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.A = A; g.sAm = sAm; g.sAk = sAk; g.sAb = sAb; g.conjA = conjA;
+  g.B = B; g.sBk = sBk; g.sBn = sBn; g.sBb = sBb; g.conjB = conjB;
+  g.C = Cm; g.ldc = ldc; g.sCb = sCb;
+  g.alpha = alpha; g.beta = beta; g.Z = Z; g.gamma = gamma;
+  CK(zgemm(g, ctx->stream));
+  return ITE_OK;
+}
+
+// Y = alpha * H_eff X + gamma * Z on sites (i, i+1)
+ite_status heff(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int chrB,
+                const cplx* L, const cplx* R, const cplx* X, cplx* Y, cplx alpha, const cplx* Z,
+                cplx gamma) {
+  const int d = H->d, D0 = H->D[i], D2 = H->D[i + 2];
+  const long long d2 = (long long)d * d;
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  cplx* T2 = P<cplx>(ctx->ws_T2);
+  // T1[(w a), (s t b')] = L[(w a), a'] X[a', (s t b')]
+  CS(gemm(ctx, D0 * chlB, (int)(d2 * chrK), chlK, L, chlK, 1, false, X, d2 * chrK, 1, false, T1,
+          d2 * chrK));
+  // T2[a, s', t', w'', b'] = sum W2[(s' t' w''), (w s t)] T1[w, a, s, t, b']
+  MixStrides ms;
+  ms.ic[0] = (long long)chlB * d2 * chrK; ms.ic[1] = (long long)d * chrK; ms.ic[2] = chrK;
+  ms.oc[0] = (long long)d * D2 * chrK; ms.oc[1] = (long long)D2 * chrK; ms.oc[2] = chrK;
+  CK(mix_apply(H->plan2[i], ms, chlB, chrK, T1, d2 * chrK, 1, T2, d2 * D2 * chrK, 1, ctx->stream));
+  // Y[(a s' t'), b] = alpha * T2[(a s' t'), (w'' b')] R[(w'' b'), b] + gamma Z
+  CS(gemm(ctx, (int)(chlB * d2), chrB, D2 * chrK, T2, (long long)D2 * chrK, 1, false, R, chrB, 1,
+          false, Y, chrB, alpha, C(0), Z, gamma));
+  return ITE_OK;
+}
+
+ite_status env_left(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB, int chrK,
+                    const cplx* Lin, const cplx* bra, const cplx* ket, cplx* Lout) {
+  const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1];
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  cplx* T2 = P<cplx>(ctx->ws_T2);
+  const long long ld = (long long)d * chrK;
+  CS(gemm(ctx, D0 * chlB, (int)ld, chlK, Lin, chlK, 1, false, ket, ld, 1, false, T1, ld));
+  MixStrides ms;
+  ms.ic[0] = (long long)chlB * ld; ms.ic[1] = chrK; ms.ic[2] = 0;
+  ms.oc[0] = (long long)chlB * ld; ms.oc[1] = chrK; ms.oc[2] = 0;
+  CK(mix_apply(H->planL[i], ms, chlB, chrK, T1, ld, 1, T2, ld, 1, ctx->stream));
+  // Lout[w'] (chrB x chrK) = bra^H ((chrB) x (chlB d)) T2[w'] ((chlB d) x chrK)
+  CS(gemm(ctx, chrB, chrK, chlB * d, bra, 1, chrB, true, T2, chrK, 1, false, Lout, chrK, C(1),
+          C(0), nullptr, C(0), D1, 0, (long long)chlB * ld, (long long)chrB * chrK));
+  return ITE_OK;
+}
+
+ite_status env_right(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB, int chrK,
+                     const cplx* Rin, const cplx* bra, const cplx* ket, cplx* Rout) {
+  const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1];
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  cplx* T2 = P<cplx>(ctx->ws_T2);
+  const long long blk = (long long)chlK * d * chrB;
+  // T1[w'][(a' s)][b] = ket[(a' s), b'] Rin[w'][b'][b]
+  CS(gemm(ctx, chlK * d, chrB, chrK, ket, chrK, 1, false, Rin, chrB, 1, false, T1, chrB, C(1),
+          C(0), nullptr, C(0), D1, 0, (long long)chrK * chrB, blk));
+  MixStrides ms;
+  ms.ic[0] = blk; ms.ic[1] = chrB; ms.ic[2] = 0;
+  ms.oc[0] = blk; ms.oc[1] = chrB; ms.oc[2] = 0;
+  CK(mix_apply(H->planR[i], ms, chlK, chrB, T1, (long long)d * chrB, 1, T2, (long long)d * chrB, 1,
+               ctx->stream));
+  // Rout[w] (chlK x chlB) = T2[w] (chlK x (d chrB)) conj(bra)^T ((d chrB) x chlB)
+  CS(gemm(ctx, chlK, chlB, d * chrB, T2, (long long)d * chrB, 1, false, bra, 1, (long long)d * chrB,
+          true, Rout, chlB, C(1), C(0), nullptr, C(0), D0, blk, 0, (long long)chlK * chlB));
+  return ITE_OK;
+}
+
+ite_status ov_left(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, const cplx* Lin,
+                   const cplx* bra, const cplx* ket, cplx* Lout) {
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  const long long ld = (long long)d * chrK;
+  CS(gemm(ctx, chlB, (int)ld, chlK, Lin, chlK, 1, false, ket, ld, 1, false, T1, ld));
+  CS(gemm(ctx, chrB, chrK, chlB * d, bra, 1, chrB, true, T1, chrK, 1, false, Lout, chrK));
+  return ITE_OK;
+}
+
+ite_status ov_right(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, const cplx* Rin,
+                    const cplx* bra, const cplx* ket, cplx* Rout) {
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  CS(gemm(ctx, chlK * d, chrB, chrK, ket, chrK, 1, false, Rin, chrB, 1, false, T1, chrB));
+  CS(gemm(ctx, chlK, chlB, d * chrB, T1, (long long)d * chrB, 1, false, bra, 1, (long long)d * chrB,
+          true, Rout, chlB));
+  return ITE_OK;
+}
+
+// out[a,s,t,b] = alpha * sum LO[a][a''] K1[a'',s,c] K2[c,t,b''] RO[b''][b]
+ite_status project(ite_ctx ctx, int d, int chlB, int chlK, int chm, int chrK, int chrB,
+                   const cplx* LO, const cplx* K1, const cplx* K2, const cplx* RO, cplx* out) {
+  cplx* T1 = P<cplx>(ctx->ws_T1);
+  cplx* T2 = P<cplx>(ctx->ws_T2);
+  CS(gemm(ctx, chlB, d * chm, chlK, LO, chlK, 1, false, K1, (long long)d * chm, 1, false, T1,
+          (long long)d * chm));
+  CS(gemm(ctx, chlB * d, d * chrK, chm, T1, chm, 1, false, K2, (long long)d * chrK, 1, false, T2,
+          (long long)d * chrK));
+  CS(gemm(ctx, chlB * d * d, chrB, chrK, T2, chrK, 1, false, RO, chrB, 1, false, out, chrB));
+  return ITE_OK;
+}
+
+ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, const cplx* K2,
+                 cplx* out) {
+  return gemm(ctx, chl * d, d * chr, chm, K1, chm, 1, false, K2, (long long)d * chr, 1, false, out,
+              (long long)d * chr);
+}
+
+// Truncated SVD of X (m x n). Writes left (m x r) and right (r x n); returns r.
+ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
+                 bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
+                 double* sigma_out = nullptr) {
+  cplx* A = P<cplx>(ctx->ws_svdA);
+  cplx* Q = P<cplx>(ctx->ws_svdQ);
+  const bool tr = m > n;
+  const int p = tr ? n : m, q = tr ? m : n;
+  if (tr) CK(conj_transpose(X, m, n, A, ctx->stream));
+  else CK(vec_copy(A, X, (long long)m * n, ctx->stream));
+  int sweeps = 0;
+  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, kJacobiTol, &sweeps, &ctx->hr->counter, ctx->dcounter,
+                 ctx->stream));
+  double* small = P<double>(ctx->ws_small);
+  double* sigma = small;
+  double* sorted = small + p;
+  int* perm = reinterpret_cast<int*>(small + 2 * p);
+  int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
+  double* disc_dev = ctx->dscal + 7;
+  CK(svd_rank(A, p, q, sigma, perm, sorted, chi_max, cutoff, kWeightFloor, kTieRel, rank_dev,
+              disc_dev, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  const int r = ctx->hr->rank;
+  if (r < 1 || r > p) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
+  if (sigma_out) CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(svd_emit(A, Q, sorted, perm, r, p, q, tr, centre_right, left, right, ctx->stream));
+  *r_out = r;
+  *disc_out = ctx->hr->disc;
+  if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
+  return ITE_OK;
+}
+
+// One GMRES cycle on (alpha I + c H_eff) X = B; X updated in place.
+ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
+                       const cplx* R, const cplx* B, cplx* X, double alpha, double c, int m,
+                       double local_tol, int* steps, double* res) {
+  const long long n = (long long)chl * H->d * H->d * chr;
+  cplx* V = P<cplx>(ctx->ws_V);
+  GmresState* gs = ctx->gm;
+  int* active = &gs->active;
+  double* r0n2 = ctx->dscal + 0;
+  double* bn2 = ctx->dscal + 1;
+  const cplx ca = C(alpha), cc = C(c);
+  // r0 = B - A X0
+  CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, X, V, cc, X, ca));
+  CK(vec_axpby(V, B, C(1), C(-1), n, ctx->stream));
+  CK(vec_norm2(V, n, r0n2, ctx->dscal + 16, nullptr, ctx->stream));
+  CK(vec_norm2(B, n, bn2, ctx->dscal + 16, nullptr, ctx->stream));
+  CK(gmres_start(gs, r0n2, bn2, ctx->stream));
+  CK(vec_scale_dev(V, &gs->inv_h, n, active, ctx->stream));
+  for (int j = 0; j < m; ++j) {
+    cplx* vj = V + j * n;
+    cplx* w = V + (j + 1) * n;
+    CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, vj, w, cc, vj, ca));
+    CK(vec_block_dot(V, n, j + 1, w, n, gs->h, ctx->partial, active, ctx->stream));
+    CK(vec_block_axpy(V, n, j + 1, nullptr, gs->h, -1.0, w, n, active, ctx->stream));
+    CK(vec_block_dot(V, n, j + 1, w, n, gs->h + 32, ctx->partial, active, ctx->stream));
+    CK(vec_block_axpy(V, n, j + 1, nullptr, gs->h + 32, -1.0, w, n, active, ctx->stream));
+    CK(gmres_collect(gs, j, m, gs->h, gs->h + 32, ctx->stream));
+    CK(vec_norm2(w, n, &gs->wnorm2, ctx->dscal + 16, active, ctx->stream));
+    CK(gmres_step(gs, j, m, kBreakdownRel, local_tol, ctx->stream));
+    CK(vec_scale_dev(w, &gs->inv_h, n, active, ctx->stream));
+  }
+  CK(gmres_finish(gs, ctx->stream));
+  CK(vec_block_axpy(V, n, m, &gs->steps, gs->y, 1.0, X, n, nullptr, ctx->stream));
+  if (steps || res) {
+    CK(cudaMemcpyAsync(&ctx->hr->steps, &gs->steps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hr->res, &gs->res, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hr->d[0], &gs->bnorm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CS(sync(ctx));
+    if (steps) *steps = ctx->hr->steps;
+    if (res) *res = ctx->hr->d[0] > 0 ? ctx->hr->res / ctx->hr->d[0] : 0.0;
+  }
+  return ITE_OK;
+}
+
+// ------------------------------------------------------------------ MPO setup
+void build_plan(std::vector<int>& rp, std::vector<int>& cols, std::vector<cplx>& vals,
+                const std::vector<cplx>& dense, int nrows, int ncols) {
+  rp.assign(nrows + 1, 0);
+  cols.clear();
+  vals.clear();
+  for (int k = 0; k < nrows; ++k) {
+    for (int j = 0; j < ncols; ++j) {
+      const cplx v = dense[(size_t)k * ncols + j];
+      if (v.x != 0.0 || v.y != 0.0) {
+        cols.push_back(j);
+        vals.push_back(v);
+      }
+    }
+    rp[k + 1] = (int)cols.size();
+  }
+}
+
+ite_status mpo_finish(ite_mpo H) {
+  ite_ctx ctx = H->ctx;
+  const int N = H->N, d = H->d;
+  H->Dmax = *std::max_element(H->D.begin(), H->D.end());
+  size_t total = 0;
+  std::vector<size_t> off(N);
+  for (int i = 0; i < N; ++i) {
+    off[i] = total;
+    total += H->Wh[i].size();
+  }
+  CS(buf_ensure(ctx, H->Wdev, total * sizeof(cplx)));
+  H->W.resize(N);
+  for (int i = 0; i < N; ++i) {
+    H->W[i] = P<cplx>(H->Wdev) + off[i];
+    CK(cudaMemcpy(H->W[i], H->Wh[i].data(), H->Wh[i].size() * sizeof(cplx), cudaMemcpyHostToDevice));
+  }
+  // mixing matrices on the host (MPO setup), then one device block for all
+  struct Host { std::vector<int> rp, col; std::vector<cplx> val; int nr, nc, rd[3], cd[3]; };
+  std::vector<Host> hs;
+  auto Wat = [&](int i, int w, int sp, int s, int w2) -> cplx {
+    const int Dr = H->D[i + 1];
+    return H->Wh[i][(((size_t)w * d + sp) * d + s) * Dr + w2];
+  };
+  for (int i = 0; i < N; ++i) {
+    const int Dl = H->D[i], Dr = H->D[i + 1];
+    // left update: rows (w', s'), cols (w, s)
+    Host hl; hl.nr = Dr * d; hl.nc = Dl * d;
+    hl.rd[0] = Dr; hl.rd[1] = d; hl.rd[2] = 1; hl.cd[0] = Dl; hl.cd[1] = d; hl.cd[2] = 1;
+    std::vector<cplx> dl((size_t)hl.nr * hl.nc, C(0));
+    for (int w = 0; w < Dl; ++w)
+      for (int sp = 0; sp < d; ++sp)
+        for (int s = 0; s < d; ++s)
+          for (int w2 = 0; w2 < Dr; ++w2) dl[(size_t)(w2 * d + sp) * hl.nc + (w * d + s)] = Wat(i, w, sp, s, w2);
+    build_plan(hl.rp, hl.col, hl.val, dl, hl.nr, hl.nc);
+    hs.push_back(hl);
+    // right update: rows (w, s'), cols (w', s)
+    Host hr; hr.nr = Dl * d; hr.nc = Dr * d;
+    hr.rd[0] = Dl; hr.rd[1] = d; hr.rd[2] = 1; hr.cd[0] = Dr; hr.cd[1] = d; hr.cd[2] = 1;
+    std::vector<cplx> dr((size_t)hr.nr * hr.nc, C(0));
+    for (int w = 0; w < Dl; ++w)
+      for (int sp = 0; sp < d; ++sp)
+        for (int s = 0; s < d; ++s)
+          for (int w2 = 0; w2 < Dr; ++w2) dr[(size_t)(w * d + sp) * hr.nc + (w2 * d + s)] = Wat(i, w, sp, s, w2);
+    build_plan(hr.rp, hr.col, hr.val, dr, hr.nr, hr.nc);
+    hs.push_back(hr);
+  }
+  for (int i = 0; i + 1 < N; ++i) {
+    const int D0 = H->D[i], D1 = H->D[i + 1], D2 = H->D[i + 2];
+    Host h2; h2.nr = d * d * D2; h2.nc = D0 * d * d;
+    h2.rd[0] = d; h2.rd[1] = d; h2.rd[2] = D2; h2.cd[0] = D0; h2.cd[1] = d; h2.cd[2] = d;
+    std::vector<cplx> dd((size_t)h2.nr * h2.nc, C(0));
+    for (int w = 0; w < D0; ++w)
+      for (int sp = 0; sp < d; ++sp)
+        for (int s = 0; s < d; ++s)
+          for (int v = 0; v < D1; ++v) {
+            const cplx a = Wat(i, w, sp, s, v);
+            if (a.x == 0.0 && a.y == 0.0) continue;
+            for (int tp = 0; tp < d; ++tp)
+              for (int t = 0; t < d; ++t)
+                for (int w2 = 0; w2 < D2; ++w2) {
+                  const cplx b = Wat(i + 1, v, tp, t, w2);
+                  cplx& dst = dd[(size_t)((sp * d + tp) * D2 + w2) * h2.nc + ((w * d + s) * d + t)];
+                  dst = cadd(dst, cmul(a, b));
+                }
+          }
+    build_plan(h2.rp, h2.col, h2.val, dd, h2.nr, h2.nc);
+    hs.push_back(h2);
+  }
+  size_t bytes = 0;
+  for (auto& h : hs) bytes += (h.rp.size() + h.col.size()) * sizeof(int) + h.val.size() * sizeof(cplx) + 64;
+  CS(buf_ensure(ctx, H->plan_mem, bytes));
+  char* base = P<char>(H->plan_mem);
+  size_t pos = 0;
+  std::vector<MixPlan> plans;
+  for (auto& h : hs) {
+    MixPlan pl;
+    pl.nrows = h.nr; pl.ncols = h.nc; pl.nnz = (int)h.val.size();
+    for (int t = 0; t < 3; ++t) { pl.rdim[t] = h.rd[t]; pl.cdim[t] = h.cd[t]; }
+    pos = (pos + 15) & ~size_t(15);
+    pl.val = reinterpret_cast<cplx*>(base + pos);
+    CK(cudaMemcpy(pl.val, h.val.data(), h.val.size() * sizeof(cplx), cudaMemcpyHostToDevice));
+    pos += h.val.size() * sizeof(cplx);
+    pl.row_ptr = reinterpret_cast<int*>(base + pos);
+    CK(cudaMemcpy(pl.row_ptr, h.rp.data(), h.rp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    pos += h.rp.size() * sizeof(int);
+    pl.col = reinterpret_cast<int*>(base + pos);
+    CK(cudaMemcpy(pl.col, h.col.data(), h.col.size() * sizeof(int), cudaMemcpyHostToDevice));
+    pos += h.col.size() * sizeof(int);
+    plans.push_back(pl);
+  }
+  H->planL.resize(N);
+  H->planR.resize(N);
+  for (int i = 0; i < N; ++i) {
+    H->planL[i] = plans[2 * i];
+    H->planR[i] = plans[2 * i + 1];
+  }
+  H->plan2.clear();
+  for (int i = 0; i + 1 < N; ++i) H->plan2.push_back(plans[2 * N + i]);
+  return ITE_OK;
+}
+
+// ------------------------------------------------------------------ MPS setup
+std::vector<int> capacities(int N, int d, int chi_cap) {
+  std::vector<int> cap(N + 1, 1);
+  for (int b = 1; b < N; ++b) {
+    long long c = chi_cap;
+    long long l = 1, r = 1;
+    for (int k = 0; k < b && l < c; ++k) l *= d;
+    for (int k = 0; k < N - b && r < c; ++k) r *= d;
+    c = std::min(c, std::min(l, r));
+    cap[b] = (int)c;
+  }
+  return cap;
+}
+
+ite_status mps_alloc(ite_ctx ctx, int N, int d, int chi_cap, ite_mps* out) {
+  ite_mps m = new ite_mps_s();
+  m->ctx = ctx;
+  m->N = N;
+  m->d = d;
+  m->chi_cap = chi_cap;
+  m->cap = capacities(N, d, chi_cap);
+  m->chi.assign(N + 1, 1);
+  size_t total = 0;
+  std::vector<size_t> off(N);
+  for (int i = 0; i < N; ++i) {
+    off[i] = total;
+    total += (size_t)m->cap[i] * d * m->cap[i + 1];
+  }
+  ite_status st = buf_ensure(ctx, m->mem, total * sizeof(cplx));
+  if (st != ITE_OK) {
+    delete m;
+    return st;
+  }
+  m->site.resize(N);
+  for (int i = 0; i < N; ++i) m->site[i] = P<cplx>(m->mem) + off[i];
+  *out = m;
+  return ITE_OK;
+}
+
+void mps_free(ite_mps m) {
+  if (!m) return;
+  if (m->work_x) mps_free(m->work_x);
+  if (m->work_b) mps_free(m->work_b);
+  if (m->work_p) mps_free(m->work_p);
+  buf_free(m->ctx, m->mem);
+  delete m;
+}
+
+ite_status mps_copy_into(ite_ctx ctx, ite_mps src, ite_mps dst) {
+  for (int i = 0; i < src->N; ++i)
+    CK(vec_copy(dst->site[i], src->site[i], (long long)src->chi[i] * src->d * src->chi[i + 1], ctx->stream));
+  dst->chi = src->chi;
+  return ITE_OK;
+}
+
+void mps_swap(ite_mps a, ite_mps b) {
+  std::swap(a->mem, b->mem);
+  std::swap(a->site, b->site);
+  std::swap(a->chi, b->chi);
+}
+
+ite_status ensure_work(ite_ctx ctx, ite_mps psi) {
+  if (!psi->work_x) CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &psi->work_x));
+  if (!psi->work_b) CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &psi->work_b));
+  return ITE_OK;
+}
+
+// workspace for sweeps over an MPS of these capacities with this MPO
+ite_status ensure_workspace(ite_ctx ctx, ite_mpo H, const std::vector<int>& cap, int d, int krylov) {
+  const int N = H->N;
+  long long nmax = 1, pmax = 1, envs = 0, ovs = 0, site_max = 1;
+  for (int i = 0; i + 1 < N; ++i) {
+    const long long m = (long long)cap[i] * d, n = (long long)d * cap[i + 2];
+    nmax = std::max(nmax, m * n);
+    pmax = std::max(pmax, std::min(m, n));
+  }
+  for (int i = 0; i < N; ++i) {
+    site_max = std::max(site_max, (long long)cap[i] * d * cap[i + 1]);
+    pmax = std::max(pmax, std::min((long long)cap[i], (long long)d * cap[i + 1]));
+  }
+  nmax = std::max(nmax, site_max);
+  for (int b = 0; b <= N; ++b) {
+    envs += (long long)H->D[b] * cap[b] * cap[b];
+    ovs += (long long)cap[b] * cap[b];
+  }
+  const size_t cs = sizeof(cplx);
+  const long long tmax = (long long)H->Dmax * nmax;
+  CS(buf_ensure(ctx, ctx->ws_X, nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_B, nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_X2, nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_V, (size_t)(krylov + 1) * nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_T1, tmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_T2, tmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_svdA, nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)pmax * pmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_left, nmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_small, (size_t)pmax * 3 * sizeof(double) + 64));
+  CS(buf_ensure(ctx, ctx->ws_env, (size_t)(2 * envs + 2 * ovs + 16) * cs));
+  return ITE_OK;
+}
+
+struct EnvSet {
+  std::vector<cplx*> LE, RE, LO, RO;
+};
+
+// carve the env workspace: operator envs sized D[b] cap_bra[b] cap_ket[b], overlaps cap^2
+EnvSet carve_envs(ite_ctx ctx, ite_mpo H, const std::vector<int>& cap) {
+  EnvSet e;
+  const int N = H->N;
+  cplx* p = P<cplx>(ctx->ws_env);
+  e.LE.resize(N + 1); e.RE.resize(N + 1); e.LO.resize(N + 1); e.RO.resize(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    const long long op = (long long)H->D[b] * cap[b] * cap[b], ov = (long long)cap[b] * cap[b];
+    e.LE[b] = p; p += op;
+    e.RE[b] = p; p += op;
+    e.LO[b] = p; p += ov;
+    e.RO[b] = p; p += ov;
+  }
+  return e;
+}
+
+ite_status set_one(ite_ctx ctx, cplx* p) {
+  const cplx one = C(1);
+  CK(cudaMemcpyAsync(p, &one, sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
+  return ITE_OK;
+}
+
+// gauge move: sites N-1..1 right-orthonormal by SVD (weight floor only)
+ite_status right_canonicalize(ite_ctx ctx, ite_mps x) {
+  const int d = x->d;
+  for (int i = x->N - 1; i >= 1; --i) {
+    const int chl = x->chi[i], chr = x->chi[i + 1];
+    int r = 0;
+    double disc = 0.0;
+    cplx* left = P<cplx>(ctx->ws_left);
+    CS(split(ctx, x->site[i], chl, d * chr, 1 << 30, 0.0, false, left, x->site[i], &r, &disc));
+    // x_{i-1} <- x_{i-1} (U S)
+    const int chll = x->chi[i - 1];
+    cplx* T = P<cplx>(ctx->ws_X2);
+    CS(gemm(ctx, chll * d, r, chl, x->site[i - 1], chl, 1, false, left, r, 1, false, T, r));
+    CK(vec_copy(x->site[i - 1], T, (long long)chll * d * r, ctx->stream));
+    x->chi[i] = r;
+  }
+  return ITE_OK;
+}
+
+struct SweepStats {
+  double max_disc = 0.0, max_res = 0.0;
+  int steps = 0;
+};
+
+// Two-site sweep solving (alpha I + c H) x = b, or (fit mode) x ~ alpha b + beta H b.
+ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, double alpha, double cbeta,
+                 int chi_max, double cutoff, const ite_solver_opts& o, SweepStats& stats) {
+  const int N = x->N, d = x->d;
+  EnvSet e = carve_envs(ctx, H, x->cap);
+  // operator envs: bra x, ket (fit ? b : x); overlap envs: bra x, ket b
+  ite_mps kop = fit ? b : x;
+  CS(set_one(ctx, e.RE[N]));
+  CS(set_one(ctx, e.RO[N]));
+  for (int i = N - 1; i >= 2; --i) {
+    CS(env_right(ctx, H, i, x->chi[i], kop->chi[i], x->chi[i + 1], kop->chi[i + 1], e.RE[i + 1],
+                 x->site[i], kop->site[i], e.RE[i]));
+    CS(ov_right(ctx, d, x->chi[i], b->chi[i], x->chi[i + 1], b->chi[i + 1], e.RO[i + 1], x->site[i],
+                b->site[i], e.RO[i]));
+  }
+  CS(set_one(ctx, e.LE[0]));
+  CS(set_one(ctx, e.LO[0]));
+  cplx* X = P<cplx>(ctx->ws_X);
+  cplx* B = P<cplx>(ctx->ws_B);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lr = pass == 0;
+    for (int k = 0; k < N - 1; ++k) {
+      const int i = lr ? k : N - 2 - k;
+      const int chl = x->chi[i], chr = x->chi[i + 2];
+      const int bl = b->chi[i], bm = b->chi[i + 1], br = b->chi[i + 2];
+      if (!fit) {
+        CS(merge(ctx, d, chl, x->chi[i + 1], chr, x->site[i], x->site[i + 1], X));
+        CS(project(ctx, d, chl, bl, bm, br, chr, e.LO[i], b->site[i], b->site[i + 1], e.RO[i + 2], B));
+        int steps = 0;
+        double res = 0.0;
+        CS(local_solve(ctx, H, i, chl, chr, e.LE[i], e.RE[i + 2], B, X, alpha, cbeta, o.krylov_dim,
+                       o.local_tol, &steps, &res));
+        stats.steps += steps;
+        stats.max_res = std::max(stats.max_res, res);
+      } else {
+        // X = alpha * P b + beta * H_eff^{mixed} (b_i b_{i+1})
+        CS(project(ctx, d, chl, bl, bm, br, chr, e.LO[i], b->site[i], b->site[i + 1], e.RO[i + 2], B));
+        cplx* theta = P<cplx>(ctx->ws_X2);
+        CS(merge(ctx, d, bl, bm, br, b->site[i], b->site[i + 1], theta));
+        CS(heff(ctx, H, i, chl, bl, br, chr, e.LE[i], e.RE[i + 2], theta, X, C(cbeta), B, C(alpha)));
+      }
+      int r = 0;
+      double disc = 0.0;
+      CS(split(ctx, X, chl * d, d * chr, chi_max, cutoff, lr, x->site[i], x->site[i + 1], &r, &disc));
+      x->chi[i + 1] = r;
+      stats.max_disc = std::max(stats.max_disc, disc);
+      if (lr) {
+        CS(env_left(ctx, H, i, x->chi[i], kop->chi[i], x->chi[i + 1], kop->chi[i + 1], e.LE[i],
+                    x->site[i], kop->site[i], e.LE[i + 1]));
+        CS(ov_left(ctx, d, x->chi[i], b->chi[i], x->chi[i + 1], b->chi[i + 1], e.LO[i], x->site[i],
+                   b->site[i], e.LO[i + 1]));
+      } else {
+        CS(env_right(ctx, H, i + 1, x->chi[i + 1], kop->chi[i + 1], x->chi[i + 2], kop->chi[i + 2],
+                     e.RE[i + 2], x->site[i + 1], kop->site[i + 1], e.RE[i + 1]));
+        CS(ov_right(ctx, d, x->chi[i + 1], b->chi[i + 1], x->chi[i + 2], b->chi[i + 2], e.RO[i + 2],
+                    x->site[i + 1], b->site[i + 1], e.RO[i + 1]));
+      }
+    }
+  }
+  return ITE_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void ite_solver_opts_default(ite_solver_opts* o) {
+  if (!o) return;
+  o->krylov_dim = 10;
+  o->sweeps = 1;
+  o->local_tol = 0.0;
+  o->sweep_tol = 0.0;
+  o->fit_sweeps = 1;
+  o->precision = ITE_FP64;
+}
+
+ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free_fn release,
+                          void* alloc_user, ite_ctx* out) {
+  if (!out) return ITE_EINVAL;
+  *out = nullptr;
+  if ((alloc == nullptr) != (release == nullptr)) return ITE_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return ITE_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return ITE_ECUDA;
+  ite_ctx ctx = new ite_ctx_s();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->alloc = alloc;
+  ctx->release = release;
+  ctx->user = alloc_user;
+  ctx->gm = (GmresState*)dev_alloc(ctx, sizeof(GmresState));
+  ctx->dscal = (double*)dev_alloc(ctx, 64 * sizeof(double) + kPartialSlots * sizeof(double));
+  ctx->dcplx = (cplx*)dev_alloc(ctx, 512 * sizeof(cplx));
+  ctx->partial = (cplx*)dev_alloc(ctx, (size_t)kPartialSlots * sizeof(cplx));
+  ctx->dcounter = (int*)dev_alloc(ctx, 16 * sizeof(int));
+  if (cudaMallocHost((void**)&ctx->hr, sizeof(HostRead)) != cudaSuccess) ctx->hr = nullptr;
+  if (!ctx->gm || !ctx->dscal || !ctx->dcplx || !ctx->partial || !ctx->dcounter || !ctx->hr) {
+    ite_ctx_destroy(ctx);
+    return ITE_ENOMEM;
+  }
+  *out = ctx;
+  return ITE_OK;
+}
+
+ite_status ite_ctx_set_stream(ite_ctx ctx, void* stream) {
+  if (!ctx) return ITE_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return ITE_OK;
+}
+
+void ite_ctx_destroy(ite_ctx ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
+                 &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env};
+  for (Buf* b : bufs) buf_free(ctx, *b);
+  dev_free(ctx, ctx->gm, sizeof(GmresState));
+  dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
+  dev_free(ctx, ctx->dcplx, 512 * sizeof(cplx));
+  dev_free(ctx, ctx->partial, (size_t)kPartialSlots * sizeof(cplx));
+  dev_free(ctx, ctx->dcounter, 16 * sizeof(int));
+  if (ctx->hr) cudaFreeHost(ctx->hr);
+  delete ctx;
+}
+
+const char* ite_last_error(ite_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t ite_ctx_device_bytes(ite_ctx ctx) { return ctx ? ctx->bytes : 0; }
+
+}  // extern "C"
+
+// ================================================================== step, measurements
+namespace {
+
+ite_status validate_pair(ite_ctx ctx, ite_mpo H, ite_mps psi) {
+  if (!ctx || !H || !psi) return ITE_EINVAL;
+  if (H->N != psi->N || H->d != psi->d) return fail(ctx, ITE_EINVAL, "MPO and MPS do not match");
+  return ITE_OK;
+}
+
+ite_status read_cplx(ite_ctx ctx, const cplx* dev, cplx* host) {
+  CK(cudaMemcpyAsync(&ctx->hr->z[0], dev, sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  *host = ctx->hr->z[0];
+  return ITE_OK;
+}
+
+std::vector<int> max_caps(ite_mps a, ite_mps b) {
+  std::vector<int> c(a->cap);
+  for (size_t k = 0; k < c.size(); ++k) c[k] = std::max(c[k], b->cap[k]);
+  return c;
+}
+
+// <bra|ket> through the overlap-environment chain; optional one-site operators
+// on the ket sites (ops[i] device d x d or nullptr)
+ite_status overlap_impl(ite_ctx ctx, ite_mps bra, ite_mps ket, const std::vector<const cplx*>* ops,
+                        cplx* out) {
+  const int N = bra->N, d = bra->d;
+  std::vector<int> cap = max_caps(bra, ket);
+  // workspace: envs of cap^2, T1 of cap*d*cap, a temp site
+  long long site_max = 1, ovs = 0;
+  for (int i = 0; i < N; ++i) site_max = std::max(site_max, (long long)cap[i] * d * cap[i + 1]);
+  for (int b = 0; b <= N; ++b) ovs += (long long)cap[b] * cap[b];
+  CS(buf_ensure(ctx, ctx->ws_T1, site_max * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_X2, site_max * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_B, (size_t)(2 * ovs + 4) * sizeof(cplx)));
+  cplx* envp = P<cplx>(ctx->ws_B);
+  std::vector<cplx*> LO(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    LO[b] = envp;
+    envp += (long long)cap[b] * cap[b];
+  }
+  CS(set_one(ctx, LO[0]));
+  for (int i = 0; i < N; ++i) {
+    const cplx* k = ket->site[i];
+    if (ops && (*ops)[i]) {
+      CK(apply_site_op((*ops)[i], k, P<cplx>(ctx->ws_X2), ket->chi[i], d, ket->chi[i + 1], ctx->stream));
+      k = P<cplx>(ctx->ws_X2);
+    }
+    CS(ov_left(ctx, d, bra->chi[i], ket->chi[i], bra->chi[i + 1], ket->chi[i + 1], LO[i],
+               bra->site[i], k, LO[i + 1]));
+  }
+  return read_cplx(ctx, LO[N], out);
+}
+
+ite_status energy_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double* E) {
+  const int N = psi->N;
+  CS(ensure_workspace(ctx, H, psi->cap, psi->d, 1));
+  EnvSet e = carve_envs(ctx, H, psi->cap);
+  CS(set_one(ctx, e.LE[0]));
+  for (int i = 0; i < N; ++i)
+    CS(env_left(ctx, H, i, psi->chi[i], psi->chi[i], psi->chi[i + 1], psi->chi[i + 1], e.LE[i],
+                psi->site[i], psi->site[i], e.LE[i + 1]));
+  cplx num;
+  CS(read_cplx(ctx, e.LE[N], &num));
+  cplx den;
+  CS(overlap_impl(ctx, psi, psi, nullptr, &den));
+  if (!(den.x > 0.0)) return fail(ctx, ITE_ESINGULAR, "zero-norm state");
+  *E = num.x / den.x;
+  if (!std::isfinite(*E)) return fail(ctx, ITE_ESINGULAR, "non-finite energy");
+  return ITE_OK;
+}
+
+ite_status normalize_impl(ite_ctx ctx, ite_mps psi) {
+  cplx nn;
+  CS(overlap_impl(ctx, psi, psi, nullptr, &nn));
+  if (!(nn.x > 0.0) || !std::isfinite(nn.x)) return fail(ctx, ITE_ESINGULAR, "zero or non-finite norm");
+  CK(vec_axpby(psi->site[0], psi->site[0], C(0), C(1.0 / std::sqrt(nn.x)),
+               (long long)psi->chi[0] * psi->d * psi->chi[1], ctx->stream));
+  return ITE_OK;
+}
+
+ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int scheme, double shift,
+                     int chi_max, double cutoff, const ite_solver_opts& o, ite_step_info* info) {
+  CS(validate_pair(ctx, H, psi));
+  if (!(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(shift) || !(cutoff >= 0.0) ||
+      chi_max < 1 || chi_max > psi->chi_cap || o.krylov_dim < 1 || o.krylov_dim > kMaxKrylov ||
+      o.sweeps < 1 || o.fit_sweeps < 1 || (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID) ||
+      o.precision != ITE_FP64 || psi->N < 2)
+    return fail(ctx, ITE_EINVAL, "invalid step arguments");
+  CS(ensure_work(ctx, psi));
+  CS(ensure_workspace(ctx, H, psi->cap, psi->d, o.krylov_dim));
+  SweepStats st;
+  ite_mps x = psi->work_x, bm = psi;
+  double c;
+  if (scheme == ITE_BACKWARD_EULER) {
+    c = dtau;
+  } else {
+    c = 0.5 * dtau;
+    bm = psi->work_b;
+    CS(mps_copy_into(ctx, psi, bm));
+    CS(right_canonicalize(ctx, bm));
+    for (int f = 0; f < o.fit_sweeps; ++f)
+      CS(sweep(ctx, H, bm, psi, true, 1.0 + c * shift, -c, chi_max, cutoff, o, st));
+  }
+  CS(mps_copy_into(ctx, bm, x));
+  CS(right_canonicalize(ctx, x));
+  if (o.sweep_tol > 0.0 && !psi->work_p) CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &psi->work_p));
+  for (int s = 0; s < o.sweeps; ++s) {
+    const bool check = o.sweep_tol > 0.0 && s > 0;
+    if (check) CS(mps_copy_into(ctx, x, psi->work_p));
+    CS(sweep(ctx, H, x, bm, false, 1.0 - c * shift, c, chi_max, cutoff, o, st));
+    if (check) {
+      cplx ab, aa, bb;
+      CS(overlap_impl(ctx, psi->work_p, x, nullptr, &ab));
+      CS(overlap_impl(ctx, psi->work_p, psi->work_p, nullptr, &aa));
+      CS(overlap_impl(ctx, x, x, nullptr, &bb));
+      const double ov = std::hypot(ab.x, ab.y) / std::sqrt(aa.x * bb.x);
+      if (1.0 - ov < o.sweep_tol) break;
+    }
+  }
+  // normalise the centre tensor (site 0; the rest is right-orthonormal)
+  const long long n0 = (long long)x->chi[0] * x->d * x->chi[1];
+  CK(vec_norm2(x->site[0], n0, ctx->dscal + 2, ctx->dscal + 16, nullptr, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->d[1], ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  const double nrm = std::sqrt(ctx->hr->d[1]);
+  if (!(nrm > 0.0) || !std::isfinite(nrm)) return fail(ctx, ITE_ESINGULAR, "solution has zero or non-finite norm");
+  CK(vec_axpby(x->site[0], x->site[0], C(0), C(1.0 / nrm), n0, ctx->stream));
+  // energy from the centre: L_1 from site 0, then tr(L_1 R_1)
+  EnvSet e = carve_envs(ctx, H, x->cap);
+  CS(set_one(ctx, e.LE[0]));
+  CS(env_left(ctx, H, 0, 1, 1, x->chi[1], x->chi[1], e.LE[0], x->site[0], x->site[0], e.LE[1]));
+  CK(env_trace(e.LE[1], e.RE[1], H->D[1], x->chi[1], x->chi[1], ctx->dcplx, ctx->partial, ctx->stream));
+  cplx E;
+  CS(read_cplx(ctx, ctx->dcplx, &E));
+  if (!std::isfinite(E.x)) return fail(ctx, ITE_ESINGULAR, "non-finite energy");
+  mps_swap(psi, x);
+  if (info) {
+    info->energy = E.x;
+    info->norm_before = nrm;
+    info->max_discarded_weight = st.max_disc;
+    info->max_local_residual = st.max_res;
+    info->shift = shift;
+    info->max_chi = *std::max_element(psi->chi.begin(), psi->chi.end());
+    info->gmres_steps = st.steps;
+    info->status = ITE_OK;
+  }
+  return ITE_OK;
+}
+
+void grid_geometric_impl(double a, double b, int K, double* nodes) {
+  nodes[0] = 0.0;
+  if (K == 1) {
+    nodes[1] = b;
+    return;
+  }
+  for (int k = 1; k <= K; ++k) nodes[k] = a * std::pow(b / a, (double)(k - 1) / (K - 1));
+}
+
+void grid_panels_impl(double tau_max, int Pn, int n, double* nodes) {
+  std::vector<double> ends(Pn + 1);
+  ends[0] = 0.0;
+  for (int j = 1; j <= Pn; ++j) ends[j] = tau_max / std::ldexp(1.0, Pn - j);
+  int k = 0;
+  nodes[k++] = 0.0;
+  for (int p = 0; p < Pn; ++p)
+    for (int i = 1; i <= n; ++i) nodes[k++] = ends[p] + (ends[p + 1] - ends[p]) * i / n;
+}
+
+ite_status evolve_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, const std::vector<double>& nodes,
+                       int scheme, int shift_mode, double shift0, int chi_max, double cutoff,
+                       const ite_solver_opts& o, ite_step_info* per_step) {
+  CS(validate_pair(ctx, H, psi));
+  if (shift_mode != ITE_SHIFT_FIXED && shift_mode != ITE_SHIFT_CURRENT_ENERGY)
+    return fail(ctx, ITE_EINVAL, "invalid shift mode");
+  CS(normalize_impl(ctx, psi));
+  double s = shift0;
+  if (shift_mode == ITE_SHIFT_CURRENT_ENERGY) CS(energy_impl(ctx, H, psi, &s));
+  for (size_t k = 1; k < nodes.size(); ++k) {
+    ite_step_info info;
+    std::memset(&info, 0, sizeof(info));
+    ite_status st = step_impl(ctx, H, psi, nodes[k] - nodes[k - 1], scheme, s, chi_max, cutoff, o, &info);
+    info.status = st;
+    if (per_step) per_step[k - 1] = info;
+    if (st != ITE_OK) return st;
+    if (shift_mode == ITE_SHIFT_CURRENT_ENERGY) s = info.energy;
+  }
+  return ITE_OK;
+}
+
+ite_status upload_ops(ite_ctx ctx, int d, const double* host, int slot, const cplx** dev) {
+  if (!host) {
+    *dev = nullptr;
+    return ITE_OK;
+  }
+  cplx* p = ctx->dcplx + 16 + slot * 64;
+  CK(cudaMemcpyAsync(p, host, sizeof(cplx) * d * d, cudaMemcpyHostToDevice, ctx->stream));
+  *dev = p;
+  return ITE_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI (objects, steps)
+extern "C" {
+
+ite_status ite_mpo_create(ite_ctx ctx, int N, const int* d, const int* D, const double* W,
+                          ite_mpo* out) {
+  if (!ctx || !out || !d || !D || !W || N < 1) return ITE_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < N; ++i)
+    if (d[i] != d[0] || d[i] < 1 || d[i] > 16) return fail(ctx, ITE_EINVAL, "site dimensions must be equal and <= 16");
+  if (D[0] != 1 || D[N] != 1) return fail(ctx, ITE_EINVAL, "MPO boundary bond dimensions must be 1");
+  for (int b = 0; b <= N; ++b)
+    if (D[b] < 1 || D[b] > 32) return fail(ctx, ITE_EINVAL, "MPO bond dimension out of range");
+  ite_mpo H = new ite_mpo_s();
+  H->ctx = ctx;
+  H->N = N;
+  H->d = d[0];
+  H->D.assign(D, D + N + 1);
+  for (int i = 0; i < N; ++i)
+    if ((long long)H->D[i] * H->d * H->d > 128 || (long long)H->D[i + 1] * H->d * H->d > 128) {
+      delete H;
+      return fail(ctx, ITE_EINVAL, "D*d^2 above 128 is not supported");
+    }
+  const double* p = W;
+  H->Wh.resize(N);
+  for (int i = 0; i < N; ++i) {
+    const size_t cnt = (size_t)H->D[i] * H->d * H->d * H->D[i + 1];
+    H->Wh[i].resize(cnt);
+    for (size_t k = 0; k < cnt; ++k) H->Wh[i][k] = cmake(p[2 * k], p[2 * k + 1]);
+    p += 2 * cnt;
+  }
+  ite_status st = mpo_finish(H);
+  if (st != ITE_OK) {
+    ite_mpo_destroy(H);
+    return st;
+  }
+  *out = H;
+  return ITE_OK;
+}
+
+// Heisenberg chain as a finite-state machine: channel 0 = nothing placed,
+// 1/2/3 = S+ / S- / Sz placed on the previous site, 4 = term complete.
+ite_status ite_mpo_create_heisenberg(ite_ctx ctx, int N, double J, double Jz, ite_mpo* out) {
+  if (!ctx || !out || N < 2) return ITE_EINVAL;
+  const int d = 2, Db = 5;
+  // local operators [s'][s], index 0 = up
+  const double Id[2][2] = {{1, 0}, {0, 1}};
+  const double Sp[2][2] = {{0, 1}, {0, 0}};
+  const double Sm[2][2] = {{0, 0}, {1, 0}};
+  const double Sz[2][2] = {{0.5, 0}, {0, -0.5}};
+  std::vector<double> bulk((size_t)Db * d * d * Db * 2, 0.0);
+  auto put = [&](int w, int w2, const double (*op)[2], double f) {
+    for (int sp = 0; sp < 2; ++sp)
+      for (int s = 0; s < 2; ++s) bulk[((((size_t)w * d + sp) * d + s) * Db + w2) * 2] += f * op[sp][s];
+  };
+  put(0, 0, Id, 1.0);
+  put(0, 1, Sp, 1.0);
+  put(0, 2, Sm, 1.0);
+  put(0, 3, Sz, 1.0);
+  put(1, 4, Sm, 0.5 * J);
+  put(2, 4, Sp, 0.5 * J);
+  put(3, 4, Sz, Jz);
+  put(4, 4, Id, 1.0);
+  std::vector<int> dv(N, d), Dv(N + 1, Db);
+  Dv[0] = Dv[N] = 1;
+  std::vector<double> W;
+  for (int i = 0; i < N; ++i) {
+    const int w0 = (i == 0) ? 0 : 0, wn = (i == 0) ? 1 : Db;
+    const int v0 = (i == N - 1) ? Db - 1 : 0, vn = (i == N - 1) ? Db : Db;
+    for (int w = w0; w < wn; ++w)
+      for (int sp = 0; sp < d; ++sp)
+        for (int s = 0; s < d; ++s)
+          for (int w2 = v0; w2 < vn; ++w2) {
+            const size_t k = (((size_t)w * d + sp) * d + s) * Db + w2;
+            W.push_back(bulk[2 * k]);
+            W.push_back(bulk[2 * k + 1]);
+          }
+  }
+  return ite_mpo_create(ctx, N, dv.data(), Dv.data(), W.data(), out);
+}
+
+// Anderson impurity, star geometry.  Local basis index n_up + 2 n_down.
+// Channels: 0 start, 1 d^dag_up F, 2 d^dag_down F, 3 F d_up, 4 F d_down, 5 done.
+ite_status ite_mpo_create_anderson(ite_ctx ctx, int n_bath, const double* eps, const double* V,
+                                   double U, double eps_d, ite_mpo* out) {
+  if (!ctx || !out || n_bath < 1 || !eps || !V) return ITE_EINVAL;
+  const int d = 4, Db = 6, N = n_bath + 1;
+  typedef std::vector<double> M4;  // 4x4 real, [s'][s]
+  auto zero = []() { return M4(16, 0.0); };
+  M4 I = zero(), F = zero(), cu = zero(), cd = zero(), nu = zero(), nd = zero();
+  for (int k = 0; k < 4; ++k) I[k * 4 + k] = 1.0;
+  F[0] = 1; F[5] = -1; F[10] = -1; F[15] = 1;
+  cu[0 * 4 + 1] = 1.0; cu[2 * 4 + 3] = 1.0;      // c_up |up> = |0>, c_up |ud> = |dn>
+  cd[0 * 4 + 2] = 1.0; cd[1 * 4 + 3] = -1.0;     // c_dn |dn> = |0>, c_dn |ud> = -|up>
+  nu[5] = 1; nu[15] = 1;
+  nd[10] = 1; nd[15] = 1;
+  auto mul = [](const M4& a, const M4& b) {
+    M4 r(16, 0.0);
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 4; ++k) r[i * 4 + j] += a[i * 4 + k] * b[k * 4 + j];
+    return r;
+  };
+  auto tr = [](const M4& a) {
+    M4 r(16, 0.0);
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) r[i * 4 + j] = a[j * 4 + i];
+    return r;
+  };
+  std::vector<int> dv(N, d), Dv(N + 1, Db);
+  Dv[0] = Dv[N] = 1;
+  std::vector<double> W;
+  for (int i = 0; i < N; ++i) {
+    std::vector<double> bulk((size_t)Db * 16 * Db, 0.0);
+    auto put = [&](int w, int w2, const M4& op, double f) {
+      for (int sp = 0; sp < 4; ++sp)
+        for (int s = 0; s < 4; ++s) bulk[(((size_t)w * 4 + sp) * 4 + s) * Db + w2] += f * op[sp * 4 + s];
+    };
+    if (i == 0) {
+      put(0, 0, I, 1.0);
+      put(0, 1, mul(tr(cu), F), 1.0);
+      put(0, 2, mul(tr(cd), F), 1.0);
+      put(0, 3, mul(F, cu), 1.0);
+      put(0, 4, mul(F, cd), 1.0);
+      M4 onsite = zero();
+      for (int k = 0; k < 16; ++k) onsite[k] = eps_d * (nu[k] + nd[k]);
+      M4 nn = mul(nu, nd);
+      for (int k = 0; k < 16; ++k) onsite[k] += U * nn[k];
+      put(0, 5, onsite, 1.0);
+    } else {
+      const double e = eps[i - 1], v = V[i - 1];
+      put(0, 0, I, 1.0);
+      M4 n = zero();
+      for (int k = 0; k < 16; ++k) n[k] = nu[k] + nd[k];
+      put(0, 5, n, e);
+      for (int ch = 1; ch <= 4; ++ch) put(ch, ch, F, 1.0);
+      put(1, 5, cu, v);
+      put(2, 5, cd, v);
+      put(3, 5, tr(cu), v);
+      put(4, 5, tr(cd), v);
+      put(5, 5, I, 1.0);
+    }
+    const int w0 = 0, wn = (i == 0) ? 1 : Db;
+    const int v0 = (i == N - 1) ? Db - 1 : 0, vn = Db;
+    for (int w = w0; w < wn; ++w)
+      for (int sp = 0; sp < d; ++sp)
+        for (int s = 0; s < d; ++s)
+          for (int w2 = v0; w2 < vn; ++w2) {
+            W.push_back(bulk[(((size_t)w * d + sp) * d + s) * Db + w2]);
+            W.push_back(0.0);
+          }
+  }
+  return ite_mpo_create(ctx, N, dv.data(), Dv.data(), W.data(), out);
+}
+
+int ite_mpo_length(ite_mpo H) { return H ? H->N : 0; }
+
+void ite_mpo_destroy(ite_mpo H) {
+  if (!H) return;
+  buf_free(H->ctx, H->Wdev);
+  buf_free(H->ctx, H->plan_mem);
+  delete H;
+}
+
+ite_status ite_mps_create(ite_ctx ctx, int N, int d, const int* chi, const double* A, int chi_cap,
+                          ite_mps* out) {
+  if (!ctx || !out || N < 1 || d < 1 || d > 16 || chi_cap < 1 || !chi || !A) return ITE_EINVAL;
+  *out = nullptr;
+  ite_mps m = nullptr;
+  CS(mps_alloc(ctx, N, d, chi_cap, &m));
+  ite_status st = ite_mps_set(ctx, m, chi, A);
+  if (st != ITE_OK) {
+    mps_free(m);
+    return st;
+  }
+  *out = m;
+  return ITE_OK;
+}
+
+ite_status ite_mps_create_product(ite_ctx ctx, int N, int d, const double* site_vecs, int chi_cap,
+                                  ite_mps* out) {
+  if (!site_vecs) return ITE_EINVAL;
+  std::vector<int> chi(N + 1, 1);
+  return ite_mps_create(ctx, N, d, chi.data(), site_vecs, chi_cap, out);
+}
+
+ite_status ite_mps_set(ite_ctx ctx, ite_mps m, const int* chi, const double* A) {
+  if (!ctx || !m || !chi || !A) return ITE_EINVAL;
+  if (chi[0] != 1 || chi[m->N] != 1) return fail(ctx, ITE_EINVAL, "boundary bond dimensions must be 1");
+  for (int b = 0; b <= m->N; ++b)
+    if (chi[b] < 1 || chi[b] > m->cap[b]) return fail(ctx, ITE_EINVAL, "bond dimension above capacity");
+  const double* p = A;
+  for (int i = 0; i < m->N; ++i) {
+    const size_t cnt = (size_t)chi[i] * m->d * chi[i + 1];
+    CK(cudaMemcpyAsync(m->site[i], p, cnt * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
+    p += 2 * cnt;
+  }
+  m->chi.assign(chi, chi + m->N + 1);
+  return sync(ctx);
+}
+
+ite_status ite_mps_copy(ite_ctx ctx, ite_mps src, ite_mps dst) {
+  if (!ctx || !src || !dst || src->N != dst->N || src->d != dst->d) return ITE_EINVAL;
+  for (int b = 0; b <= src->N; ++b)
+    if (src->chi[b] > dst->cap[b]) return fail(ctx, ITE_EINVAL, "destination capacity too small");
+  CS(mps_copy_into(ctx, src, dst));
+  return sync(ctx);
+}
+
+ite_status ite_mps_bond_dims(ite_mps m, int* chi, size_t* n_doubles) {
+  if (!m) return ITE_EINVAL;
+  size_t tot = 0;
+  for (int i = 0; i < m->N; ++i) tot += (size_t)m->chi[i] * m->d * m->chi[i + 1];
+  if (chi) std::copy(m->chi.begin(), m->chi.end(), chi);
+  if (n_doubles) *n_doubles = 2 * tot;
+  return ITE_OK;
+}
+
+ite_status ite_mps_get(ite_ctx ctx, ite_mps m, double* A, size_t cap_doubles) {
+  if (!ctx || !m || !A) return ITE_EINVAL;
+  size_t need = 0;
+  ite_mps_bond_dims(m, nullptr, &need);
+  if (cap_doubles < need) return fail(ctx, ITE_EINVAL, "output buffer too small");
+  double* p = A;
+  for (int i = 0; i < m->N; ++i) {
+    const size_t cnt = (size_t)m->chi[i] * m->d * m->chi[i + 1];
+    CK(cudaMemcpyAsync(p, m->site[i], cnt * sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream));
+    p += 2 * cnt;
+  }
+  return sync(ctx);
+}
+
+void ite_mps_destroy(ite_mps m) { mps_free(m); }
+
+ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int scheme,
+                             double shift, int chi_max, double cutoff, const ite_solver_opts* opts,
+                             ite_step_info* info) {
+  ite_solver_opts o;
+  ite_solver_opts_default(&o);
+  if (opts) o = *opts;
+  return step_impl(ctx, H, psi, dtau, scheme, shift, chi_max, cutoff, o, info);
+}
+
+ite_status ite_grid_geometric(double tau0, double tau_max, int n_steps, double* nodes) {
+  if (!nodes || n_steps < 1 || !(tau0 > 0.0) || !(tau_max >= tau0)) return ITE_EINVAL;
+  grid_geometric_impl(tau0, tau_max, n_steps, nodes);
+  return ITE_OK;
+}
+
+ite_status ite_grid_panels(double tau_max, int Pn, int n, double* nodes) {
+  if (!nodes || Pn < 1 || n < 1 || !(tau_max > 0.0) || Pn > 1000) return ITE_EINVAL;
+  grid_panels_impl(tau_max, Pn, n, nodes);
+  return ITE_OK;
+}
+
+ite_status ite_evolve_loggrid(ite_ctx ctx, ite_mpo H, ite_mps psi, double tau0, double tau_max,
+                              int n_steps, int scheme, int shift_mode, double shift0, int chi_max,
+                              double cutoff, const ite_solver_opts* opts, ite_step_info* per_step,
+                              double* nodes_out) {
+  std::vector<double> nodes(std::max(n_steps, 1) + 1);
+  if (ite_grid_geometric(tau0, tau_max, n_steps, nodes.data()) != ITE_OK)
+    return fail(ctx, ITE_EINVAL, "invalid grid");
+  if (nodes_out) std::copy(nodes.begin(), nodes.end(), nodes_out);
+  ite_solver_opts o;
+  ite_solver_opts_default(&o);
+  if (opts) o = *opts;
+  return evolve_impl(ctx, H, psi, nodes, scheme, shift_mode, shift0, chi_max, cutoff, o, per_step);
+}
+
+ite_status ite_evolve_panels(ite_ctx ctx, ite_mpo H, ite_mps psi, double tau_max, int Pn, int n,
+                             int scheme, int shift_mode, double shift0, int chi_max, double cutoff,
+                             const ite_solver_opts* opts, ite_step_info* per_step, double* nodes_out) {
+  if (Pn < 1 || n < 1 || Pn > 1000) return fail(ctx, ITE_EINVAL, "invalid grid");
+  std::vector<double> nodes((size_t)Pn * n + 1);
+  if (ite_grid_panels(tau_max, Pn, n, nodes.data()) != ITE_OK) return fail(ctx, ITE_EINVAL, "invalid grid");
+  if (nodes_out) std::copy(nodes.begin(), nodes.end(), nodes_out);
+  ite_solver_opts o;
+  ite_solver_opts_default(&o);
+  if (opts) o = *opts;
+  return evolve_impl(ctx, H, psi, nodes, scheme, shift_mode, shift0, chi_max, cutoff, o, per_step);
+}
+
+ite_status ite_energy(ite_ctx ctx, ite_mpo H, ite_mps psi, double* E) {
+  CS(validate_pair(ctx, H, psi));
+  if (!E) return ITE_EINVAL;
+  return energy_impl(ctx, H, psi, E);
+}
+
+ite_status ite_overlap(ite_ctx ctx, ite_mps bra, ite_mps ket, double out[2]) {
+  if (!ctx || !bra || !ket || !out) return ITE_EINVAL;
+  if (bra->N != ket->N || bra->d != ket->d) return fail(ctx, ITE_EINVAL, "MPS shapes differ");
+  cplx z;
+  CS(overlap_impl(ctx, bra, ket, nullptr, &z));
+  out[0] = z.x;
+  out[1] = z.y;
+  return ITE_OK;
+}
+
+ite_status ite_correlator(ite_ctx ctx, ite_mps psi, const double* O, int i, const double* Pm,
+                          int j, const double* string_op, double out[2]) {
+  if (!ctx || !psi || !O || !Pm || !out || i < 0 || j >= psi->N || i > j) return ITE_EINVAL;
+  const int d = psi->d;
+  std::vector<const cplx*> ops(psi->N, nullptr);
+  const cplx *o, *p, *s;
+  CS(upload_ops(ctx, d, O, 0, &o));
+  CS(upload_ops(ctx, d, Pm, 1, &p));
+  CS(upload_ops(ctx, d, string_op, 2, &s));
+  if (i == j) {
+    // O P on one site: form the product on the host
+    std::vector<double> op(2 * d * d, 0.0);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b)
+        for (int k = 0; k < d; ++k) {
+          const double ar = O[2 * (a * d + k)], ai = O[2 * (a * d + k) + 1];
+          const double br = Pm[2 * (k * d + b)], bi = Pm[2 * (k * d + b) + 1];
+          op[2 * (a * d + b)] += ar * br - ai * bi;
+          op[2 * (a * d + b) + 1] += ar * bi + ai * br;
+        }
+    CS(upload_ops(ctx, d, op.data(), 3, &o));
+    CS(sync(ctx));
+    ops[i] = o;
+  } else {
+    ops[i] = o;
+    ops[j] = p;
+    if (s)
+      for (int k = i + 1; k < j; ++k) ops[k] = s;
+  }
+  cplx num, den;
+  CS(overlap_impl(ctx, psi, psi, &ops, &num));
+  CS(overlap_impl(ctx, psi, psi, nullptr, &den));
+  if (!(den.x > 0.0)) return fail(ctx, ITE_ESINGULAR, "zero-norm state");
+  out[0] = num.x / den.x;
+  out[1] = num.y / den.x;
+  return ITE_OK;
+}
+
+// ------------------------------------------------------------------ kernel-level entry points
+ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_ket,
+                      int chr_bra, const double* L, const double* R, const double* X, double* Y,
+                      const double alpha[2], const double* Z, const double gamma[2]) {
+  if (!ctx || !H || !L || !R || !X || !Y || !alpha || i < 0 || i + 1 >= H->N || chl_bra < 1 ||
+      chl_ket < 1 || chr_ket < 1 || chr_bra < 1)
+    return ITE_EINVAL;
+  const long long d2 = (long long)H->d * H->d;
+  const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * d2 * std::max(chr_ket, chr_bra);
+  CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_T2, t * sizeof(cplx)));
+  const cplx g = gamma ? C(gamma[0], gamma[1]) : C(0);
+  CS(heff(ctx, H, i, chl_bra, chl_ket, chr_ket, chr_bra, (const cplx*)L, (const cplx*)R,
+          (const cplx*)X, (cplx*)Y, C(alpha[0], alpha[1]), (const cplx*)Z, g));
+  return sync(ctx);
+}
+
+ite_status ite_k_env_left(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
+                          int chr_ket, const double* Lin, const double* bra, const double* ket,
+                          double* Lout) {
+  if (!ctx || !H || !Lin || !bra || !ket || !Lout || i < 0 || i >= H->N || chl_bra < 1 ||
+      chl_ket < 1 || chr_bra < 1 || chr_ket < 1)
+    return ITE_EINVAL;
+  const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * H->d * std::max(chr_bra, chr_ket);
+  CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_T2, t * sizeof(cplx)));
+  CS(env_left(ctx, H, i, chl_bra, chl_ket, chr_bra, chr_ket, (const cplx*)Lin, (const cplx*)bra,
+              (const cplx*)ket, (cplx*)Lout));
+  return sync(ctx);
+}
+
+ite_status ite_k_env_right(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
+                           int chr_ket, const double* Rin, const double* bra, const double* ket,
+                           double* Rout) {
+  if (!ctx || !H || !Rin || !bra || !ket || !Rout || i < 0 || i >= H->N || chl_bra < 1 ||
+      chl_ket < 1 || chr_bra < 1 || chr_ket < 1)
+    return ITE_EINVAL;
+  const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * H->d * std::max(chr_bra, chr_ket);
+  CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_T2, t * sizeof(cplx)));
+  CS(env_right(ctx, H, i, chl_bra, chl_ket, chr_bra, chr_ket, (const cplx*)Rin, (const cplx*)bra,
+               (const cplx*)ket, (cplx*)Rout));
+  return sync(ctx);
+}
+
+ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const double* L,
+                             const double* R, const double* B, double* X, double alpha, double c,
+                             int krylov_dim, double local_tol, int* steps, double* rel_res) {
+  if (!ctx || !H || !L || !R || !B || !X || i < 0 || i + 1 >= H->N || chl < 1 || chr < 1 ||
+      krylov_dim < 1 || krylov_dim > kMaxKrylov)
+    return ITE_EINVAL;
+  const long long n = (long long)chl * H->d * H->d * chr;
+  CS(buf_ensure(ctx, ctx->ws_V, (size_t)(krylov_dim + 1) * n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_T1, (size_t)H->Dmax * n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_T2, (size_t)H->Dmax * n * sizeof(cplx)));
+  int s = 0;
+  double r = 0.0;
+  CS(local_solve(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B, (cplx*)X,
+                 alpha, c, krylov_dim, local_tol, &s, &r));
+  if (steps) *steps = s;
+  if (rel_res) *rel_res = r;
+  return ITE_OK;
+}
+
+ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
+                       int centre_right, double* left, double* right, double* sigma, int* rank,
+                       double* discarded) {
+  if (!ctx || !X || !left || !right || m < 1 || n < 1 || chi_max < 1 || !(cutoff >= 0.0))
+    return ITE_EINVAL;
+  const long long p = std::min(m, n);
+  CS(buf_ensure(ctx, ctx->ws_svdA, (size_t)m * n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)p * p * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_small, (size_t)p * 3 * sizeof(double) + 64));
+  int r = 0;
+  double disc = 0.0;
+  CS(split(ctx, (const cplx*)X, m, n, chi_max, cutoff, centre_right != 0, (cplx*)left, (cplx*)right,
+           &r, &disc, sigma));
+  CS(sync(ctx));
+  if (rank) *rank = r;
+  if (discarded) *discarded = disc;
+  return ITE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,296 @@
+// FP64 truncated SVD of the two-site blocks and the gauge moves: parallel
+// one-sided (Hestenes) Jacobi on the rows of a p x q complex matrix.
+//
+// Each launch performs one round of a round-robin tournament: the p rows form
+// p/2 disjoint pairs, one CTA per pair.  The CTA forms alpha = |a_u|^2,
+// beta = |a_v|^2 and gamma = a_u^H a_v, and if |gamma| > tol sqrt(alpha beta)
+// applies the complex Jacobi rotation that makes the pair orthogonal to both
+// the pair of rows and to the matching rows of the accumulated unitary Q.  A
+// sweep is p-1 rounds; sweeps repeat until no rotation fires.  On exit
+// Q A_in = A_out, the rows of A_out are orthogonal with norms sigma_i, so
+// A_in = Q^H diag(sigma) V^H with V^H the normalised rows.
+#include "common.cuh"
+
+namespace ite {
+namespace {
+
+constexpr int JT = 128;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int player(int pos, int round, int pp) {
+  return pos == 0 ? 0 : ((pos - 1 + round) % (pp - 1)) + 1;
+}
+
+__global__ void __launch_bounds__(JT)
+k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, int* counter) {
+  const int k = blockIdx.x;
+  int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
+  if (u >= p || v >= p) return;
+  if (u > v) { const int t = u; u = v; v = t; }
+  cplx* au = A + (long long)u * q;
+  cplx* av = A + (long long)v * q;
+  double sa = 0.0, sb = 0.0, gr = 0.0, gi = 0.0;
+  for (int e = threadIdx.x; e < q; e += JT) {
+    const cplx x = au[e], y = av[e];
+    sa = fma(x.x, x.x, fma(x.y, x.y, sa));
+    sb = fma(y.x, y.x, fma(y.y, y.y, sb));
+    gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // Re(conj(x) y)
+    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));    // Im(conj(x) y)
+  }
+  __shared__ double sh[4][JT / 32];
+  __shared__ double rot[4];
+  sa = warp_sum(sa); sb = warp_sum(sb); gr = warp_sum(gr); gi = warp_sum(gi);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][wid] = sa; sh[1][wid] = sb; sh[2][wid] = gr; sh[3][wid] = gi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double al = 0, be = 0, Gr = 0, Gi = 0;
+    for (int w = 0; w < JT / 32; ++w) { al += sh[0][w]; be += sh[1][w]; Gr += sh[2][w]; Gi += sh[3][w]; }
+    const double gabs = hypot(Gr, Gi);
+    double c = 1.0, sr = 0.0, si = 0.0;   // rotation: c, and s*e^{i theta}
+    if (gabs > tol * sqrt(al * be) && gabs > 0.0) {
+      const double zeta = (be - al) / (2.0 * gabs);
+      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      c = 1.0 / sqrt(1.0 + t * t);
+      const double s = c * t;
+      sr = s * Gr / gabs;
+      si = s * Gi / gabs;
+      atomicAdd(counter, 1);
+    }
+    rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != 0.0 || si != 0.0) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (rot[3] == 0.0) return;
+  const double c = rot[0];
+  const cplx se = cmake(rot[1], rot[2]);      // s e^{i theta}
+  const cplx sec = cconj(se);                  // s e^{-i theta}
+  // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
+  for (int e = threadIdx.x; e < q; e += JT) {
+    const cplx x = au[e], y = av[e];
+    au[e] = csub(cscale(x, c), cmul(sec, y));
+    av[e] = cadd(cmul(se, x), cscale(y, c));
+  }
+  cplx* qu = Q + (long long)u * p;
+  cplx* qv = Q + (long long)v * p;
+  for (int e = threadIdx.x; e < p; e += JT) {
+    const cplx x = qu[e], y = qv[e];
+    qu[e] = csub(cscale(x, c), cmul(sec, y));
+    qv[e] = cadd(cmul(se, x), cscale(y, c));
+  }
+}
+
+__global__ void k_identity(cplx* Q, int p) {
+  const long long tot = (long long)p * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / p, j = e - i * p;
+    Q[e] = cmake(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+__global__ void k_row_norms(const cplx* A, int p, int q, double* sigma) {
+  const int i = blockIdx.x;
+  const cplx* a = A + (long long)i * q;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < q; e += JT) s = fma(a[e].x, a[e].x, fma(a[e].y, a[e].y, s));
+  __shared__ double sh[JT / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < JT / 32; ++w) t += sh[w];
+    sigma[i] = sqrt(t);
+  }
+}
+
+// sort descending (ties by index) by counting, then the truncation rule
+__global__ void k_sort_rank(const double* sigma, int p, int* perm, double* sorted, int chi_max,
+                            double cutoff, double floor_w, double tie_rel, int* rank_out,
+                            double* disc_out) {
+  // a non-finite value leaves no valid ordering: report rank -1 and stop
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < p; i += blockDim.x)
+    if (!isfinite(sigma[i])) bad = 1;
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) {
+      *rank_out = -1;
+      *disc_out = 0.0;
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    const double si = sigma[i];
+    int pos = 0;
+    for (int j = 0; j < p; ++j) {
+      const double sj = sigma[j];
+      pos += (sj > si) || (sj == si && j < i);
+    }
+    perm[pos] = i;
+    sorted[pos] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // tail[r] = sum_{k >= r} sigma_k^2, accumulated from the smallest value up
+  double total = 0.0;
+  for (int k = p - 1; k >= 0; --k) total += sorted[k] * sorted[k];
+  int r = p;
+  if (total == 0.0) {
+    *rank_out = 1;
+    *disc_out = 0.0;
+    return;
+  }
+  const double tol = (cutoff > floor_w ? cutoff : floor_w) * total;
+  // find the smallest r >= 1 with tail[r] <= tol: walk up from the end
+  {
+    double tail = 0.0;     // tail[p] = 0
+    int best = p;
+    for (int cand = p; cand >= 1; --cand) {
+      // tail currently = tail[cand]
+      if (tail <= tol) best = cand; else break;
+      tail += sorted[cand - 1] * sorted[cand - 1];
+    }
+    r = best;
+  }
+  if (r > chi_max) r = chi_max;
+  if (r < p && sorted[r] >= sorted[r - 1] * (1.0 - tie_rel)) {
+    int g = r - 1;
+    while (g > 0 && sorted[g] >= sorted[g - 1] * (1.0 - tie_rel)) --g;
+    if (g >= 1) r = g;
+  }
+  double tail = 0.0;
+  for (int k = p - 1; k >= r; --k) tail += sorted[k] * sorted[k];
+  *rank_out = r;
+  *disc_out = tail / total;
+}
+
+// transposed == false: A = M (m x n, m <= n), Q is m x m, u_k = conj(Q row), s_k v_k^H = A row
+// transposed == true : A = M^H (n x m),     Q is n x n, s_k u_k = conj(A row), v_k^H = Q row
+__global__ void k_emit(const cplx* Arot, const cplx* Q, const double* sorted, const int* perm,
+                       int r, int p, int q, bool transposed, bool centre_right, cplx* left,
+                       cplx* right) {
+  // left: (m x r), right: (r x n); m = transposed ? q : p; n = transposed ? p : q
+  const int m = transposed ? q : p, n = transposed ? p : q;
+  const long long totL = (long long)m * r, totR = (long long)r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totL + totR;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < totL) {
+      const long long i = e / r;
+      const int k = (int)(e - i * r);
+      const int src = perm[k];
+      const double s = sorted[k];
+      cplx v;
+      if (!transposed) {
+        v = cconj(Q[(long long)src * p + i]);
+        if (!centre_right) v = cscale(v, s);
+      } else {
+        v = cconj(Arot[(long long)src * q + i]);
+        if (centre_right) v = cscale(v, 1.0 / s);
+      }
+      left[e] = v;
+    } else {
+      const long long f = e - totL;
+      const int k = (int)(f / n);
+      const long long j = f - (long long)k * n;
+      const int src = perm[k];
+      const double s = sorted[k];
+      cplx v;
+      if (!transposed) {
+        v = Arot[(long long)src * q + j];
+        if (!centre_right) v = cscale(v, 1.0 / s);
+      } else {
+        v = Q[(long long)src * p + j];
+        if (centre_right) v = cscale(v, s);
+      }
+      right[f] = v;
+    }
+  }
+}
+
+__global__ void k_conj_transpose(const cplx* A, int m, int n, cplx* out) {
+  __shared__ cplx tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int i = by + y, j = bx + threadIdx.x;
+    if (i < m && j < n) tile[y][threadIdx.x] = A[(long long)i * n + j];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int j = bx + y, i = by + threadIdx.x;
+    if (i < m && j < n) out[(long long)j * m + i] = cconj(tile[threadIdx.x][y]);
+  }
+}
+
+}  // namespace
+
+cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
+  long long tot = (long long)p * p;
+  long long g = (tot + 255) / 256;
+  if (g > 1216) g = 1216;
+  if (g < 1) g = 1;
+  k_identity<<<(int)g, 256, 0, st>>>(Q, p);
+  return cudaGetLastError();
+}
+
+cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
+                        int* sweeps_done, int* host_counter, int* dev_counter,
+                        cudaStream_t st) {
+  cudaError_t err = set_identity(Q, p, st);
+  if (err != cudaSuccess) return err;
+  *sweeps_done = 0;
+  if (p < 2) return cudaSuccess;
+  const int pp = p + (p & 1);
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    err = cudaMemsetAsync(dev_counter, 0, sizeof(int), st);
+    if (err != cudaSuccess) return err;
+    for (int r = 0; r < pp - 1; ++r)
+      k_jacobi_round<<<pp / 2, JT, 0, st>>>(A, p, q, Q, r, pp, tol, dev_counter);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    err = cudaMemcpyAsync(host_counter, dev_counter, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return err;
+    err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return err;
+    *sweeps_done = sw + 1;
+    if (*host_counter == 0) break;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
+                     int chi_max, double cutoff, double weight_floor, double tie_rel,
+                     int* rank_out, double* discarded_out, cudaStream_t st) {
+  if (p <= 0) return cudaErrorInvalidValue;
+  k_row_norms<<<p, JT, 0, st>>>(A, p, q, sigma);
+  k_sort_rank<<<1, 1024, 0, st>>>(sigma, p, perm, sorted_sigma, chi_max, cutoff, weight_floor,
+                                  tie_rel, rank_out, discarded_out);
+  return cudaGetLastError();
+}
+
+cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma,
+                     const int* perm, int r, int p, int q, bool transposed, bool centre_right,
+                     cplx* left, cplx* right, cudaStream_t st) {
+  const long long tot = (long long)r * (p + q);
+  long long g = (tot + 255) / 256;
+  if (g > 1216) g = 1216;
+  if (g < 1) g = 1;
+  k_emit<<<(int)g, 256, 0, st>>>(Arot, Q, sorted_sigma, perm, r, p, q, transposed, centre_right,
+                                  left, right);
+  return cudaGetLastError();
+}
+
+cudaError_t conj_transpose(const cplx* A, int m, int n, cplx* out, cudaStream_t st) {
+  dim3 grid((n + 31) / 32, (m + 31) / 32);
+  k_conj_transpose<<<grid, dim3(32, 8), 0, st>>>(A, m, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ite

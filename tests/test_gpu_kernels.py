@@ -1,0 +1,195 @@
+"""GPU parity of each kernel-level step of the sweep against the oracle, at
+small sizes (element by element, several tiles and ragged tails) and at the
+workload sizes (sampled entries the oracle computes one by one).
+
+Tolerance: all FP64.  A contraction over K terms has rounding error of order
+K * 2^-53 relative to the largest partial sums; with K <= 4e4 that is below
+1e-11, so element-wise checks use 1e-12 (small) / 1e-11 (workload sizes)
+relative to the largest output magnitude."""
+import numpy as np
+import pytest
+
+from oracle import linsolve as ls, mpo as ompo
+from paper_2606_02930_gb300 import inputs
+
+from tests.gpu_util import (L_from_lib, L_to_lib, R_from_lib, R_to_lib, crandn, rel_err,
+                            to_dev, to_host)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_02930_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.ctx_create(0)
+
+
+def _models(n_sites_heis=8, n_bath=5):
+    Wh = ompo.heisenberg_mpo(n_sites_heis)
+    eps, V = inputs.flat_band_bath(n_bath)
+    Wa = ompo.anderson_mpo(-0.15, 0.3, eps, V)
+    return {"heisenberg": Wh, "anderson": Wa}
+
+
+@pytest.mark.parametrize("model", ["heisenberg", "anderson"])
+@pytest.mark.parametrize("dims", [(1, 1, 1, 1), (3, 3, 5, 5), (7, 5, 6, 9), (33, 40, 37, 35)])
+def test_heff_matches_oracle(api, ctx, model, dims):
+    Ws = _models()[model]
+    H = api.mpo_create(ctx, Ws)
+    rng = np.random.default_rng(hash((model, dims)) % 2**32)
+    chlB, chlK, chrK, chrB = dims
+    i = 2
+    D0, D2, d = Ws[i].shape[0], Ws[i + 1].shape[3], Ws[i].shape[1]
+    L = crandn(rng, chlB, D0, chlK)
+    R = crandn(rng, chrB, D2, chrK)
+    X = crandn(rng, chlK, d, d, chrK)
+    Z = crandn(rng, chlB, d, d, chrB)
+    want = 0.7 * ls.heff_apply(L, Ws[i], Ws[i + 1], R, X) + (0.2 - 0.1j) * Z
+    Y = to_dev(np.zeros_like(Z))
+    api.k_heff(ctx, H, i, to_dev(L_to_lib(L)), to_dev(R_to_lib(R)), to_dev(X), Y, alpha=0.7,
+               Z=to_dev(Z), gamma=0.2 - 0.1j)
+    assert rel_err(to_host(Y), want) < 1e-12
+
+
+@pytest.mark.parametrize("model,chi,nsamp", [("heisenberg", 256, 6), ("anderson", 512, 3)])
+def test_heff_workload_size_sampled(api, ctx, model, chi, nsamp):
+    # bulk two-site block of the N=64 chi=256 Heisenberg chain and of the
+    # chi=512 Anderson chain
+    Ws = _models()[model]
+    H = api.mpo_create(ctx, Ws)
+    rng = np.random.default_rng(chi)
+    i = 2
+    D0, D2, d = Ws[i].shape[0], Ws[i + 1].shape[3], Ws[i].shape[1]
+    L = crandn(rng, chi, D0, chi)
+    R = crandn(rng, chi, D2, chi)
+    X = crandn(rng, chi, d, d, chi)
+    Y = to_dev(np.zeros((chi, d, d, chi)))
+    api.k_heff(ctx, H, i, to_dev(L_to_lib(L)), to_dev(R_to_lib(R)), to_dev(X), Y)
+    Yh = to_host(Y)
+    scale = None
+    for k in range(nsamp):
+        a, b = int(rng.integers(chi)), int(rng.integers(chi))
+        want = ls.heff_entry(L, Ws[i], Ws[i + 1], R, X, a, b)
+        scale = np.abs(want).max() if scale is None else max(scale, np.abs(want).max())
+        assert np.abs(Yh[a, :, :, b] - want).max() < 1e-11 * scale
+    assert np.isfinite(Yh).all()
+
+
+@pytest.mark.parametrize("model", ["heisenberg", "anderson"])
+@pytest.mark.parametrize("dims", [(1, 1, 2, 3), (4, 6, 5, 7), (31, 17, 40, 33)])
+def test_env_updates_match_oracle(api, ctx, model, dims):
+    Ws = _models()[model]
+    H = api.mpo_create(ctx, Ws)
+    rng = np.random.default_rng(7 + sum(dims))
+    chlB, chlK, chrB, chrK = dims
+    i = 3
+    W = Ws[i]
+    Dl, d, Dr = W.shape[0], W.shape[1], W.shape[3]
+    bra = crandn(rng, chlB, d, chrB)
+    ket = crandn(rng, chlK, d, chrK)
+    Lin = crandn(rng, chlB, Dl, chlK)
+    want = ls.left_env_update(Lin, bra, W, ket)
+    Lout = to_dev(np.zeros((Dr, chrB, chrK)))
+    api.k_env_left(ctx, H, i, to_dev(L_to_lib(Lin)), to_dev(bra), to_dev(ket), Lout)
+    assert rel_err(L_from_lib(to_host(Lout)), want) < 1e-12
+    Rin = crandn(rng, chrB, Dr, chrK)
+    want = ls.right_env_update(Rin, bra, W, ket)
+    Rout = to_dev(np.zeros((Dl, chlK, chlB)))
+    api.k_env_right(ctx, H, i, to_dev(R_to_lib(Rin)), to_dev(bra), to_dev(ket), Rout)
+    assert rel_err(R_from_lib(to_host(Rout)), want) < 1e-12
+
+
+def _spectrum_matrix(rng, m, n, sv):
+    U, _ = np.linalg.qr(crandn(rng, m, len(sv)))
+    V, _ = np.linalg.qr(crandn(rng, n, len(sv)))
+    return (U * sv[None, :]) @ V.conj().T
+
+
+@pytest.mark.parametrize("m,n,kind", [(1, 7, "rand"), (9, 1, "rand"), (20, 33, "decay"),
+                                      (40, 24, "decay"), (64, 64, "ties"), (30, 50, "lowrank"),
+                                      (512, 512, "decay")])
+def test_split_matches_oracle(api, ctx, m, n, kind):
+    rng = np.random.default_rng(m * 1000 + n)
+    p = min(m, n)
+    if kind == "rand":
+        X = crandn(rng, m, n)
+    elif kind == "decay":
+        X = _spectrum_matrix(rng, m, n, np.exp(-np.arange(p) / 6.0))
+    elif kind == "ties":
+        sv = np.repeat(np.exp(-np.arange(p // 4) / 3.0), 4)       # quadruplets
+        X = _spectrum_matrix(rng, m, n, sv)
+    else:
+        sv = np.concatenate([np.exp(-np.arange(p // 3) / 4.0), np.zeros(p - p // 3)])
+        X = _spectrum_matrix(rng, m, n, sv)
+    S_ref = np.linalg.svd(X, compute_uv=False)
+    for chi_max, cutoff in ((p, 0.0), (max(1, p // 2), 1e-10), (max(1, p // 3 + 1), 0.0)):
+        r_ref, disc_ref = ls.choose_rank(S_ref, chi_max, cutoff)
+        for centre_right in (True, False):
+            left = to_dev(np.zeros(m * p))
+            right = to_dev(np.zeros(p * n))
+            sig = __import__("torch").zeros(p, dtype=__import__("torch").float64, device="cuda")
+            r, disc = api.k_split(ctx, to_dev(X), m, n, chi_max, cutoff, centre_right, left, right,
+                                  sig)
+            assert r == r_ref
+            assert abs(disc - disc_ref) <= 1e-12 * max(disc_ref, 1e-12) + 1e-15
+            assert np.allclose(sig.cpu().numpy(), S_ref, rtol=0, atol=1e-13 * S_ref[0])
+            Lh = to_host(left)[: m * r].reshape(m, r)
+            Rh = to_host(right)[: r * n].reshape(r, n)
+            # the truncated product is gauge invariant: compare with the oracle split
+            A1, A2, _, _ = ls.split_two_site(X.reshape(m, 1, 1, n), chi_max, cutoff, centre_right)
+            want = A1.reshape(m, -1) @ A2.reshape(-1, n)
+            assert rel_err(Lh @ Rh, want) < 1e-11
+            iso = Lh if centre_right else Rh.conj().T
+            assert np.abs(iso.conj().T @ iso - np.eye(r)).max() < 1e-12
+
+
+def _canonical_envs(Ws, A, i):
+    """Environments of a mixed-canonical random MPS around bond (i, i+1)."""
+    from oracle import mps as omps
+    B = ls.right_canonicalize_svd(A)
+    for k in range(i):
+        chl, d, chr_ = B[k].shape
+        Q, Rm = np.linalg.qr(B[k].reshape(chl * d, chr_))
+        B[k] = Q.reshape(chl, d, Q.shape[1])
+        B[k + 1] = np.tensordot(Rm, B[k + 1], axes=([1], [0]))
+    L = np.ones((1, 1, 1), complex)
+    for k in range(i):
+        L = ls.left_env_update(L, B[k], Ws[k], B[k])
+    R = np.ones((1, 1, 1), complex)
+    for k in range(len(B) - 1, i + 1, -1):
+        R = ls.right_env_update(R, B[k], Ws[k], B[k])
+    X0 = np.tensordot(B[i], B[i + 1], axes=([2], [0]))
+    return L, R, X0
+
+
+@pytest.mark.parametrize("model,N,chi,i", [("heisenberg", 10, 8, 4), ("heisenberg", 20, 64, 9),
+                                           ("anderson", 6, 16, 2), ("heisenberg", 24, 256, 11)])
+def test_local_solve_matches_oracle_gmres(api, ctx, model, N, chi, i):
+    if model == "heisenberg":
+        Ws = ompo.heisenberg_mpo(N)
+        A = inputs.random_mps(N, 2, chi, 100 + N)
+    else:
+        eps, V = inputs.flat_band_bath(N - 1)
+        Ws = ompo.anderson_mpo(-0.15, 0.3, eps, V)
+        A = inputs.random_mps(N, 4, chi, 100 + N)
+    H = api.mpo_create(ctx, Ws)
+    L, R, X0 = _canonical_envs(Ws, A, i)
+    rng = np.random.default_rng(N)
+    B = X0 + 0.3 * crandn(rng, *X0.shape)
+    for c, s, m in ((0.05, -1.0, 10), (30.0, 0.2, 10), (1.0, 0.0, 4)):
+        alpha = 1.0 - c * s
+        mv = lambda V: alpha * V + c * ls.heff_apply(L, Ws[i], Ws[i + 1], R, V)
+        Xw, (k_ref, res_ref) = ls.gmres(mv, B, X0, m)
+        X = to_dev(X0)
+        k, res = api.k_local_solve(ctx, H, i, to_dev(L_to_lib(L)), to_dev(R_to_lib(R)), to_dev(B), X,
+                                   alpha, c, m)
+        assert k == k_ref
+        assert rel_err(to_host(X), Xw) < 1e-10
+        assert abs(res - res_ref) < 1e-8 * max(res_ref, 1e-6)
