@@ -1,0 +1,314 @@
+"""Benchmark: tau-steps/s of the implicit MPS imaginary-time step on GB300.
+
+Workload (the configuration the headline metric is quoted on): Heisenberg XXX
+chain, N = 64, J = 1, open boundaries, MPO bond dimension 5, chi_max = 256,
+SVD cutoff 1e-10, backward Euler (implicit Euler) on the geometric tau grid
+1e-3 -> 1e3 with 40 steps, shift = energy of the current state.  The start
+state is a seeded synthetic MPS at the saturated bond dimension (chi = 256 in
+the bulk), standing in for the evolved random product state once chi has
+saturated, where the evolution spends its time.  One benchmark step = one
+implicit tau-step (gauge move, environments, a full L->R->R->L sweep of
+GMRES(10) local solves with truncated SVD splits, normalisation, energy) on
+the next node of the grid.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas (one chain per rank, no data-path
+collective), launched with torch.distributed.run.  --impl reference times the
+CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SITES, CHI, CUTOFF, D_MPO, D_SITE = 64, 256, 1e-10, 5, 2
+TAU0, TAU_MAX, K_GRID = 1e-3, 1e3, 40
+SEED = 2000
+METRIC = "H_eff matvec TFLOP/s; τ-steps/s vs plain FP64 at equal ΔE; p50/p99 latency"
+UNIT = "tau-steps/s"
+# FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz ~ 1.26 TFLOP/s;
+# the nominal figure is 1.25 TFLOP/s (a DFMA probe measured 1.19 at 1995 MHz).
+FP64_PEAK_TFLOPS = 1.25
+WORKLOAD = ("heisenberg_bulk: XXX chain N=64 J=1 OBC, D=5, chi_max=256, cutoff 1e-10, "
+            "backward Euler on geometric grid 1e-3->1e3 (40 steps), shift=current energy, "
+            "saturated synthetic start (chi=256 bulk)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def bond_weights():
+    """Cost of each of the 2(N-1) two-site updates of a sweep relative to a
+    bulk update, by the algorithmic H_eff FLOP count (chi profile of the
+    saturated state)."""
+    from paper_2606_02930_gb300 import inputs
+    cap = [1] + inputs.bond_profile(N_SITES, D_SITE, CHI) + [1]
+    d, D = D_SITE, D_MPO
+
+    def fl(chl, chr_):
+        return D * d * d * chl * chr_ * (chl + chr_) + 2 * D * D * d ** 3 * chl * chr_
+
+    bulk = fl(CHI, CHI)
+    w = [fl(cap[i], cap[i + 2]) / bulk for i in range(N_SITES - 1)]
+    return 2.0 * sum(w)
+
+
+def oracle_bond_sample(n_bonds):
+    """Time the oracle on n_bonds bulk two-site updates (projection of the
+    right-hand side, GMRES(10) on (1 - c s) X + c H_eff X, truncated SVD split,
+    environment updates) at chi = 256.  Returns seconds per bulk update."""
+    from oracle import linsolve as ls, mpo as ompo
+    rng = np.random.default_rng(SEED)
+
+    def cr(*s):
+        return (rng.standard_normal(s) + 1j * rng.standard_normal(s)) / np.sqrt(2 * s[0])
+
+    Ws = ompo.heisenberg_mpo(N_SITES)
+    c, s = 0.1, -10.0
+    L, R = cr(CHI, D_MPO, CHI), cr(CHI, D_MPO, CHI)
+    Lo, Ro = cr(CHI, CHI), cr(CHI, CHI)
+    A1, A2 = cr(CHI, D_SITE, CHI), cr(CHI, D_SITE, CHI)
+    t0 = time.perf_counter()
+    for b in range(n_bonds):
+        i = 20 + b
+        B = ls.project_two_site(Lo, A1, A2, Ro)
+        X0 = np.tensordot(A1, A2, axes=([2], [0]))
+        mv = lambda V: (1 - c * s) * V + c * ls.heff_apply(L, Ws[i], Ws[i + 1], R, V)
+        X, _ = ls.gmres(mv, B, X0, 10)
+        U, SV, _, _ = ls.split_two_site(X, CHI, CUTOFF, True)
+        ls.left_env_update(L, U, Ws[i], U)
+        ls.left_overlap_update(Lo, U, A1)
+    return (time.perf_counter() - t0) / n_bonds
+
+
+def cpu_baseline_line(n_bonds):
+    t_bond = oracle_bond_sample(n_bonds)
+    per_step = t_bond * bond_weights()
+    return {"value": 1.0 / per_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"{n_bonds} bulk chi=256 two-site updates of the oracle (RHS projection, "
+                       f"GMRES(10), truncated SVD, environment updates) timed on the host, scaled "
+                       f"by the {bond_weights():.1f} bulk-equivalent updates of one tau-step")}
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    for _ in range(W):
+        oracle_bond_sample(1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(K):
+        t = oracle_bond_sample(args.bonds) * bond_weights()
+        vals.append(t)
+    tot = time.perf_counter() - t0
+    value = 1.0 / statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * statistics.mean(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{args.bonds} bulk bonds per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"each step: {args.bonds} bulk chi=256 two-site updates "
+                                        f"scaled by {bond_weights():.1f} bulk-equivalent updates "
+                                        f"per tau-step; wall {tot:.1f} s")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2606_02930_gb300 import api, inputs
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    ctx = api.ctx_create(local_rank)
+    stream = torch.cuda.current_stream()
+    H = api.mpo_create_heisenberg(ctx, N_SITES)
+    A0 = inputs.random_mps(N_SITES, D_SITE, CHI, SEED + rank)
+    psi = api.mps_create(ctx, A0, CHI)
+    nodes = api.grid_geometric(TAU0, TAU_MAX, K_GRID)
+    state = {"k": 0, "s": api.energy(ctx, H, psi)}
+
+    def one_step(p):
+        k = state["k"] % K_GRID
+        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], "be", state["s"], CHI, CUTOFF)
+        state["k"] += 1
+        state["s"] = info["energy"]
+        return info
+
+    for _ in range(args.warmup):
+        one_step(psi)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region: state resident in HBM
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    launches0 = api.kernel_launches()
+    api.profile_start(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [one_step(psi) for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    prof = api.profile_stop(ctx)
+    launches = api.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    cap = [1] + inputs.bond_profile(N_SITES, D_SITE, CHI) + [1]
+    cap_doubles = sum(2 * cap[i] * D_SITE * cap[i + 1] for i in range(N_SITES))
+    host = torch.empty(cap_doubles, dtype=torch.float64, pin_memory=True)
+    from paper_2606_02930_gb300 import _lib as L
+    import ctypes as C
+    lib = L.lib
+    host_chi = np.zeros(N_SITES + 1, np.int32)
+    hptr = C.cast(C.c_void_p(host.data_ptr()), C.POINTER(C.c_double))
+    n = C.c_size_t()
+    L.check(lib.ite_mps_bond_dims(psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
+    L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
+    h2d = d2h = 0
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.check(lib.ite_mps_set(ctx.h, psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)), hptr),
+                ctx.h)
+        h2d += 8 * n.value
+        one_step(psi)
+        L.check(lib.ite_mps_bond_dims(psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)),
+                                      C.byref(n)))
+        L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
+        d2h += 8 * n.value
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    heff = prof["heff"]
+    achieved = heff["flops"] / (heff["ms"] * 1e-3) / 1e12 if heff["ms"] > 0 else 0.0
+    breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_SITES, "chi_max": CHI, "cutoff": CUTOFF,
+                       "scheme": "backward_euler", "precision": "fp64",
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state 134 MB + environments 0.7 GB per chain)"},
+            "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "two-site H_eff (zgemm_kernel x2 + k_mix), FP64", "bound": "alu",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_note": "nominal FP64 pipe rate (no measured FP64 peak in the peaks file)"},
+            "stage_ms_per_step": breakdown,
+            "heff_calls_per_step": heff["count"] // max(1, args.steps),
+            "energies": [i["energy"] for i in infos],
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line(args.bonds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

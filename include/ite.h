@@ -114,6 +114,16 @@ void ite_ctx_destroy(ite_ctx ctx);
 const char* ite_last_error(ite_ctx ctx);
 /* Bytes currently held through the allocator by this context and its objects. */
 size_t ite_ctx_device_bytes(ite_ctx ctx);
+/* Number of CUDA kernels the library has launched so far in this process. */
+unsigned long long ite_kernel_launches(void);
+/* Stage timers (CUDA events on the context stream).  Between start and stop
+ * every stage of the sweep records an event pair; stop synchronises and
+ * returns, per category, the summed milliseconds, the summed algorithmic FLOPs
+ * and the number of stages: 0 two-site H_eff, 1 environment updates, 2 local
+ * solves (GMRES, H_eff included), 3 truncated SVD splits, 4 gauge moves (SVDs
+ * included), 5 local right-hand sides and two-site merges, 6 whole steps. */
+ite_status ite_profile_start(ite_ctx ctx);
+ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long long counts[8]);
 
 /* MPO from explicit site tensors: d[N] site dimensions (all equal), D[N+1]
  * bond dimensions with D[0] = D[N] = 1, W the concatenated W_i (interleaved

@@ -297,3 +297,25 @@ def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None
     check(lib.ite_k_split(ctx.h, _p(X), m, n, chi_max, cutoff, 1 if centre_right else 0, _p(left),
                           _p(right), _p(sigma), C.byref(r), C.byref(disc)), ctx.h)
     return r.value, disc.value
+
+
+# ------------------------------------------------------------------ profiling
+PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step")
+
+
+def kernel_launches():
+    return int(lib.ite_kernel_launches())
+
+
+def profile_start(ctx):
+    check(lib.ite_profile_start(ctx.h), ctx.h)
+
+
+def profile_stop(ctx):
+    ms = np.zeros(8)
+    fl = np.zeros(8)
+    cnt = np.zeros(8, np.int64)
+    check(lib.ite_profile_stop(ctx.h, _dptr(ms), _dptr(fl),
+                               cnt.ctypes.data_as(C.POINTER(C.c_longlong))), ctx.h)
+    return {k: {"ms": float(ms[i]), "flops": float(fl[i]), "count": int(cnt[i])}
+            for i, k in enumerate(PROFILE_CATEGORIES)}

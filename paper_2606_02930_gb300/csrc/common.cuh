@@ -34,6 +34,10 @@ __host__ __device__ __forceinline__ void cfma_conj(cplx& acc, cplx a, cplx b) {
 
 namespace ite {
 
+// Number of kernels this library has launched (process-wide, all contexts).
+void count_launches(unsigned long long n);
+unsigned long long launches();
+
 // ---------------------------------------------------------------- GEMM (FP64)
 // C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] (+ gamma * Z[b] if Z), complex.
 // Element (i, k) of A is at A[b*sAb + i*sAm + k*sAk] (conjugated if conjA);

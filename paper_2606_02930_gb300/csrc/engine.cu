@@ -17,6 +17,7 @@
 #include "ite_kernels.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,12 @@
 #include <vector>
 
 using namespace ite;
+
+namespace ite {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace ite
 
 namespace {
 
@@ -69,6 +76,12 @@ struct ite_ctx_s {
   cplx* partial = nullptr;     // reduction partials
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
+  // event profiling of the sweep's stages (off unless started)
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  struct Rec { int cat; size_t e0, e1; double flops; };
+  std::vector<Rec> recs;
 };
 
 struct ite_mpo_s {
@@ -159,6 +172,37 @@ ite_status sync(ite_ctx ctx) {
   return ITE_OK;
 }
 
+// ------------------------------------------------------------------ profiling
+enum { P_HEFF = 0, P_ENV, P_SOLVE, P_SVD, P_GAUGE, P_PROJ, P_STEP, P_NCAT };
+
+size_t prof_event(ite_ctx ctx) {
+  if (ctx->evused == ctx->evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    ctx->evpool.push_back(e);
+  }
+  const size_t k = ctx->evused++;
+  cudaEventRecord(ctx->evpool[k], ctx->stream);
+  return k;
+}
+
+// Records an event pair around a stage when profiling is on.
+struct Scope {
+  ite_ctx ctx;
+  int cat;
+  size_t e0;
+  double flops;
+  Scope(ite_ctx c, int k, double f = 0.0) : ctx(c), cat(k), e0((size_t)-1), flops(f) {
+    if (ctx->prof) e0 = prof_event(ctx);
+  }
+  ~Scope() {
+    if (ctx->prof && e0 != (size_t)-1) {
+      const size_t e1 = prof_event(ctx);
+      if (e1 != (size_t)-1) ctx->recs.push_back({cat, e0, e1, flops});
+    }
+  }
+};
+
 // ------------------------------------------------------------------ contractions
 // Plain GEMM helpers.  Row-major matrices; strides in complex units.
 ite_status gemm(ite_ctx ctx, int M, int N, int K, const cplx* A, long long sAm, long long sAk,
@@ -180,8 +224,12 @@ ite_status gemm(ite_ctx ctx, int M, int N, int K, const cplx* A, long long sAm, 
 ite_status heff(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int chrB,
                 const cplx* L, const cplx* R, const cplx* X, cplx* Y, cplx alpha, const cplx* Z,
                 cplx gamma) {
-  const int d = H->d, D0 = H->D[i], D2 = H->D[i + 2];
+  const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1], D2 = H->D[i + 2];
   const long long d2 = (long long)d * d;
+  // algorithmic real FLOPs of the dense two-site contraction (complex MACs x 8)
+  const double flops = 8.0 * ((double)D0 * d2 * chlB * chlK * chrK + (double)D2 * d2 * chlB * chrK * chrB +
+                              2.0 * D1 * D1 * d2 * d * chlB * chrK);
+  Scope sc(ctx, P_HEFF, flops);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   cplx* T2 = P<cplx>(ctx->ws_T2);
   // T1[(w a), (s t b')] = L[(w a), a'] X[a', (s t b')]
@@ -201,6 +249,7 @@ ite_status heff(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int
 ite_status env_left(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB, int chrK,
                     const cplx* Lin, const cplx* bra, const cplx* ket, cplx* Lout) {
   const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1];
+  Scope sc(ctx, P_ENV);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   cplx* T2 = P<cplx>(ctx->ws_T2);
   const long long ld = (long long)d * chrK;
@@ -218,6 +267,7 @@ ite_status env_left(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB,
 ite_status env_right(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB, int chrK,
                      const cplx* Rin, const cplx* bra, const cplx* ket, cplx* Rout) {
   const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1];
+  Scope sc(ctx, P_ENV);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   cplx* T2 = P<cplx>(ctx->ws_T2);
   const long long blk = (long long)chlK * d * chrB;
@@ -237,6 +287,7 @@ ite_status env_right(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB
 
 ite_status ov_left(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, const cplx* Lin,
                    const cplx* bra, const cplx* ket, cplx* Lout) {
+  Scope sc(ctx, P_ENV);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   const long long ld = (long long)d * chrK;
   CS(gemm(ctx, chlB, (int)ld, chlK, Lin, chlK, 1, false, ket, ld, 1, false, T1, ld));
@@ -246,6 +297,7 @@ ite_status ov_left(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, c
 
 ite_status ov_right(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, const cplx* Rin,
                     const cplx* bra, const cplx* ket, cplx* Rout) {
+  Scope sc(ctx, P_ENV);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   CS(gemm(ctx, chlK * d, chrB, chrK, ket, chrK, 1, false, Rin, chrB, 1, false, T1, chrB));
   CS(gemm(ctx, chlK, chlB, d * chrB, T1, (long long)d * chrB, 1, false, bra, 1, (long long)d * chrB,
@@ -256,6 +308,7 @@ ite_status ov_right(ite_ctx ctx, int d, int chlB, int chlK, int chrB, int chrK, 
 // out[a,s,t,b] = alpha * sum LO[a][a''] K1[a'',s,c] K2[c,t,b''] RO[b''][b]
 ite_status project(ite_ctx ctx, int d, int chlB, int chlK, int chm, int chrK, int chrB,
                    const cplx* LO, const cplx* K1, const cplx* K2, const cplx* RO, cplx* out) {
+  Scope sc(ctx, P_PROJ);
   cplx* T1 = P<cplx>(ctx->ws_T1);
   cplx* T2 = P<cplx>(ctx->ws_T2);
   CS(gemm(ctx, chlB, d * chm, chlK, LO, chlK, 1, false, K1, (long long)d * chm, 1, false, T1,
@@ -268,6 +321,7 @@ ite_status project(ite_ctx ctx, int d, int chlB, int chlK, int chm, int chrK, in
 
 ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, const cplx* K2,
                  cplx* out) {
+  Scope sc(ctx, P_PROJ);
   return gemm(ctx, chl * d, d * chr, chm, K1, chm, 1, false, K2, (long long)d * chr, 1, false, out,
               (long long)d * chr);
 }
@@ -276,6 +330,7 @@ ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, 
 ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
                  bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
                  double* sigma_out = nullptr) {
+  Scope sc(ctx, P_SVD);
   cplx* A = P<cplx>(ctx->ws_svdA);
   cplx* Q = P<cplx>(ctx->ws_svdQ);
   const bool tr = m > n;
@@ -310,6 +365,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
 ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
                        const cplx* R, const cplx* B, cplx* X, double alpha, double c, int m,
                        double local_tol, int* steps, double* res) {
+  Scope sc(ctx, P_SOLVE);
   const long long n = (long long)chl * H->d * H->d * chr;
   cplx* V = P<cplx>(ctx->ws_V);
   GmresState* gs = ctx->gm;
@@ -598,6 +654,7 @@ ite_status set_one(ite_ctx ctx, cplx* p) {
 
 // gauge move: sites N-1..1 right-orthonormal by SVD (weight floor only)
 ite_status right_canonicalize(ite_ctx ctx, ite_mps x) {
+  Scope sc(ctx, P_GAUGE);
   const int d = x->d;
   for (int i = x->N - 1; i >= 1; --i) {
     const int chl = x->chi[i], chr = x->chi[i + 1];
@@ -746,12 +803,45 @@ void ite_ctx_destroy(ite_ctx ctx) {
   dev_free(ctx, ctx->partial, (size_t)kPartialSlots * sizeof(cplx));
   dev_free(ctx, ctx->dcounter, 16 * sizeof(int));
   if (ctx->hr) cudaFreeHost(ctx->hr);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
 }
 
 const char* ite_last_error(ite_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 size_t ite_ctx_device_bytes(ite_ctx ctx) { return ctx ? ctx->bytes : 0; }
+
+unsigned long long ite_kernel_launches(void) { return ite::launches(); }
+
+ite_status ite_profile_start(ite_ctx ctx) {
+  if (!ctx) return ITE_EINVAL;
+  ctx->prof = true;
+  ctx->evused = 0;
+  ctx->recs.clear();
+  return ITE_OK;
+}
+
+ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long long counts[8]) {
+  if (!ctx) return ITE_EINVAL;
+  ctx->prof = false;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < 8; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (flops) flops[k] = 0.0;
+    if (counts) counts[k] = 0;
+  }
+  for (const auto& r : ctx->recs) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ctx->evpool[r.e0], ctx->evpool[r.e1]));
+    if (r.cat < 0 || r.cat >= 8) continue;
+    if (ms) ms[r.cat] += t;
+    if (flops) flops[r.cat] += r.flops;
+    if (counts) counts[r.cat] += 1;
+  }
+  ctx->recs.clear();
+  ctx->evused = 0;
+  return ITE_OK;
+}
 
 }  // extern "C"
 
@@ -846,6 +936,7 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
     return fail(ctx, ITE_EINVAL, "invalid step arguments");
   CS(ensure_work(ctx, psi));
   CS(ensure_workspace(ctx, H, psi->cap, psi->d, o.krylov_dim));
+  Scope step_scope(ctx, P_STEP);
   SweepStats st;
   ite_mps x = psi->work_x, bm = psi;
   double c;

@@ -236,6 +236,7 @@ cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
   long long g = (tot + 255) / 256;
   if (g > 1216) g = 1216;
   if (g < 1) g = 1;
+  count_launches(1);
   k_identity<<<(int)g, 256, 0, st>>>(Q, p);
   return cudaGetLastError();
 }
@@ -253,6 +254,7 @@ cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double t
     if (err != cudaSuccess) return err;
     for (int r = 0; r < pp - 1; ++r)
       k_jacobi_round<<<pp / 2, JT, 0, st>>>(A, p, q, Q, r, pp, tol, dev_counter);
+    count_launches(pp - 1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     err = cudaMemcpyAsync(host_counter, dev_counter, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -269,7 +271,9 @@ cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, doub
                      int chi_max, double cutoff, double weight_floor, double tie_rel,
                      int* rank_out, double* discarded_out, cudaStream_t st) {
   if (p <= 0) return cudaErrorInvalidValue;
+  count_launches(1);
   k_row_norms<<<p, JT, 0, st>>>(A, p, q, sigma);
+  count_launches(1);
   k_sort_rank<<<1, 1024, 0, st>>>(sigma, p, perm, sorted_sigma, chi_max, cutoff, weight_floor,
                                   tie_rel, rank_out, discarded_out);
   return cudaGetLastError();
@@ -282,6 +286,7 @@ cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma
   long long g = (tot + 255) / 256;
   if (g > 1216) g = 1216;
   if (g < 1) g = 1;
+  count_launches(1);
   k_emit<<<(int)g, 256, 0, st>>>(Arot, Q, sorted_sigma, perm, r, p, q, transposed, centre_right,
                                   left, right);
   return cudaGetLastError();
@@ -289,6 +294,7 @@ cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma
 
 cudaError_t conj_transpose(const cplx* A, int m, int n, cplx* out, cudaStream_t st) {
   dim3 grid((n + 31) / 32, (m + 31) / 32);
+  count_launches(1);
   k_conj_transpose<<<grid, dim3(32, 8), 0, st>>>(A, m, n, out);
   return cudaGetLastError();
 }

@@ -280,16 +280,19 @@ __global__ void k_gmres_finish(GmresState* s) {
 
 cudaError_t vec_copy(cplx* y, const cplx* x, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launches(1);
   k_copy<<<grid_for(n), VT, 0, st>>>(y, x, n);
   return cudaGetLastError();
 }
 cudaError_t vec_zero(cplx* y, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launches(1);
   k_zero<<<grid_for(n), VT, 0, st>>>(y, n);
   return cudaGetLastError();
 }
 cudaError_t vec_axpby(cplx* y, const cplx* x, cplx a, cplx b, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launches(1);
   k_axpby<<<grid_for(n), VT, 0, st>>>(y, x, a, b, n);
   return cudaGetLastError();
 }
@@ -298,7 +301,9 @@ cudaError_t vec_block_dot(const cplx* V, long long ldv, int nv, const cplx* w, l
   if (nv <= 0) return cudaSuccess;
   if (nv > MAXV) return cudaErrorInvalidValue;
   const int g = grid_for(n);
+  count_launches(1);
   k_block_dot<<<g, VT, 0, st>>>(V, ldv, nv, w, n, partial, active);
+  count_launches(1);
   k_reduce_cplx<<<1, 32, 0, st>>>(partial, g, nv, out, active);
   return cudaGetLastError();
 }
@@ -307,19 +312,23 @@ cudaError_t vec_block_axpy(const cplx* V, long long ldv, int nv, const int* nv_d
                            cudaStream_t st) {
   if (nv <= 0 || n <= 0) return cudaSuccess;
   if (nv > MAXV) return cudaErrorInvalidValue;
+  count_launches(1);
   k_block_axpy<<<grid_for(n), VT, 0, st>>>(V, ldv, nv, nv_dev, h, sign, w, n, active);
   return cudaGetLastError();
 }
 cudaError_t vec_norm2(const cplx* x, long long n, double* out, double* partial,
                       const int* active, cudaStream_t st) {
   const int g = grid_for(n);
+  count_launches(1);
   k_norm2_partial<<<g, VT, 0, st>>>(x, n, partial, active);
+  count_launches(1);
   k_reduce_real<<<1, 32, 0, st>>>(partial, g, out, active);
   return cudaGetLastError();
 }
 cudaError_t vec_scale_dev(cplx* y, const double* scale, long long n, const int* active,
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  count_launches(1);
   k_scale_dev<<<grid_for(n), VT, 0, st>>>(y, scale, n, active);
   return cudaGetLastError();
 }
@@ -327,7 +336,9 @@ cudaError_t env_trace(const cplx* L, const cplx* R, int D, int m, int n, cplx* o
                       cplx* partial, cudaStream_t st) {
   const long long tot = (long long)D * m * n;
   const int g = grid_for(tot);
+  count_launches(1);
   k_env_trace<<<g, VT, 0, st>>>(L, R, D, m, n, partial);
+  count_launches(1);
   k_reduce_cplx<<<1, 32, 0, st>>>(partial, g, 1, out, nullptr);
   return cudaGetLastError();
 }
@@ -335,6 +346,7 @@ cudaError_t apply_site_op(const cplx* O, const cplx* K, cplx* Kout, int chl, int
                           cudaStream_t st) {
   const long long tot = (long long)chl * d * chr;
   if (tot <= 0) return cudaSuccess;
+  count_launches(1);
   k_site_op<<<grid_for(tot), VT, 0, st>>>(O, K, Kout, chl, d, chr);
   return cudaGetLastError();
 }
@@ -346,26 +358,31 @@ cudaError_t mix_apply(const MixPlan& plan, const MixStrides& s, int P, int Q, co
   if (tot <= 0) return cudaSuccess;
   long long g = (tot + 127) / 128;
   if (g > 1216) g = 1216;
+  count_launches(1);
   k_mix<<<(int)g, 128, 0, st>>>(plan, s, P, Q, in, iP, iQ, out, oP, oQ);
   return cudaGetLastError();
 }
 cudaError_t gmres_start(GmresState* s, const double* r0norm2, const double* bnorm2,
                         cudaStream_t st) {
+  count_launches(1);
   k_gmres_start<<<1, 1, 0, st>>>(s, r0norm2, bnorm2);
   return cudaGetLastError();
 }
 cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cplx* h2,
                           cudaStream_t st) {
   (void)m;
+  count_launches(1);
   k_gmres_collect<<<1, 32, 0, st>>>(s, j, h1, h2);
   return cudaGetLastError();
 }
 cudaError_t gmres_step(GmresState* s, int j, int m, double breakdown_rel, double local_tol,
                        cudaStream_t st) {
+  count_launches(1);
   k_gmres_step<<<1, 1, 0, st>>>(s, j, m, breakdown_rel, local_tol);
   return cudaGetLastError();
 }
 cudaError_t gmres_finish(GmresState* s, cudaStream_t st) {
+  count_launches(1);
   k_gmres_finish<<<1, 1, 0, st>>>(s);
   return cudaGetLastError();
 }

@@ -97,6 +97,7 @@ cudaError_t zgemm(const GemmArgs& g, cudaStream_t st) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
   const bool a_kfast = (g.sAk == 1);
   const bool b_nfast = (g.sBn == 1) || (g.sBk != 1);
+  count_launches(1);
   if (g.conjA && g.conjB)
     zgemm_kernel<true, true><<<grid, THREADS, 0, st>>>(g, a_kfast, b_nfast);
   else if (g.conjA)
