@@ -65,6 +65,25 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded);
 
+/* Same result as ite_k_heff, for callers that cannot allocate device memory
+ * at call time (cudaMalloc can synchronise the whole device, the process may
+ * have given all device memory to another pool, or allocation calls may be
+ * forbidden where the caller runs).  This call allocates nothing: its two
+ * intermediates live in one static device array of 2 x 524288 complex doubles
+ * (16 MiB), held by every GPU that loads the library until the process exits.
+ * The paper has no counterpart; it is a property of this library.
+ * Sizes: D_i*chl_bra*d^2*chr_ket and D_{i+2}*chl_bra*d^2*chr_ket must each be
+ * <= 524288, otherwise ITE_EINVAL (message in ite_last_error) and nothing runs.
+ * All calls share the array: calls whose GPU work overlaps (other streams or
+ * host threads) race and must be ordered by the caller.  Nothing in the array
+ * needs to start at zero.  The first call on a device looks up the array's
+ * device address, so make it before any stream capture.  Synchronises the
+ * context stream before returning. */
+ite_status ite_k_heff_noalloc(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                              int chr_ket, int chr_bra, const double* L, const double* R,
+                              const double* X, double* Y, const double alpha[2],
+                              const double* Z, const double gamma[2]);
+
 #ifdef __cplusplus
 }
 #endif

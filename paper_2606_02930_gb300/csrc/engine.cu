@@ -1468,3 +1468,29 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
 }
 
 }  // extern "C"
+
+// ================================================================== accessors
+// Read-only views of context and MPO internals for the allocation-free
+// variant in heff_static.cu.
+namespace ite {
+
+bool internal_ctx_info(ite_ctx ctx, int* device, cudaStream_t* stream) {
+  if (!ctx) return false;
+  *device = ctx->device;
+  *stream = ctx->stream;
+  return true;
+}
+
+bool internal_bond_info(ite_mpo H, int i, int* d, int* D0, int* D1, int* D2, const MixPlan** plan) {
+  if (!H || i < 0 || i + 1 >= H->N) return false;
+  *d = H->d;
+  *D0 = H->D[i];
+  *D1 = H->D[i + 1];
+  *D2 = H->D[i + 2];
+  *plan = &H->plan2[i];
+  return true;
+}
+
+ite_status internal_fail(ite_ctx ctx, ite_status st, const char* msg) { return fail(ctx, st, msg); }
+
+}  // namespace ite
