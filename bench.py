@@ -5,8 +5,9 @@ chain, N = 64, J = 1, open boundaries, MPO bond dimension 5, chi_max = 256,
 SVD cutoff 1e-10, backward Euler (implicit Euler) on the geometric tau grid
 1e-3 -> 1e3 with 40 steps, shift = energy of the current state.  The start
 state is a seeded synthetic MPS at the saturated bond dimension (chi = 256 in
-the bulk), standing in for the evolved random product state once chi has
-saturated, where the evolution spends its time.  One benchmark step = one
+the bulk: random isometries with bond weights exp(-b/64), so the cap of 256
+binds rather than the cutoff), standing in for the evolved random product
+state once chi has saturated, where the evolution spends its time.  One benchmark step = one
 implicit tau-step (gauge move, environments, a full L->R->R->L sweep of
 GMRES(10) local solves with truncated SVD splits, normalisation, energy) on
 the next node of the grid.
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
+    ap.add_argument("--only", choices=["heff", "split"], default=None,
+                    help="time one kernel-level call at the bulk shape (for profiler captures)")
     return ap.parse_args()
 
 
@@ -196,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = api.ctx_create(local_rank)
     stream = torch.cuda.current_stream()
     H = api.mpo_create_heisenberg(ctx, N_SITES)
-    A0 = inputs.random_mps(N_SITES, D_SITE, CHI, SEED + rank)
+    A0 = inputs.random_isometric_mps(N_SITES, D_SITE, CHI, SEED + rank)
     psi = api.mps_create(ctx, A0, CHI)
     nodes = api.grid_geometric(TAU0, TAU_MAX, K_GRID)
     state = {"k": 0, "s": api.energy(ctx, H, psi)}
@@ -221,6 +224,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clocks.start()
     launches0 = api.kernel_launches()
+    api.svd_stats(ctx)
     api.profile_start(ctx)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -229,6 +233,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     prof = api.profile_stop(ctx)
+    svd = api.svd_stats(ctx)
     launches = api.kernel_launches() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
@@ -289,6 +294,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_note": "nominal FP64 pipe rate (no measured FP64 peak in the peaks file)"},
             "stage_ms_per_step": breakdown,
             "heff_calls_per_step": heff["count"] // max(1, args.steps),
+            "svd_jacobi": svd,
             "energies": [i["energy"] for i in infos],
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -299,8 +305,51 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    """Time one kernel-level entry point at the workload's bulk shape: the
+    two-site H_eff (chi = 256, d = 2, D = 5) or the truncated SVD split of a
+    512 x 512 two-site block.  Prints one JSON line (not a benchmark line)."""
+    import torch
+    from paper_2606_02930_gb300 import api, inputs
+    ctx = api.ctx_create(0)
+    rng = np.random.default_rng(SEED)
+
+    def dev(*shape):
+        a = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(shape[-1])
+        return torch.from_numpy(a).to("cuda")
+
+    H = api.mpo_create_heisenberg(ctx, N_SITES)
+    if args.only == "heff":
+        L, R, X = dev(D_MPO, CHI, CHI), dev(D_MPO, CHI, CHI), dev(CHI, D_SITE, D_SITE, CHI)
+        Y = torch.empty_like(X)
+        call = lambda: api.k_heff(ctx, H, 20, L, R, X, Y)
+        flops = 8.0 * (2 * D_MPO * D_SITE ** 2 * CHI ** 3 + 2 * D_MPO ** 2 * D_SITE ** 3 * CHI ** 2)
+    else:
+        A = inputs.random_isometric_mps(4, D_SITE, CHI, SEED)
+        X = torch.from_numpy(np.tensordot(A[1], A[2], axes=([2], [0])).reshape(512, 512)).to("cuda")
+        left = torch.empty(512 * 512, dtype=torch.complex128, device="cuda")
+        right = torch.empty_like(left)
+        call = lambda: api.k_split(ctx, X, 512, 512, CHI, CUTOFF, True, left, right)
+        flops = 0.0
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        call()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    out = {"only": args.only, "ms_per_call": ms}
+    if flops:
+        out["tflops"] = flops / (ms * 1e-3) / 1e12
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.only:
+        run_only(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -123,6 +123,9 @@ unsigned long long ite_kernel_launches(void);
  * solves (GMRES, H_eff included), 3 truncated SVD splits, 4 gauge moves (SVDs
  * included), 5 local right-hand sides and two-site merges, 6 whole steps. */
 ite_status ite_profile_start(ite_ctx ctx);
+/* Jacobi SVD statistics since the last call (then reset): splits performed,
+ * total and largest number of sweeps. */
+ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max);
 ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long long counts[8]);
 
 /* MPO from explicit site tensors: d[N] site dimensions (all equal), D[N+1]

@@ -319,3 +319,10 @@ def profile_stop(ctx):
                                cnt.ctypes.data_as(C.POINTER(C.c_longlong))), ctx.h)
     return {k: {"ms": float(ms[i]), "flops": float(fl[i]), "count": int(cnt[i])}
             for i, k in enumerate(PROFILE_CATEGORIES)}
+
+
+def svd_stats(ctx):
+    splits, total, mx = C.c_longlong(), C.c_longlong(), C.c_int()
+    check(lib.ite_svd_stats(ctx.h, C.byref(splits), C.byref(total), C.byref(mx)), ctx.h)
+    return {"splits": splits.value, "sweeps_mean": total.value / max(1, splits.value),
+            "sweeps_max": mx.value}

@@ -128,11 +128,12 @@ cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cpl
 
 // ---------------------------------------------------------------- SVD (FP64)
 // One-sided Jacobi SVD of a p x q complex matrix stored row-major in A (rows
-// are the rotated vectors, p <= q expected).  Q (p x p) receives the
-// accumulated row rotations: on return Q A_in = A_out with orthogonal rows.
+// are the rotated vectors).  Q (p x p) receives the accumulated row rotations:
+// on return Q A_in = A_out with mutually orthogonal rows.  Runs as one
+// cooperative launch; dev_state (8 device words) returns the sweeps done in
+// word 5 and a nonzero word 4 if a grid-barrier wait ran out.
 cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        int* sweeps_done, int* host_counter, int* dev_counter,
-                        cudaStream_t st);
+                        unsigned int* dev_state, cudaStream_t st);
 // row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
 // by index), and the kept rank by the truncation rule (see engine).
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

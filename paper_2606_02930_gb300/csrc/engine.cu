@@ -37,8 +37,10 @@ namespace {
 constexpr double kWeightFloor = 1e-24;   // relative squared weight treated as zero
 constexpr double kTieRel = 1e-10;        // near-degenerate singular values
 constexpr double kBreakdownRel = 1e-14;  // GMRES breakdown threshold (relative to |r0|)
-constexpr double kJacobiTol = 1e-14;     // one-sided Jacobi orthogonality tolerance
-constexpr int kJacobiSweeps = 40;
+// one-sided Jacobi: rows count as orthogonal once |a_u^H a_v| <= q eps |a_u||a_v|
+// (the rounding floor of a length-q inner product); sweeps are capped
+constexpr double kEps = 2.220446049250313e-16;
+constexpr int kJacobiSweeps = 30;
 constexpr int kMaxKrylov = 32;
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
@@ -76,6 +78,8 @@ struct ite_ctx_s {
   cplx* partial = nullptr;     // reduction partials
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
+  long long jacobi_sweeps_total = 0, jacobi_splits = 0;
+  int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
   bool prof = false;
   std::vector<cudaEvent_t> evpool;
@@ -337,9 +341,9 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   const int p = tr ? n : m, q = tr ? m : n;
   if (tr) CK(conj_transpose(X, m, n, A, ctx->stream));
   else CK(vec_copy(A, X, (long long)m * n, ctx->stream));
-  int sweeps = 0;
-  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, kJacobiTol, &sweeps, &ctx->hr->counter, ctx->dcounter,
-                 ctx->stream));
+  unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
+  const double jtol = std::max(1e-15, q * kEps);
+  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, jtol, jstate, ctx->stream));
   double* small = P<double>(ctx->ws_small);
   double* sigma = small;
   double* sorted = small + p;
@@ -350,7 +354,13 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
               disc_dev, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
+  ctx->jacobi_sweeps_total += ctx->hr->pad;
+  ctx->jacobi_splits += 1;
+  ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
   const int r = ctx->hr->rank;
   if (r < 1 || r > p) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
   if (sigma_out) CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -812,6 +822,16 @@ const char* ite_last_error(ite_ctx ctx) { return ctx ? ctx->err.c_str() : "null 
 size_t ite_ctx_device_bytes(ite_ctx ctx) { return ctx ? ctx->bytes : 0; }
 
 unsigned long long ite_kernel_launches(void) { return ite::launches(); }
+
+ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max) {
+  if (!ctx) return ITE_EINVAL;
+  if (splits) *splits = ctx->jacobi_splits;
+  if (sweeps_total) *sweeps_total = ctx->jacobi_sweeps_total;
+  if (sweeps_max) *sweeps_max = ctx->jacobi_sweeps_max;
+  ctx->jacobi_splits = ctx->jacobi_sweeps_total = 0;
+  ctx->jacobi_sweeps_max = 0;
+  return ITE_OK;
+}
 
 ite_status ite_profile_start(ite_ctx ctx) {
   if (!ctx) return ITE_EINVAL;

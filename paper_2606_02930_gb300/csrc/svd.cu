@@ -26,11 +26,9 @@ __device__ __forceinline__ int player(int pos, int round, int pp) {
   return pos == 0 ? 0 : ((pos - 1 + round) % (pp - 1)) + 1;
 }
 
-__global__ void __launch_bounds__(JT)
-k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, int* counter) {
-  const int k = blockIdx.x;
-  int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
-  if (u >= p || v >= p) return;
+// One Jacobi rotation on rows u, v of A (and of Q): make the pair orthogonal
+// if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block.
+__device__ void jacobi_pair(cplx* A, int p, int q, cplx* Q, int u, int v, double tol, int* counter) {
   if (u > v) { const int t = u; u = v; v = t; }
   cplx* au = A + (long long)u * q;
   cplx* av = A + (long long)v * q;
@@ -65,10 +63,12 @@ k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, in
     rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != 0.0 || si != 0.0) ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (rot[3] == 0.0) return;
   const double c = rot[0];
   const cplx se = cmake(rot[1], rot[2]);      // s e^{i theta}
   const cplx sec = cconj(se);                  // s e^{-i theta}
+  const bool apply = rot[3] != 0.0;
+  __syncthreads();                             // rot[] is reused by the next pair
+  if (!apply) return;
   // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
   for (int e = threadIdx.x; e < q; e += JT) {
     const cplx x = au[e], y = av[e];
@@ -81,6 +81,71 @@ k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, in
     const cplx x = qu[e], y = qv[e];
     qu[e] = csub(cscale(x, c), cmul(sec, y));
     qv[e] = cadd(cmul(se, x), cscale(y, c));
+  }
+}
+
+__global__ void __launch_bounds__(JT)
+k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, int* counter) {
+  const int k = blockIdx.x;
+  const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
+  if (u >= p || v >= p) return;
+  jacobi_pair(A, p, q, Q, u, v, tol, counter);
+}
+
+// Grid-wide barrier for a cooperative launch.  st[0] arrivals, st[1]
+// generation, st[4] error flag.  Waits are bounded: after ~2^24 polls the
+// error flag is set and the block leaves (the caller then exits).
+__device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = st + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(st, 1u);
+    if (ticket == nblocks - 1) {
+      atomicExch(st, 0u);
+      __threadfence();
+      atomicAdd(st + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*gen == g) {
+        if (++spins > (1ull << 24)) {
+          atomicExch(st + 4, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile unsigned int*)(st + 4)) == 0u;
+}
+
+// All sweeps of the round-robin one-sided Jacobi in one cooperative launch.
+// st[2], st[3]: rotation counters of even / odd sweeps; st[5]: sweeps done.
+// A sweep's counter is read by every block after the sweep's last barrier;
+// the counter of the following sweep is cleared by block 0 in round 1 of the
+// current sweep, after every block has passed round 0 (and so has finished
+// reading it two sweeps ago).
+__global__ void __launch_bounds__(JT)
+k_jacobi_persistent(cplx* A, int p, int q, cplx* Q, int pp, double tol, int max_sweeps,
+                    unsigned int* st) {
+  const unsigned int nb = gridDim.x;
+  int* counters = reinterpret_cast<int*>(st + 2);
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    int* cnt = counters + (sw & 1);
+    for (int r = 0; r < pp - 1; ++r) {
+      if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[(sw + 1) & 1] = 0;
+      for (int k = blockIdx.x; k < pp / 2; k += nb) {
+        const int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
+        if (u < p && v < p) jacobi_pair(A, p, q, Q, u, v, tol, cnt);
+      }
+      if (!grid_barrier(st, nb)) return;
+    }
+    const int rotations = *((volatile int*)cnt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[5] = (unsigned int)(sw + 1);
+    if (rotations == 0) break;
   }
 }
 
@@ -242,29 +307,42 @@ cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
 }
 
 cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        int* sweeps_done, int* host_counter, int* dev_counter,
-                        cudaStream_t st) {
+                        unsigned int* dev_state, cudaStream_t st) {
   cudaError_t err = set_identity(Q, p, st);
   if (err != cudaSuccess) return err;
-  *sweeps_done = 0;
+  err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
   if (p < 2) return cudaSuccess;
   const int pp = p + (p & 1);
-  for (int sw = 0; sw < max_sweeps; ++sw) {
-    err = cudaMemsetAsync(dev_counter, 0, sizeof(int), st);
-    if (err != cudaSuccess) return err;
-    for (int r = 0; r < pp - 1; ++r)
-      k_jacobi_round<<<pp / 2, JT, 0, st>>>(A, p, q, Q, r, pp, tol, dev_counter);
-    count_launches(pp - 1);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    err = cudaMemcpyAsync(host_counter, dev_counter, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (err != cudaSuccess) return err;
-    err = cudaStreamSynchronize(st);
-    if (err != cudaSuccess) return err;
-    *sweeps_done = sw + 1;
-    if (*host_counter == 0) break;
+  if (pp == 2) {
+    // a single pair: one rotation makes it orthogonal; a second launch confirms
+    int* cnt = reinterpret_cast<int*>(dev_state + 2);
+    for (int sw = 0; sw < 2; ++sw) {
+      count_launches(1);
+      k_jacobi_round<<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, cnt);
+    }
+    return cudaGetLastError();
   }
-  return cudaSuccess;
+  // co-resident grid for the cooperative launch (cached per device)
+  static int cached_dev = -1, max_blocks = 0;
+  int dev = 0;
+  err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev != cached_dev) {
+    int per_sm = 0, sms = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_persistent, JT, 0);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    max_blocks = per_sm * sms;
+    cached_dev = dev;
+  }
+  int nblk = pp / 2;
+  if (nblk > max_blocks) nblk = max_blocks;
+  if (nblk < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {&A, &p, &q, &Q, (void*)&pp, &tol, &max_sweeps, &dev_state};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JT), args, 0, st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

@@ -62,6 +62,30 @@ def random_mps(N, d, chi_max, seed, decay=16.0):
     return out
 
 
+def random_isometric_mps(N, d, chi_max, seed, kappa=64.0):
+    """A random MPS at full bond dimension whose bond spectra decay slowly:
+    site i is a Haar-like random isometry Q_i (QR of a complex Gaussian
+    (chi_{i-1} d) x chi_i matrix) times weights exp(-b/kappa) on its right
+    bond, so with kappa = 64 the weight ratio at b = 256 is e^-8 and a cutoff
+    of 1e-10 does not bind before chi_max does.  Used as the saturated start
+    state of the benchmark workload."""
+    rng = np.random.default_rng(seed)
+    chis = [1] + bond_profile(N, d, chi_max) + [1]
+    out = []
+    for i in range(N):
+        a, b = chis[i], chis[i + 1]
+        g = rng.standard_normal((a * d, b, 2))
+        G = g[..., 0] + 1j * g[..., 1]
+        if a * d >= b:
+            Q, _ = np.linalg.qr(G)
+        else:
+            Q, _ = np.linalg.qr(G.conj().T)
+            Q = Q.conj().T
+        w = np.exp(-np.arange(b) / kappa)
+        out.append((Q * (w / np.linalg.norm(w))[None, :]).reshape(a, d, b))
+    return out
+
+
 def flat_band_bath(n_bath, half_bandwidth=1.0, gamma=0.05):
     """Linear discretisation of a flat band of half-bandwidth D: symmetric
     midpoints eps_j = -D + D(2j-1)/N_b, equal couplings V_j = sqrt(2 D Gamma /
