@@ -65,6 +65,16 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded);
 
+/* Tensor-core GEMM (the contraction engine of the library on sm_103a):
+ * C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major with K contiguous
+ * (leading dimensions lda, ldb in elements, multiples of 8, pointers 16-byte
+ * aligned), C fp32 row-major with leading dimension ldc.  Products are exact
+ * in fp32 and accumulated in fp32 in tensor memory.  Serves the dense
+ * contractions of the two-site effective Hamiltonian (App. B).
+ * ITE_ETIMEOUT if a bounded wait inside the kernel ran out. */
+ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
+                           const void* B, long long ldb, float* C, long long ldc);
+
 /* Same result as ite_k_heff, for callers that cannot allocate device memory
  * at call time (cudaMalloc can synchronise the whole device, the process may
  * have given all device memory to another pool, or allocation calls may be

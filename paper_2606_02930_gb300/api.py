@@ -326,3 +326,13 @@ def svd_stats(ctx):
     check(lib.ite_svd_stats(ctx.h, C.byref(splits), C.byref(total), C.byref(mx)), ctx.h)
     return {"splits": splits.value, "sweeps_mean": total.value / max(1, splits.value),
             "sweeps_max": mx.value}
+
+
+def k_gemm_bf16(ctx, A, B, Cout):
+    """Cout[M][N] (fp32) = A[M][K] B[N][K]^T on the tensor cores; A, B bf16
+    CUDA tensors with K contiguous (row strides multiples of 8)."""
+    M, K = A.shape
+    N = B.shape[0]
+    check(lib.ite_k_gemm_bf16(ctx.h, M, N, K, C.c_void_p(A.data_ptr()), A.stride(0),
+                              C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(Cout.data_ptr()),
+                              Cout.stride(0)), ctx.h)

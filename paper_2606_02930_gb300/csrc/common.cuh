@@ -53,6 +53,13 @@ struct GemmArgs {
 };
 cudaError_t zgemm(const GemmArgs& g, cudaStream_t st);
 
+// ---------------------------------------------------------------- tensor cores
+// C[M][N] (fp32, leading dimension ldc) = A[M][K] B[N][K]^T with A, B bf16
+// row-major (K contiguous, leading dimensions lda, ldb: multiples of 8).
+// tcgen05 MMA with TMA-staged tiles; *err is set if a bounded wait ran out.
+cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, float* C,
+                         long long ldc, int M, int N, int K, int* err, cudaStream_t st);
+
 // ---------------------------------------------------------------- MPO mixing
 // Sparse "gather - small matrix - scatter" along the MPO channel and physical
 // indices.  Row k and column j of the small matrix decompose into up to three

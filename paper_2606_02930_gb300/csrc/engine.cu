@@ -1468,6 +1468,20 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   return ITE_OK;
 }
 
+ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
+                           const void* B, long long ldb, float* Cm, long long ldc) {
+  if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N ||
+      lda % 8 || ldb % 8)
+    return ITE_EINVAL;
+  int* err = reinterpret_cast<int*>(ctx->dcounter) + 8;
+  CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  CK(tc_gemm_bf16(A, lda, B, ldb, Cm, ldc, M, N, K, err, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
+  return ITE_OK;
+}
+
 ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded) {

@@ -1,0 +1,317 @@
+// Tensor-core GEMM on sm_103a with the fifth-generation MMA (tcgen05):
+//   C[M][N] (fp32) = A[M][K] * B[N][K]^T,  A and B bf16, both K-major.
+//
+// One CTA computes a 128 x BN tile.  Warp 0 (one thread) streams A and B
+// tiles of 64 K-elements into shared memory with TMA (128-byte swizzle) through
+// a ring of STAGES buffers; warp 1 (one thread) issues tcgen05.mma (M = 128,
+// N = BN, K = 16 per instruction) that accumulate in tensor memory; each MMA
+// group's completion frees its ring slot through tcgen05.commit.  After the
+// last group, all four warps read the accumulator out of TMEM
+// (tcgen05.ld 32x32b: warp w owns rows 32w..32w+31) and store fp32 to C.
+//
+// Every wait on an mbarrier is bounded.  A wait that runs out sets an error
+// word, the block stops issuing work, drains (again bounded) the copies and
+// MMAs it already issued, frees its TMEM and returns; the host reports
+// ITE_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace ite {
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;                 // bf16 elements per 128-byte swizzle row
+constexpr int TC_STAGES = 4;
+constexpr unsigned long long kSpinLimit = 1ull << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (unsigned long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major bf16 tile in the 128-byte
+// swizzle layout written by TMA: rows of 128 bytes, 8-row groups 1024 bytes
+// apart (stride byte offset), leading byte offset unused, descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor: fp32 accumulate, bf16 A and B, both
+// K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t bf16_idesc(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               float* __restrict__ C, int M, int N, int K, long long ldc, int* err) {
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
+  constexpr uint32_t B_BYTES = BN * TC_BK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte alignment for the 128-byte swizzle pattern
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + TC_STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * B_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accb = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  __shared__ int s_fail, s_issued_tma, s_issued_mma;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
+  const int nk = (K + TC_BK - 1) / TC_BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_issued_tma = 0;
+    s_issued_mma = 0;
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // ---- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (kb >= TC_STAGES && !mbar_wait(&empty[s], ((kb / TC_STAGES) + 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kb * TC_BK, m0);
+      tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kb * TC_BK, n0);
+      s_issued_tma = kb + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = bf16_idesc(BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk)
+        mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+      s_issued_mma = kb + 1;
+    }
+    mma_commit(accb);
+  }
+  __syncthreads();
+  // ---- epilogue: every warp waits for the accumulator
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0) ? 1 : 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool failed = s_fail != 0;
+  if (ok && !failed) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      float v[32];
+      tmem_ld32(tbase + c * 32, v);
+      if (row < M) {
+        float* crow = C + (long long)row * ldc + n0 + c * 32;
+        const int lim = N - (n0 + c * 32);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < lim) crow[i] = v[i];
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+  }
+  // ---- drain (bounded) copies this block issued that no MMA consumed
+  if (threadIdx.x == 0 && (!ok || failed)) {
+    for (int kb = s_issued_mma; kb < s_issued_tma; ++kb)
+      mbar_wait(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mutex;
+
+cudaError_t get_encoder() {
+  std::lock_guard<std::mutex> lock(g_encode_mutex);
+  if (g_encode) return cudaSuccess;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return cudaSuccess;
+}
+
+// 2-D bf16 tensor map: `rows` rows of `cols` elements (row stride ld
+// elements), box of box_rows x 64 elements, 128-byte swizzle, zero fill.
+cudaError_t make_map(CUtensorMap* map, const void* base, long long rows, long long cols,
+                     long long ld, int box_rows) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || cols < 1 || rows < 1)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN>
+size_t smem_bytes() {
+  return 1024 + TC_STAGES * (TC_BM * TC_BK * 2 + BN * TC_BK * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+}
+
+template <int BN>
+cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int M, int N, int K,
+                   long long ldc, int* err, cudaStream_t st) {
+  static bool attr_done = false;
+  const size_t sm = smem_bytes<BN>();
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM);
+  count_launches(1);
+  k_tc_gemm_bf16<BN><<<grid, TC_THREADS, sm, st>>>(ma, mb, C, M, N, K, ldc, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, float* C,
+                         long long ldc, int M, int N, int K, int* err, cudaStream_t st) {
+  if (M < 1 || N < 1 || K < 1) return cudaSuccess;
+  if (M > 65535 * TC_BM) return cudaErrorInvalidValue;
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  const int bn = (N <= 64) ? 64 : 128;
+  CUtensorMap ma, mb;
+  e = make_map(&ma, A, M, K, lda, TC_BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(&mb, B, N, K, ldb, bn);
+  if (e != cudaSuccess) return e;
+  if (bn == 64) return launch<64>(ma, mb, C, M, N, K, ldc, err, st);
+  return launch<128>(ma, mb, C, M, N, K, ldc, err, st);
+}
+
+}  // namespace ite
