@@ -70,10 +70,23 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
  * (leading dimensions lda, ldb in elements, multiples of 8, pointers 16-byte
  * aligned), C fp32 row-major with leading dimension ldc.  Products are exact
  * in fp32 and accumulated in fp32 in tensor memory.  Serves the dense
- * contractions of the two-site effective Hamiltonian (App. B).
+ * contractions of the two-site effective Hamiltonian (App. B).  flags bit 0
+ * selects 32-wide K tiles (64-byte swizzle) instead of 64-wide (128-byte).
  * ITE_ETIMEOUT if a bounded wait inside the kernel ran out. */
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
-                           const void* B, long long ldb, float* C, long long ldc);
+                           const void* B, long long ldb, float* C, long long ldc, int flags);
+
+/* Complex GEMM C = alpha op(A) op(B) + beta C in FP64, the contraction
+ * primitive of every environment and two-site product.  Element (i,k) of A
+ * is A[i sAm + k sAk] (conjugated if conjA), element (k,j) of B is
+ * B[k sBk + j sBn]; C is row-major with leading dimension ldc (complex
+ * units).  mode 0: native FP64 arithmetic.  mode 1: FP64-class accuracy from
+ * the bf16 tensor cores by exact 7-bit slicing of A and B (error below about
+ * K 2^-48 max|A row| max|B column|).  alpha, beta may be NULL (1, 0). */
+ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double* A, long long sAm,
+                       long long sAk, int conjA, const double* B, long long sBk, long long sBn,
+                       int conjB, double* C, long long ldc, const double alpha[2],
+                       const double beta[2]);
 
 /* Same result as ite_k_heff, for callers that cannot allocate device memory
  * at call time (cudaMalloc can synchronise the whole device, the process may

@@ -80,7 +80,9 @@ SIGNATURES = {
     "ite_k_heff_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _pd, _vp, _pd]),
     "ite_k_local_solve": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _d, _d, _i, _d, _pi, _pd]),
     "ite_k_gemm_bf16": (_i, [_vp, _i, _i, _i, _vp, C.c_longlong, _vp, C.c_longlong, _vp,
-                             C.c_longlong]),
+                             C.c_longlong, _i]),
+    "ite_k_zgemm": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _i, _vp,
+                         C.c_longlong, C.c_longlong, _i, _vp, C.c_longlong, _pd, _pd]),
     "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd]),
 }
 

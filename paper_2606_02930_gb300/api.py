@@ -328,11 +328,26 @@ def svd_stats(ctx):
             "sweeps_max": mx.value}
 
 
-def k_gemm_bf16(ctx, A, B, Cout):
+def k_gemm_bf16(ctx, A, B, Cout, k_tile=64):
     """Cout[M][N] (fp32) = A[M][K] B[N][K]^T on the tensor cores; A, B bf16
     CUDA tensors with K contiguous (row strides multiples of 8)."""
     M, K = A.shape
     N = B.shape[0]
     check(lib.ite_k_gemm_bf16(ctx.h, M, N, K, C.c_void_p(A.data_ptr()), A.stride(0),
                               C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(Cout.data_ptr()),
-                              Cout.stride(0)), ctx.h)
+                              Cout.stride(0), 1 if k_tile == 32 else 0), ctx.h)
+
+
+def k_zgemm(ctx, A, B, Cout, mode=1, conjA=False, conjB=False, alpha=1.0, beta=0.0, transA=False,
+            transB=False):
+    """Cout = alpha op(A) op(B) + beta Cout for complex128 CUDA tensors; op is
+    an optional transpose (by strides) and conjugation.  mode 0: native FP64,
+    mode 1: tensor-core emulation."""
+    M, K = (A.shape[1], A.shape[0]) if transA else (A.shape[0], A.shape[1])
+    N = B.shape[0] if transB else B.shape[1]
+    sAm, sAk = (A.stride(1), A.stride(0)) if transA else (A.stride(0), A.stride(1))
+    sBk, sBn = (B.stride(1), B.stride(0)) if transB else (B.stride(0), B.stride(1))
+    a, b = _cpair(alpha), _cpair(beta)
+    check(lib.ite_k_zgemm(ctx.h, mode, M, N, K, C.c_void_p(A.data_ptr()), sAm, sAk,
+                          1 if conjA else 0, C.c_void_p(B.data_ptr()), sBk, sBn, 1 if conjB else 0,
+                          C.c_void_p(Cout.data_ptr()), Cout.stride(0), _dptr(a), _dptr(b)), ctx.h)

@@ -57,8 +57,17 @@ cudaError_t zgemm(const GemmArgs& g, cudaStream_t st);
 // C[M][N] (fp32, leading dimension ldc) = A[M][K] B[N][K]^T with A, B bf16
 // row-major (K contiguous, leading dimensions lda, ldb: multiples of 8).
 // tcgen05 MMA with TMA-staged tiles; *err is set if a bounded wait ran out.
+// bk = 64 (128-byte swizzle tiles) or 32 (64-byte swizzle tiles).
 cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, float* C,
-                         long long ldc, int M, int N, int K, int* err, cudaStream_t st);
+                         long long ldc, int M, int N, int K, int* err, cudaStream_t st,
+                         int bk = 64);
+
+// FP64-accurate complex GEMM on the bf16 tensor cores (exact 7-bit slicing,
+// see tc_zgemm.cu): same contract as zgemm; scratch of at least
+// zgemm_emu_scratch_bytes(M, N, K) bytes; *err set if a bounded wait ran out.
+size_t zgemm_emu_scratch_bytes(int M, int N, int K);
+cudaError_t zgemm_emu(const GemmArgs& g, void* scratch, size_t scratch_bytes, int* err,
+                      cudaStream_t st);
 
 // ---------------------------------------------------------------- MPO mixing
 // Sparse "gather - small matrix - scatter" along the MPO channel and physical

@@ -71,7 +71,7 @@ struct ite_ctx_s {
   std::string err;
   size_t bytes = 0;
   // workspace
-  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env;
+  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu;
   GmresState* gm = nullptr;
   double* dscal = nullptr;     // device scalars
   cplx* dcplx = nullptr;       // device complex scalars
@@ -805,7 +805,8 @@ void ite_ctx_destroy(ite_ctx ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
-                 &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env};
+                 &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
+                 &ctx->ws_emu};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
@@ -1469,16 +1470,45 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
 }
 
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
-                           const void* B, long long ldb, float* Cm, long long ldc) {
+                           const void* B, long long ldb, float* Cm, long long ldc, int flags) {
   if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N ||
       lda % 8 || ldb % 8)
     return ITE_EINVAL;
   int* err = reinterpret_cast<int*>(ctx->dcounter) + 8;
   CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-  CK(tc_gemm_bf16(A, lda, B, ldb, Cm, ldc, M, N, K, err, ctx->stream));
+  CK(tc_gemm_bf16(A, lda, B, ldb, Cm, ldc, M, N, K, err, ctx->stream, (flags & 1) ? 32 : 64));
   CK(cudaMemcpyAsync(&ctx->hr->counter, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
   if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
+  return ITE_OK;
+}
+
+ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double* A, long long sAm,
+                       long long sAk, int conjA, const double* B, long long sBk, long long sBn,
+                       int conjB, double* Cm, long long ldc, const double alpha[2],
+                       const double beta[2]) {
+  if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || (mode != 0 && mode != 1))
+    return ITE_EINVAL;
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.batch = 1;
+  g.A = (const cplx*)A; g.sAm = sAm; g.sAk = sAk; g.sAb = 0; g.conjA = conjA != 0;
+  g.B = (const cplx*)B; g.sBk = sBk; g.sBn = sBn; g.sBb = 0; g.conjB = conjB != 0;
+  g.C = (cplx*)Cm; g.ldc = ldc; g.sCb = 0;
+  g.alpha = alpha ? C(alpha[0], alpha[1]) : C(1);
+  g.beta = beta ? C(beta[0], beta[1]) : C(0);
+  g.Z = nullptr; g.gamma = C(0);
+  if (mode == 0) {
+    CK(zgemm(g, ctx->stream));
+    return sync(ctx);
+  }
+  const size_t need = zgemm_emu_scratch_bytes(M, N, K);
+  CS(buf_ensure(ctx, ctx->ws_emu, need));
+  int* err = reinterpret_cast<int*>(ctx->dcounter) + 9;
+  CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  CK(zgemm_emu(g, ctx->ws_emu.p, ctx->ws_emu.n, err, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "emulated GEMM wait ran out");
   return ITE_OK;
 }
 

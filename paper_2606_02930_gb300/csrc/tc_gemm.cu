@@ -21,115 +21,17 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace ite {
 namespace {
 
+using namespace tc;
+
 constexpr int TC_THREADS = 128;
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;                 // bf16 elements per 128-byte swizzle row
 constexpr int TC_STAGES = 4;
-constexpr unsigned long long kSpinLimit = 1ull << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; returns false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned long long i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major bf16 tile in the 128-byte
-// swizzle layout written by TMA: rows of 128 bytes, 8-row groups 1024 bytes
-// apart (stride byte offset), leading byte offset unused, descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// kind::f16 instruction descriptor: fp32 accumulate, bf16 A and B, both
-// K-major, M = 128, N = bn.
-__host__ __device__ constexpr uint32_t bf16_idesc(int bn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
-         ((uint32_t)(TC_BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <int BN>
+template <int BN, int TC_BK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                float* __restrict__ C, int M, int N, int K, long long ldc, int* err) {
@@ -199,7 +101,7 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 16; ++kk)
-        mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+        mma_bf16(tmem, kmajor_desc<TC_BK>(a0 + kk * 32), kmajor_desc<TC_BK>(b0 + kk * 32), idesc,
                  (kb > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&empty[s]);
       s_issued_mma = kb + 1;
@@ -261,57 +163,70 @@ cudaError_t get_encoder() {
 // 2-D bf16 tensor map: `rows` rows of `cols` elements (row stride ld
 // elements), box of box_rows x 64 elements, 128-byte swizzle, zero fill.
 cudaError_t make_map(CUtensorMap* map, const void* base, long long rows, long long cols,
-                     long long ld, int box_rows) {
+                     long long ld, int box_rows, int bk) {
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || cols < 1 || rows < 1)
     return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN>
+template <int BN, int BK>
 size_t smem_bytes() {
-  return 1024 + TC_STAGES * (TC_BM * TC_BK * 2 + BN * TC_BK * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+  return 1024 + TC_STAGES * (TC_BM * BK * 2 + BN * BK * 2) + (2 * TC_STAGES + 1) * 8 + 16;
 }
 
-template <int BN>
+template <int BN, int BK>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int M, int N, int K,
                    long long ldc, int* err, cudaStream_t st) {
   static bool attr_done = false;
-  const size_t sm = smem_bytes<BN>();
+  const size_t sm = smem_bytes<BN, BK>();
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_bf16<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM);
   count_launches(1);
-  k_tc_gemm_bf16<BN><<<grid, TC_THREADS, sm, st>>>(ma, mb, C, M, N, K, ldc, err);
+  k_tc_gemm_bf16<BN, BK><<<grid, TC_THREADS, sm, st>>>(ma, mb, C, M, N, K, ldc, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t make_digit_map(CUtensorMap* map, const void* base, long long rows, long long cols,
+                           int box_rows) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  return make_map(map, base, rows, cols, cols, box_rows, 32);
+}
+
 cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, float* C,
-                         long long ldc, int M, int N, int K, int* err, cudaStream_t st) {
+                         long long ldc, int M, int N, int K, int* err, cudaStream_t st, int bk) {
   if (M < 1 || N < 1 || K < 1) return cudaSuccess;
   if (M > 65535 * TC_BM) return cudaErrorInvalidValue;
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
   const int bn = (N <= 64) ? 64 : 128;
+  if (bk != 64 && bk != 32) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  e = make_map(&ma, A, M, K, lda, TC_BM);
+  e = make_map(&ma, A, M, K, lda, TC_BM, bk);
   if (e != cudaSuccess) return e;
-  e = make_map(&mb, B, N, K, ldb, bn);
+  e = make_map(&mb, B, N, K, ldb, bn, bk);
   if (e != cudaSuccess) return e;
-  if (bn == 64) return launch<64>(ma, mb, C, M, N, K, ldc, err, st);
-  return launch<128>(ma, mb, C, M, N, K, ldc, err, st);
+  if (bk == 32) {
+    if (bn == 64) return launch<64, 32>(ma, mb, C, M, N, K, ldc, err, st);
+    return launch<128, 32>(ma, mb, C, M, N, K, ldc, err, st);
+  }
+  if (bn == 64) return launch<64, 64>(ma, mb, C, M, N, K, ldc, err, st);
+  return launch<128, 64>(ma, mb, C, M, N, K, ldc, err, st);
 }
 
 }  // namespace ite

@@ -18,14 +18,15 @@ def api():
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 64, 16), (256, 256, 512), (300, 200, 136),
                                    (1, 1, 8), (77, 130, 1000), (2560, 1024, 512), (1024, 256, 2560)])
-def test_tc_gemm_bf16(api, M, N, K):
+@pytest.mark.parametrize("k_tile", [64, 32])
+def test_tc_gemm_bf16(api, M, N, K, k_tile):
     import torch
     ctx = api.ctx_create(0)
     g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
     B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
     Cm = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
-    api.k_gemm_bf16(ctx, A, B, Cm)
+    api.k_gemm_bf16(ctx, A, B, Cm, k_tile)
     a = A.double().cpu()
     b = B.double().cpu()
     exact = (a @ b.T).numpy()
