@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
+    ap.add_argument("--precision", choices=["fp64", "fp64_tc"], default="fp64_tc",
+                    help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores")
     ap.add_argument("--only", choices=["heff", "split"], default=None,
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
     return ap.parse_args()
@@ -203,10 +205,12 @@ def run_ours(args, rank, world, local_rank):
     psi = api.mps_create(ctx, A0, CHI)
     nodes = api.grid_geometric(TAU0, TAU_MAX, K_GRID)
     state = {"k": 0, "s": api.energy(ctx, H, psi)}
+    opts = api.solver_opts(precision=args.precision)
 
     def one_step(p):
         k = state["k"] % K_GRID
-        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], "be", state["s"], CHI, CUTOFF)
+        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], "be", state["s"], CHI, CUTOFF,
+                                 opts)
         state["k"] += 1
         state["s"] = info["energy"]
         return info
@@ -282,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_SITES, "chi_max": CHI, "cutoff": CUTOFF,
-                       "scheme": "backward_euler", "precision": "fp64",
+                       "scheme": "backward_euler", "precision": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state 134 MB + environments 0.7 GB per chain)"},
             "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,

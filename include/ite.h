@@ -69,8 +69,11 @@ typedef enum {
  * first-order A-stable (and L-stable) implicit step, R(z) = 1/(1+z). */
 typedef enum { ITE_BACKWARD_EULER = 0, ITE_TRAPEZOID = 1 } ite_scheme;
 
-/* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere. */
-typedef enum { ITE_FP64 = 0 } ite_precision;
+/* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere on the
+ * FP64 pipes.  ITE_FP64_TC: the same algorithm, with every large contraction
+ * computed to FP64-class accuracy on the bf16 tensor cores by exact slicing
+ * (ite_k_zgemm mode 1); everything else stays FP64. */
+typedef enum { ITE_FP64 = 0, ITE_FP64_TC = 1 } ite_precision;
 
 /* Spectrum shift s of each step.  FIXED: the caller's value.  CURRENT_ENERGY:
  * s_k = <psi_{k-1}|H|psi_{k-1}> (App. D: shift by the energy of the new
@@ -88,7 +91,7 @@ typedef struct {
   double local_tol;   /* stop GMRES at |r|/|B| <= local_tol (0: fixed effort)  */
   double sweep_tol;   /* stop sweeping at 1-|<x_s|x_{s-1}>| < tol (0: fixed)   */
   int fit_sweeps;     /* sweeps of the trapezoid right-hand-side fit (1)       */
-  int precision;      /* ite_precision (ITE_FP64)                              */
+  int precision;      /* ite_precision (ITE_FP64 or ITE_FP64_TC)               */
 } ite_solver_opts;
 
 /* Per-step report. */

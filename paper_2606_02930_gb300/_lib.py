@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(_HERE, "libite.so")
 
 ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA = range(7)
 ITE_BACKWARD_EULER, ITE_TRAPEZOID = 0, 1
-ITE_FP64 = 0
+ITE_FP64, ITE_FP64_TC = 0, 1
 ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
 STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",
                 4: "ITE_ENOTCONV", 5: "ITE_ETIMEOUT", 6: "ITE_ECUDA"}

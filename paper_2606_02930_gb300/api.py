@@ -31,11 +31,16 @@ def _c128(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
 
 
-def solver_opts(krylov_dim=10, sweeps=1, local_tol=0.0, sweep_tol=0.0, fit_sweeps=1):
+PRECISIONS = {"fp64": L.ITE_FP64, "fp64_tc": L.ITE_FP64_TC}
+
+
+def solver_opts(krylov_dim=10, sweeps=1, local_tol=0.0, sweep_tol=0.0, fit_sweeps=1,
+                precision="fp64"):
     o = L.ite_solver_opts()
     lib.ite_solver_opts_default(C.byref(o))
     o.krylov_dim, o.sweeps, o.local_tol = krylov_dim, sweeps, local_tol
     o.sweep_tol, o.fit_sweeps = sweep_tol, fit_sweeps
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return o
 
 

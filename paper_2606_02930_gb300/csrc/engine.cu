@@ -42,6 +42,7 @@ constexpr double kBreakdownRel = 1e-14;  // GMRES breakdown threshold (relative 
 constexpr double kEps = 2.220446049250313e-16;
 constexpr int kJacobiSweeps = 30;
 constexpr int kMaxKrylov = 32;
+constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay native
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -78,6 +79,7 @@ struct ite_ctx_s {
   cplx* partial = nullptr;     // reduction partials
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
+  int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
   int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
@@ -220,6 +222,14 @@ ite_status gemm(ite_ctx ctx, int M, int N, int K, const cplx* A, long long sAm, 
   g.B = B; g.sBk = sBk; g.sBn = sBn; g.sBb = sBb; g.conjB = conjB;
   g.C = Cm; g.ldc = ldc; g.sCb = sCb;
   g.alpha = alpha; g.beta = beta; g.Z = Z; g.gamma = gamma;
+  // large contractions on the tensor cores when the step asks for it; small
+  // ones (edge bonds) stay on the FP64 pipe where launch latency dominates
+  if (ctx->gemm_mode == 1 && (double)M * N * K >= kEmuMinWork && K >= 16) {
+    CS(buf_ensure(ctx, ctx->ws_emu, zgemm_emu_scratch_bytes(M, N, K)));
+    CK(zgemm_emu(g, ctx->ws_emu.p, ctx->ws_emu.n, reinterpret_cast<int*>(ctx->dcounter) + 10,
+                 ctx->stream));
+    return ITE_OK;
+  }
   CK(zgemm(g, ctx->stream));
   return ITE_OK;
 }
@@ -356,8 +366,11 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
   if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
+  if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
   ctx->jacobi_sweeps_total += ctx->hr->pad;
   ctx->jacobi_splits += 1;
   ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
@@ -953,11 +966,17 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
   if (!(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(shift) || !(cutoff >= 0.0) ||
       chi_max < 1 || chi_max > psi->chi_cap || o.krylov_dim < 1 || o.krylov_dim > kMaxKrylov ||
       o.sweeps < 1 || o.fit_sweeps < 1 || (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID) ||
-      o.precision != ITE_FP64 || psi->N < 2)
+      (o.precision != ITE_FP64 && o.precision != ITE_FP64_TC) || psi->N < 2)
     return fail(ctx, ITE_EINVAL, "invalid step arguments");
   CS(ensure_work(ctx, psi));
   CS(ensure_workspace(ctx, H, psi->cap, psi->d, o.krylov_dim));
   Scope step_scope(ctx, P_STEP);
+  struct ModeGuard {
+    ite_ctx c;
+    ~ModeGuard() { c->gemm_mode = 0; }
+  } mode_guard{ctx};
+  ctx->gemm_mode = o.precision == ITE_FP64_TC ? 1 : 0;
+  CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
   SweepStats st;
   ite_mps x = psi->work_x, bm = psi;
   double c;

@@ -135,31 +135,64 @@ def test_anderson_fixed_mode(api, ctx, scheme):
         assert infid(ost, gst) <= TOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
 @pytest.mark.parametrize("scheme", ["be", "tr"])
-def test_saturated_input_one_step(api, ctx, scheme):
-    # a full-bond-dimension random input (chi = 64 in the bulk of N = 20)
+def test_saturated_input_one_step(api, ctx, scheme, precision):
+    # a full-bond-dimension random input (chi = 64 in the bulk of N = 20); in
+    # fp64_tc mode the bulk contractions run on the tensor cores
     N, chi = 20, 64
     Ws = ompo.heisenberg_mpo(N)
     H = api.mpo_create_heisenberg(ctx, N)
-    A = inputs.random_mps(N, 2, chi, 2001)
+    A = inputs.random_isometric_mps(N, 2, chi, 2001)
     pairs = run_pair(api, ctx, Ws, H, A, np.array([0.0, 0.5, 3.0]), scheme, chi, 1e-10,
-                     shift_mode="energy")
+                     shift_mode="energy", opts=api.solver_opts(precision=precision))
     for ost, oinfo, gst, ginfo in pairs:
         assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
         assert infid(ost, gst) <= TOL
 
 
-def test_workload_size_step_invariants(api, ctx):
+@pytest.mark.parametrize("scheme", ["be", "tr"])
+def test_tensor_core_mode_matches_oracle_chi128(api, ctx, scheme):
+    # N = 16, chi = 128 (the bulk two-site blocks are 256 x 256): one step in
+    # fp64_tc mode against the oracle, FP64 bar
+    N, chi = 16, 128
+    Ws = ompo.heisenberg_mpo(N)
+    H = api.mpo_create_heisenberg(ctx, N)
+    A = inputs.random_isometric_mps(N, 2, chi, 2002)
+    pairs = run_pair(api, ctx, Ws, H, A, np.array([0.0, 0.2]), scheme, chi, 1e-10,
+                     shift_mode="energy", opts=api.solver_opts(precision="fp64_tc"))
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
+        assert infid(ost, gst) <= TOL
+
+
+@pytest.mark.parametrize("scheme", ["be", "tr"])
+def test_tensor_core_mode_anderson(api, ctx, scheme):
+    nb = 5
+    eps, V = inputs.flat_band_bath(nb)
+    Ws = ompo.anderson_mpo(-0.15, 0.3, eps, V)
+    H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
+    A = inputs.random_isometric_mps(nb + 1, 4, 64, 3001)
+    pairs = run_pair(api, ctx, Ws, H, A, np.array([0.0, 0.1, 1.0]), scheme, 64, 1e-14,
+                     shift_mode="energy", opts=api.solver_opts(precision="fp64_tc"))
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
+        assert infid(ost, gst) <= TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_workload_size_step_invariants(api, ctx, precision):
     # N = 64, chi_max = 256, cutoff 1e-10, saturated random input: one backward
     # Euler step with a certified lower bound s <= E0 must not raise the energy
     # (R_BE positive and decreasing on the spectrum) and must not grow the norm.
     N, chi = 64, 256
     H = api.mpo_create_heisenberg(ctx, N)
-    A = inputs.random_mps(N, 2, chi, 2000)
+    A = inputs.random_isometric_mps(N, 2, chi, 2000)
     psi = api.mps_create(ctx, A, chi)
     e_in = api.energy(ctx, H, psi)
     s = -0.75 * (N - 1)
-    info = api.implicit_step(ctx, H, psi, 0.1, "be", s, chi, 1e-10)
+    info = api.implicit_step(ctx, H, psi, 0.1, "be", s, chi, 1e-10,
+                             api.solver_opts(precision=precision))
     assert info["energy"] < e_in
     assert abs(info["energy"] - api.energy(ctx, H, psi)) < 1e-10 * abs(info["energy"])
     chis, _ = psi.bond_dims()
