@@ -333,7 +333,8 @@ def run_only(args):
         X = torch.from_numpy(np.tensordot(A[1], A[2], axes=([2], [0])).reshape(512, 512)).to("cuda")
         left = torch.empty(512 * 512, dtype=torch.complex128, device="cuda")
         right = torch.empty_like(left)
-        call = lambda: api.k_split(ctx, X, 512, 512, CHI, CUTOFF, True, left, right)
+        tc = args.precision == "fp64_tc"
+        call = lambda: api.k_split(ctx, X, 512, 512, CHI, CUTOFF, True, left, right, tc=tc)
         flops = 0.0
     for _ in range(args.warmup):
         call()

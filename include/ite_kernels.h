@@ -60,10 +60,14 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
  * writes left = U_r (m x r) and right = S_r V_r^dag (r x n); otherwise
  * left = U_r S_r and right = V_r^dag.  left needs m*min(m,n) and right
  * min(m,n)*n complex entries of room.  sigma (device, may be NULL) receives
- * the min(m,n) singular values in descending order. */
+ * the min(m,n) singular values in descending order.  flags bit 0 selects the
+ * tensor-core mode: when min(m,n) is 96 or more, the FP64 Jacobi is
+ * preconditioned by fp32 Jacobi (rotations made unitary to FP64 precision by
+ * Newton-Schulz steps) and the GEMMs run on the tensor cores.  flags bit 1
+ * runs that preconditioned algorithm with FP64-pipe GEMMs. */
 ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
                        int centre_right, double* left, double* right, double* sigma, int* rank,
-                       double* discarded);
+                       double* discarded, int flags);
 
 /* Tensor-core GEMM (the contraction engine of the library on sm_103a):
  * C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major with K contiguous

@@ -83,7 +83,7 @@ SIGNATURES = {
                              C.c_longlong, _i]),
     "ite_k_zgemm": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _i, _vp,
                          C.c_longlong, C.c_longlong, _i, _vp, C.c_longlong, _pd, _pd]),
-    "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd]),
+    "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd, _i]),
 }
 
 

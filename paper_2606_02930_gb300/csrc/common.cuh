@@ -155,6 +155,20 @@ cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double t
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
                      int chi_max, double cutoff, double weight_floor, double tie_rel,
                      int* rank_out, double* discarded_out, cudaStream_t st);
+// sort given singular values descending and apply the truncation rule
+cudaError_t sort_rank(const double* sigma, int p, int* perm, double* sorted_sigma, int chi_max,
+                      double cutoff, double weight_floor, double tie_rel, int* rank_out,
+                      double* discarded_out, cudaStream_t st);
+// fp32 one-sided Jacobi (same contract as jacobi_rows)
+cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
+                            unsigned int* dev_state, cudaStream_t st);
+// mixed-precision SVD pieces (svd_mixed.cu)
+cudaError_t mixsvd_to_f32(const cplx* X, int m, int n, bool ct, float2* out, cudaStream_t st);
+cudaError_t mixsvd_q32_to_w(const float2* Q, int p, cplx* W, cudaStream_t st);
+cudaError_t mixsvd_gather(const cplx* W, const int* perm, int p, int r, bool ct, cplx* out,
+                          cudaStream_t st);
+cudaError_t mixsvd_gather_rows(const cplx* B, const int* perm, int q, int r, bool ct, cplx* out,
+                               cudaStream_t st);
 // write the two factors of a split (see engine for the four cases)
 cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma,
                      const int* perm, int r, int p, int q, bool transposed, bool centre_right,

@@ -43,6 +43,9 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr int kJacobiSweeps = 30;
 constexpr int kMaxKrylov = 32;
 constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay native
+constexpr int kMixedSvdMinP = 96;        // isometry dimension from which the mixed SVD is used
+constexpr int kMixedSweeps = 12;         // fp32 Jacobi sweeps of the mixed SVD (cap)
+constexpr int kPolarSteps = 2;           // Newton-Schulz steps making the fp32 vectors unitary
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -72,7 +75,8 @@ struct ite_ctx_s {
   std::string err;
   size_t bytes = 0;
   // workspace
-  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu;
+  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu,
+      ws_mix;
   GmresState* gm = nullptr;
   double* dscal = nullptr;     // device scalars
   cplx* dcplx = nullptr;       // device complex scalars
@@ -80,6 +84,7 @@ struct ite_ctx_s {
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
   int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
+  bool mixed_svd = false;      // mixed-precision SVD with native GEMMs (kernel-level tests)
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
   int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
@@ -340,11 +345,106 @@ ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, 
               (long long)d * chr);
 }
 
+// Mixed-precision truncated SVD (tensor-core mode).  The same one-sided
+// Jacobi as the FP64 path, on the same p = min(m, n) vectors (rows of M, or of
+// M^H when m > n), preconditioned in fp32: fp32 Jacobi gives rotations Q32;
+// two Newton-Schulz steps W <- W (3 I - W^H W) / 2 turn W0 = Q32^H into a
+// unitary matrix to FP64 precision; B = W^H A then has rows that are already
+// orthogonal to fp32 accuracy, and FP64 Jacobi on B finishes in a few sweeps.
+// With Q64 B = B_rot, the rotation of A is Q = Q64 W^H, and the factors are
+// emitted exactly as in the FP64 path.  The products are tensor-core GEMMs
+// with FP64-class accuracy.
+ite_status split_mixed(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
+                       bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
+                       double* sigma_out) {
+  const bool tr = m > n;
+  const int p = tr ? n : m, q = tr ? m : n;
+  const long long pp = (long long)p * p;
+  // carve the workspace with every piece on a 256-byte boundary
+  const size_t sizes[] = {(size_t)pp * sizeof(cplx), (size_t)pp * sizeof(cplx),
+                          (size_t)pp * sizeof(cplx), (size_t)pp * sizeof(cplx),
+                          (size_t)p * q * sizeof(cplx), (size_t)p * q * sizeof(float2),
+                          (size_t)pp * sizeof(float2)};
+  const int npieces = (int)(sizeof(sizes) / sizeof(sizes[0]));
+  size_t need = 0;
+  for (int k = 0; k < npieces; ++k) need += (sizes[k] + 255) & ~size_t(255);
+  CS(buf_ensure(ctx, ctx->ws_mix, need));
+  char* pieces[8];
+  {
+    char* at = P<char>(ctx->ws_mix);
+    for (int k = 0; k < npieces; ++k) {
+      pieces[k] = at;
+      at += (sizes[k] + 255) & ~size_t(255);
+    }
+  }
+  cplx* W = reinterpret_cast<cplx*>(pieces[0]);
+  cplx* Wn = reinterpret_cast<cplx*>(pieces[1]);
+  cplx* T = reinterpret_cast<cplx*>(pieces[2]);
+  cplx* Q64 = reinterpret_cast<cplx*>(pieces[3]);
+  cplx* Bm = reinterpret_cast<cplx*>(pieces[4]);
+  float2* A32 = reinterpret_cast<float2*>(pieces[5]);
+  float2* Q32 = reinterpret_cast<float2*>(pieces[6]);
+  unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
+  // 1. fp32 Jacobi on the rows of A = M (or M^H)
+  CK(mixsvd_to_f32(X, m, n, tr, A32, ctx->stream));
+  CK(jacobi_rows_f32(A32, p, q, Q32, kMixedSweeps, (float)std::max(1e-6, q * 1.1920929e-7), jstate,
+                     ctx->stream));
+  CK(mixsvd_q32_to_w(Q32, p, W, ctx->stream));
+  // 2. unitary W: W <- 1.5 W - 0.5 W (W^H W)
+  for (int it = 0; it < kPolarSteps; ++it) {
+    CS(gemm(ctx, p, p, p, W, 1, p, true, W, p, 1, false, T, p));                         // W^H W
+    CS(gemm(ctx, p, p, p, W, p, 1, false, T, p, 1, false, Wn, p, C(-0.5), C(0), W, C(1.5)));
+    std::swap(W, Wn);
+  }
+  // 3. B = W^H A
+  if (!tr)
+    CS(gemm(ctx, p, n, m, W, 1, p, true, X, n, 1, false, Bm, n));        // W^H M
+  else
+    CS(gemm(ctx, p, m, n, W, 1, p, true, X, 1, n, true, Bm, m));         // W^H M^H
+  // 4. FP64 one-sided Jacobi on the rows of B; the rotation of A is Q64 W^H
+  CK(jacobi_rows(Bm, p, q, Q64, kJacobiSweeps, std::max(1e-15, q * kEps), jstate, ctx->stream));
+  CS(gemm(ctx, p, p, p, Q64, p, 1, false, W, 1, p, true, Wn, p));
+  cplx* Qrot = Wn;
+  // 5. singular values (row norms of the rotated B), order and rank
+  double* small = P<double>(ctx->ws_small);
+  double* sigma = small;
+  double* sorted = small + p;
+  int* perm = reinterpret_cast<int*>(small + 2 * p);
+  int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
+  double* disc_dev = ctx->dscal + 7;
+  CK(svd_rank(Bm, p, q, sigma, perm, sorted, chi_max, cutoff, kWeightFloor, kTieRel, rank_dev,
+              disc_dev, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
+  if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
+  ctx->jacobi_sweeps_total += ctx->hr->pad;
+  ctx->jacobi_splits += 1;
+  ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
+  const int r = ctx->hr->rank;
+  if (r < 1 || r > p) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
+  if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
+  if (sigma_out) CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+  // 6. factors, as in the FP64 path
+  CK(svd_emit(Bm, Qrot, sorted, perm, r, p, q, tr, centre_right, left, right, ctx->stream));
+  *r_out = r;
+  *disc_out = ctx->hr->disc;
+  return ITE_OK;
+}
+
 // Truncated SVD of X (m x n). Writes left (m x r) and right (r x n); returns r.
 ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
                  bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
                  double* sigma_out = nullptr) {
   Scope sc(ctx, P_SVD);
+  if ((ctx->gemm_mode == 1 || ctx->mixed_svd) && std::min(m, n) >= kMixedSvdMinP)
+    return split_mixed(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, r_out, disc_out,
+                       sigma_out);
   cplx* A = P<cplx>(ctx->ws_svdA);
   cplx* Q = P<cplx>(ctx->ws_svdQ);
   const bool tr = m > n;
@@ -819,7 +919,7 @@ void ite_ctx_destroy(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu};
+                 &ctx->ws_emu, &ctx->ws_mix};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
@@ -1533,9 +1633,19 @@ ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double*
 
 ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
                        int centre_right, double* left, double* right, double* sigma, int* rank,
-                       double* discarded) {
+                       double* discarded, int flags) {
   if (!ctx || !X || !left || !right || m < 1 || n < 1 || chi_max < 1 || !(cutoff >= 0.0))
     return ITE_EINVAL;
+  struct ModeGuard {
+    ite_ctx c;
+    ~ModeGuard() {
+      c->gemm_mode = 0;
+      c->mixed_svd = false;
+    }
+  } mode_guard{ctx};
+  ctx->gemm_mode = (flags & 1) ? 1 : 0;
+  ctx->mixed_svd = (flags & 2) != 0;
+  CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
   const long long p = std::min(m, n);
   CS(buf_ensure(ctx, ctx->ws_svdA, (size_t)m * n * sizeof(cplx)));
   CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)p * p * sizeof(cplx)));

@@ -26,70 +26,94 @@ __device__ __forceinline__ int player(int pos, int round, int pp) {
   return pos == 0 ? 0 : ((pos - 1 + round) % (pp - 1)) + 1;
 }
 
+// complex helpers over the real type R (double: FP64 path, float: the
+// approximate FP32 stage of the mixed-precision SVD)
+template <typename R> struct Cx;
+template <> struct Cx<double> { typedef double2 T; };
+template <> struct Cx<float> { typedef float2 T; };
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T cx(R a, R b) {
+  typename Cx<R>::T z;
+  z.x = a;
+  z.y = b;
+  return z;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // One Jacobi rotation on rows u, v of A (and of Q): make the pair orthogonal
 // if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block.
-__device__ void jacobi_pair(cplx* A, int p, int q, cplx* Q, int u, int v, double tol, int* counter) {
+template <typename R>
+__device__ void jacobi_pair(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int u, int v,
+                            R tol, int* counter) {
+  typedef typename Cx<R>::T T;
   if (u > v) { const int t = u; u = v; v = t; }
-  cplx* au = A + (long long)u * q;
-  cplx* av = A + (long long)v * q;
-  double sa = 0.0, sb = 0.0, gr = 0.0, gi = 0.0;
+  T* au = A + (long long)u * q;
+  T* av = A + (long long)v * q;
+  R sa = 0, sb = 0, gr = 0, gi = 0;
   for (int e = threadIdx.x; e < q; e += JT) {
-    const cplx x = au[e], y = av[e];
+    const T x = au[e], y = av[e];
     sa = fma(x.x, x.x, fma(x.y, x.y, sa));
     sb = fma(y.x, y.x, fma(y.y, y.y, sb));
     gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // Re(conj(x) y)
     gi = fma(x.x, y.y, fma(-x.y, y.x, gi));    // Im(conj(x) y)
   }
-  __shared__ double sh[4][JT / 32];
-  __shared__ double rot[4];
-  sa = warp_sum(sa); sb = warp_sum(sb); gr = warp_sum(gr); gi = warp_sum(gi);
+  __shared__ R sh[4][JT / 32];
+  __shared__ R rot[4];
+  sa = warp_sum_t(sa); sb = warp_sum_t(sb); gr = warp_sum_t(gr); gi = warp_sum_t(gi);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) { sh[0][wid] = sa; sh[1][wid] = sb; sh[2][wid] = gr; sh[3][wid] = gi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double al = 0, be = 0, Gr = 0, Gi = 0;
+    R al = 0, be = 0, Gr = 0, Gi = 0;
     for (int w = 0; w < JT / 32; ++w) { al += sh[0][w]; be += sh[1][w]; Gr += sh[2][w]; Gi += sh[3][w]; }
-    const double gabs = hypot(Gr, Gi);
-    double c = 1.0, sr = 0.0, si = 0.0;   // rotation: c, and s*e^{i theta}
-    if (gabs > tol * sqrt(al * be) && gabs > 0.0) {
-      const double zeta = (be - al) / (2.0 * gabs);
-      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      c = 1.0 / sqrt(1.0 + t * t);
-      const double s = c * t;
-      sr = s * Gr / gabs;
-      si = s * Gi / gabs;
+    const R gabs = hypot(Gr, Gi);
+    R c = 1, sr = 0, si = 0;   // rotation: c, and s*e^{i theta}
+    if (gabs > tol * sqrt(al * be) && gabs > R(0)) {
+      const R zeta = (be - al) / (R(2) * gabs);
+      const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+      c = R(1) / sqrt(R(1) + t * t);
+      const R sn = c * t;
+      sr = sn * Gr / gabs;
+      si = sn * Gi / gabs;
       atomicAdd(counter, 1);
     }
-    rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != 0.0 || si != 0.0) ? 1.0 : 0.0;
+    rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != R(0) || si != R(0)) ? R(1) : R(0);
   }
   __syncthreads();
-  const double c = rot[0];
-  const cplx se = cmake(rot[1], rot[2]);      // s e^{i theta}
-  const cplx sec = cconj(se);                  // s e^{-i theta}
-  const bool apply = rot[3] != 0.0;
+  const R c = rot[0], sr = rot[1], si = rot[2];   // se = s e^{i theta}
+  const bool apply = rot[3] != R(0);
   __syncthreads();                             // rot[] is reused by the next pair
   if (!apply) return;
   // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
   for (int e = threadIdx.x; e < q; e += JT) {
-    const cplx x = au[e], y = av[e];
-    au[e] = csub(cscale(x, c), cmul(sec, y));
-    av[e] = cadd(cmul(se, x), cscale(y, c));
+    const T x = au[e], y = av[e];
+    au[e] = cx<R>(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
+    av[e] = cx<R>((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
   }
-  cplx* qu = Q + (long long)u * p;
-  cplx* qv = Q + (long long)v * p;
+  T* qu = Q + (long long)u * p;
+  T* qv = Q + (long long)v * p;
   for (int e = threadIdx.x; e < p; e += JT) {
-    const cplx x = qu[e], y = qv[e];
-    qu[e] = csub(cscale(x, c), cmul(sec, y));
-    qv[e] = cadd(cmul(se, x), cscale(y, c));
+    const T x = qu[e], y = qv[e];
+    qu[e] = cx<R>(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
+    qv[e] = cx<R>((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
   }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(JT)
-k_jacobi_round(cplx* A, int p, int q, cplx* Q, int round, int pp, double tol, int* counter) {
+k_jacobi_round(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int round, int pp, R tol,
+               int* counter) {
   const int k = blockIdx.x;
   const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
   if (u >= p || v >= p) return;
-  jacobi_pair(A, p, q, Q, u, v, tol, counter);
+  jacobi_pair<R>(A, p, q, Q, u, v, tol, counter);
 }
 
 // Grid-wide barrier for a cooperative launch.  st[0] arrivals, st[1]
@@ -128,9 +152,10 @@ __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
 // the counter of the following sweep is cleared by block 0 in round 1 of the
 // current sweep, after every block has passed round 0 (and so has finished
 // reading it two sweeps ago).
+template <typename R>
 __global__ void __launch_bounds__(JT)
-k_jacobi_persistent(cplx* A, int p, int q, cplx* Q, int pp, double tol, int max_sweeps,
-                    unsigned int* st) {
+k_jacobi_persistent(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int pp, R tol,
+                    int max_sweeps, unsigned int* st) {
   const unsigned int nb = gridDim.x;
   int* counters = reinterpret_cast<int*>(st + 2);
   for (int sw = 0; sw < max_sweeps; ++sw) {
@@ -139,13 +164,23 @@ k_jacobi_persistent(cplx* A, int p, int q, cplx* Q, int pp, double tol, int max_
       if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[(sw + 1) & 1] = 0;
       for (int k = blockIdx.x; k < pp / 2; k += nb) {
         const int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
-        if (u < p && v < p) jacobi_pair(A, p, q, Q, u, v, tol, cnt);
+        if (u < p && v < p) jacobi_pair<R>(A, p, q, Q, u, v, tol, cnt);
       }
       if (!grid_barrier(st, nb)) return;
     }
     const int rotations = *((volatile int*)cnt);
     if (blockIdx.x == 0 && threadIdx.x == 0) st[5] = (unsigned int)(sw + 1);
     if (rotations == 0) break;
+  }
+}
+
+template <typename R>
+__global__ void k_identity_t(typename Cx<R>::T* Q, int p) {
+  const long long tot = (long long)p * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / p, j = e - i * p;
+    Q[e] = cx<R>(i == j ? R(1) : R(0), R(0));
   }
 }
 
@@ -306,11 +341,18 @@ cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        unsigned int* dev_state, cudaStream_t st) {
-  cudaError_t err = set_identity(Q, p, st);
-  if (err != cudaSuccess) return err;
-  err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
+template <typename R>
+cudaError_t jacobi_rows_t(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int max_sweeps,
+                          R tol, unsigned int* dev_state, cudaStream_t st) {
+  {
+    long long tot = (long long)p * p;
+    long long g = (tot + 255) / 256;
+    if (g > 1216) g = 1216;
+    if (g < 1) g = 1;
+    count_launches(1);
+    k_identity_t<R><<<(int)g, 256, 0, st>>>(Q, p);
+  }
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (p < 2) return cudaSuccess;
   const int pp = p + (p & 1);
@@ -319,18 +361,18 @@ cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double t
     int* cnt = reinterpret_cast<int*>(dev_state + 2);
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, cnt);
+      k_jacobi_round<R><<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, cnt);
     }
     return cudaGetLastError();
   }
-  // co-resident grid for the cooperative launch (cached per device)
+  // co-resident grid for the cooperative launch (cached per device and type)
   static int cached_dev = -1, max_blocks = 0;
   int dev = 0;
   err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev != cached_dev) {
     int per_sm = 0, sms = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_persistent, JT, 0);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_persistent<R>, JT, 0);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
@@ -342,7 +384,17 @@ cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double t
   if (nblk < 1) return cudaErrorInvalidConfiguration;
   void* args[] = {&A, &p, &q, &Q, (void*)&pp, &tol, &max_sweeps, &dev_state};
   count_launches(1);
-  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JT), args, 0, st);
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent<R>, dim3(nblk), dim3(JT), args, 0, st);
+}
+
+cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
+                        unsigned int* dev_state, cudaStream_t st) {
+  return jacobi_rows_t<double>(A, p, q, Q, max_sweeps, tol, dev_state, st);
+}
+
+cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
+                            unsigned int* dev_state, cudaStream_t st) {
+  return jacobi_rows_t<float>(A, p, q, Q, max_sweeps, tol, dev_state, st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
@@ -351,6 +403,16 @@ cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, doub
   if (p <= 0) return cudaErrorInvalidValue;
   count_launches(1);
   k_row_norms<<<p, JT, 0, st>>>(A, p, q, sigma);
+  count_launches(1);
+  k_sort_rank<<<1, 1024, 0, st>>>(sigma, p, perm, sorted_sigma, chi_max, cutoff, weight_floor,
+                                  tie_rel, rank_out, discarded_out);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_rank(const double* sigma, int p, int* perm, double* sorted_sigma, int chi_max,
+                      double cutoff, double weight_floor, double tie_rel, int* rank_out,
+                      double* discarded_out, cudaStream_t st) {
+  if (p <= 0) return cudaErrorInvalidValue;
   count_launches(1);
   k_sort_rank<<<1, 1024, 0, st>>>(sigma, p, perm, sorted_sigma, chi_max, cutoff, weight_floor,
                                   tie_rel, rank_out, discarded_out);

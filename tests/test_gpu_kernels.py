@@ -193,3 +193,36 @@ def test_local_solve_matches_oracle_gmres(api, ctx, model, N, chi, i):
         assert k == k_ref
         assert rel_err(to_host(X), Xw) < 1e-10
         assert abs(res - res_ref) < 1e-8 * max(res_ref, 1e-6)
+
+
+@pytest.mark.parametrize("m,n,kind", [(128, 128, "decay"), (512, 512, "decay"), (200, 160, "ties"),
+                                      (160, 200, "decay"), (256, 512, "decay")])
+def test_split_tensor_core_mode(api, ctx, m, n, kind):
+    # mixed-precision split (fp32 Jacobi, FP64 polish on the tensor-core GEMMs
+    # and FP64 Jacobi): same rank and truncated product as the oracle's SVD
+    import torch
+    rng = np.random.default_rng(m * 31 + n)
+    p = min(m, n)
+    if kind == "decay":
+        X = _spectrum_matrix(rng, m, n, np.exp(-np.arange(p) / 20.0))
+    else:
+        sv = np.repeat(np.exp(-np.arange(p // 4) / 8.0), 4)
+        X = _spectrum_matrix(rng, m, n, sv)
+    S_ref = np.linalg.svd(X, compute_uv=False)
+    for chi_max, cutoff in ((p, 1e-10), (max(1, p // 2), 1e-10), (max(1, p // 3 + 1), 0.0)):
+        eff = cutoff
+        r_ref, disc_ref = ls.choose_rank(S_ref, chi_max, eff)
+        for centre_right in (True, False):
+            left = to_dev(np.zeros(m * max(m, n)))
+            right = to_dev(np.zeros(max(m, n) * n))
+            r, disc = api.k_split(ctx, to_dev(X), m, n, chi_max, cutoff, centre_right, left, right,
+                                  tc=True)
+            assert r == r_ref
+            assert abs(disc - disc_ref) <= 1e-10 * max(disc_ref, 1e-12) + 1e-15
+            Lh = to_host(left)[: m * r].reshape(m, r)
+            Rh = to_host(right)[: r * n].reshape(r, n)
+            A1, A2, _, _ = ls.split_two_site(X.reshape(m, 1, 1, n), chi_max, eff, centre_right)
+            want = A1.reshape(m, -1) @ A2.reshape(-1, n)
+            assert rel_err(Lh @ Rh, want) < 1e-11
+            iso = Lh if centre_right else Rh.conj().T
+            assert np.abs(iso.conj().T @ iso - np.eye(r)).max() < 1e-12
