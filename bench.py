@@ -329,8 +329,8 @@ def run_only(args):
         call = lambda: api.k_heff(ctx, H, 20, L, R, X, Y)
         flops = 8.0 * (2 * D_MPO * D_SITE ** 2 * CHI ** 3 + 2 * D_MPO ** 2 * D_SITE ** 3 * CHI ** 2)
     else:
-        A = inputs.random_isometric_mps(4, D_SITE, CHI, SEED)
-        X = torch.from_numpy(np.tensordot(A[1], A[2], axes=([2], [0])).reshape(512, 512)).to("cuda")
+        A = inputs.random_isometric_mps(20, D_SITE, CHI, SEED)
+        X = torch.from_numpy(np.tensordot(A[9], A[10], axes=([2], [0])).reshape(512, 512)).to("cuda")
         left = torch.empty(512 * 512, dtype=torch.complex128, device="cuda")
         right = torch.empty_like(left)
         tc = args.precision == "fp64_tc"

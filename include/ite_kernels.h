@@ -60,7 +60,10 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
  * writes left = U_r (m x r) and right = S_r V_r^dag (r x n); otherwise
  * left = U_r S_r and right = V_r^dag.  left needs m*min(m,n) and right
  * min(m,n)*n complex entries of room.  sigma (device, may be NULL) receives
- * the min(m,n) singular values in descending order.  flags bit 0 selects the
+ * min(m,n) values in descending order: the singular values down to a squared
+ * weight of 1e-3 max(cutoff, 1e-25) of the total; below that the rows are
+ * never kept and are left unresolved, so those entries are norms of a mixed
+ * block whose sum of squares alone is exact.  flags bit 0 selects the
  * tensor-core mode: when min(m,n) is 96 or more, the FP64 Jacobi is
  * preconditioned by fp32 Jacobi (rotations made unitary to FP64 precision by
  * Newton-Schulz steps) and the GEMMs run on the tensor cores.  flags bit 1

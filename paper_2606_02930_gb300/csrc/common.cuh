@@ -147,9 +147,12 @@ cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cpl
 // are the rotated vectors).  Q (p x p) receives the accumulated row rotations:
 // on return Q A_in = A_out with mutually orthogonal rows.  Runs as one
 // cooperative launch; dev_state (8 device words) returns the sweeps done in
-// word 5 and a nonzero word 4 if a grid-barrier wait ran out.
+// word 5 and a nonzero word 4 if a grid-barrier wait ran out.  *anorm2
+// (device) is |A|_F^2: pairs of rows whose squared norms are both
+// <= skip_rel |A|_F^2 are left as they are.
 cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        unsigned int* dev_state, cudaStream_t st);
+                        const double* anorm2, double skip_rel, unsigned int* dev_state,
+                        cudaStream_t st);
 // row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
 // by index), and the kept rank by the truncation rule (see engine).
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
@@ -161,7 +164,11 @@ cudaError_t sort_rank(const double* sigma, int p, int* perm, double* sorted_sigm
                       double* discarded_out, cudaStream_t st);
 // fp32 one-sided Jacobi (same contract as jacobi_rows)
 cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
-                            unsigned int* dev_state, cudaStream_t st);
+                            const double* anorm2, double skip_rel, unsigned int* dev_state,
+                            cudaStream_t st);
+// *out = scale * sum |x|^2 (device), deterministic
+cudaError_t scaled_norm2(const cplx* x, long long n, double scale, double* out, double* partial,
+                         cudaStream_t st);
 // mixed-precision SVD pieces (svd_mixed.cu)
 cudaError_t mixsvd_to_f32(const cplx* X, int m, int n, bool ct, float2* out, cudaStream_t st);
 cudaError_t mixsvd_q32_to_w(const float2* Q, int p, cplx* W, cudaStream_t st);

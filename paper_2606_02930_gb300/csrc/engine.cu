@@ -46,6 +46,11 @@ constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay 
 constexpr int kMixedSvdMinP = 96;        // isometry dimension from which the mixed SVD is used
 constexpr int kMixedSweeps = 12;         // fp32 Jacobi sweeps of the mixed SVD (cap)
 constexpr int kPolarSteps = 2;           // Newton-Schulz steps making the fp32 vectors unitary
+// Rows whose squared norm is below skip_weight(cutoff) |A|^2 can never be
+// kept by the truncation rule, so the Jacobi sweeps do not orthogonalise two
+// such rows against each other (their total weight is exact regardless).
+constexpr double kSkipWeight32 = 1e-12;  // fp32 preconditioner: below its resolution
+double skip_weight(double cutoff) { return 1e-3 * std::max(cutoff, kWeightFloor * 0.1); }
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -357,7 +362,7 @@ ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, 
 ite_status split_mixed(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
                        bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
                        double* sigma_out) {
-  const bool tr = m > n;
+  const bool tr = m > n || (m == n && !centre_right);
   const int p = tr ? n : m, q = tr ? m : n;
   const long long pp = (long long)p * p;
   // carve the workspace with every piece on a 256-byte boundary
@@ -386,9 +391,11 @@ ite_status split_mixed(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, do
   float2* Q32 = reinterpret_cast<float2*>(pieces[6]);
   unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
   // 1. fp32 Jacobi on the rows of A = M (or M^H)
+  double* anorm2 = ctx->dscal + 8;
+  CK(scaled_norm2(X, (long long)m * n, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
   CK(mixsvd_to_f32(X, m, n, tr, A32, ctx->stream));
-  CK(jacobi_rows_f32(A32, p, q, Q32, kMixedSweeps, (float)std::max(1e-6, q * 1.1920929e-7), jstate,
-                     ctx->stream));
+  CK(jacobi_rows_f32(A32, p, q, Q32, kMixedSweeps, (float)std::max(1e-6, q * 1.1920929e-7), anorm2,
+                     kSkipWeight32, jstate, ctx->stream));
   CK(mixsvd_q32_to_w(Q32, p, W, ctx->stream));
   // 2. unitary W: W <- 1.5 W - 0.5 W (W^H W)
   for (int it = 0; it < kPolarSteps; ++it) {
@@ -402,7 +409,8 @@ ite_status split_mixed(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, do
   else
     CS(gemm(ctx, p, m, n, W, 1, p, true, X, 1, n, true, Bm, m));         // W^H M^H
   // 4. FP64 one-sided Jacobi on the rows of B; the rotation of A is Q64 W^H
-  CK(jacobi_rows(Bm, p, q, Q64, kJacobiSweeps, std::max(1e-15, q * kEps), jstate, ctx->stream));
+  CK(jacobi_rows(Bm, p, q, Q64, kJacobiSweeps, std::max(1e-15, q * kEps), anorm2, skip_weight(cutoff),
+                 jstate, ctx->stream));
   CS(gemm(ctx, p, p, p, Q64, p, 1, false, W, 1, p, true, Wn, p));
   cplx* Qrot = Wn;
   // 5. singular values (row norms of the rotated B), order and rank
@@ -447,13 +455,17 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
                        sigma_out);
   cplx* A = P<cplx>(ctx->ws_svdA);
   cplx* Q = P<cplx>(ctx->ws_svdQ);
-  const bool tr = m > n;
+  // rotate the rows of the smaller side; for a square block, the side whose
+  // isometry is wanted, so that it comes from the unitary Q
+  const bool tr = m > n || (m == n && !centre_right);
   const int p = tr ? n : m, q = tr ? m : n;
   if (tr) CK(conj_transpose(X, m, n, A, ctx->stream));
   else CK(vec_copy(A, X, (long long)m * n, ctx->stream));
   unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
   const double jtol = std::max(1e-15, q * kEps);
-  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, jtol, jstate, ctx->stream));
+  double* anorm2 = ctx->dscal + 8;
+  CK(scaled_norm2(A, (long long)p * q, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
+  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, jtol, anorm2, skip_weight(cutoff), jstate, ctx->stream));
   double* small = P<double>(ctx->ws_small);
   double* sigma = small;
   double* sorted = small + p;

@@ -51,7 +51,7 @@ __device__ __forceinline__ R warp_sum_t(R v) {
 // if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block.
 template <typename R>
 __device__ void jacobi_pair(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int u, int v,
-                            R tol, int* counter) {
+                            R tol, R skip, int* counter) {
   typedef typename Cx<R>::T T;
   if (u > v) { const int t = u; u = v; v = t; }
   T* au = A + (long long)u * q;
@@ -75,14 +75,23 @@ __device__ void jacobi_pair(typename Cx<R>::T* A, int p, int q, typename Cx<R>::
     for (int w = 0; w < JT / 32; ++w) { al += sh[0][w]; be += sh[1][w]; Gr += sh[2][w]; Gi += sh[3][w]; }
     const R gabs = hypot(Gr, Gi);
     R c = 1, sr = 0, si = 0;   // rotation: c, and s*e^{i theta}
-    if (gabs > tol * sqrt(al * be) && gabs > R(0)) {
+    // A pair of rows both below the skip weight can never be kept: their
+    // mutual orthogonality does not matter (their total weight does, and
+    // rotations preserve it).
+    if (gabs > tol * sqrt(al * be) && gabs > R(0) && (al > skip || be > skip)) {
       const R zeta = (be - al) / (R(2) * gabs);
       const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
       c = R(1) / sqrt(R(1) + t * t);
       const R sn = c * t;
       sr = sn * Gr / gabs;
       si = sn * Gi / gabs;
-      atomicAdd(counter, 1);
+      // Only rotations by an angle above tol between two rows that can be
+      // kept keep the sweeps going.  Rotations against rows below the skip
+      // weight are still applied, but those rows are never rotated among
+      // themselves, so they stay a non-orthogonal set, and orthogonalising a
+      // kept row against all of them one pair at a time converges only
+      // slowly; its overlap with them changes the kept product at second order.
+      if (fabs(t) > tol && al > skip && be > skip) atomicAdd(counter, 1);
     }
     rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != R(0) || si != R(0)) ? R(1) : R(0);
   }
@@ -109,11 +118,12 @@ __device__ void jacobi_pair(typename Cx<R>::T* A, int p, int q, typename Cx<R>::
 template <typename R>
 __global__ void __launch_bounds__(JT)
 k_jacobi_round(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int round, int pp, R tol,
-               int* counter) {
+               const double* anorm2, double skip_rel, int* counter) {
   const int k = blockIdx.x;
   const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
   if (u >= p || v >= p) return;
-  jacobi_pair<R>(A, p, q, Q, u, v, tol, counter);
+  const double a2 = anorm2 ? *anorm2 : 0.0;
+  jacobi_pair<R>(A, p, q, Q, u, v, tol, (R)(skip_rel * a2), counter);
 }
 
 // Grid-wide barrier for a cooperative launch.  st[0] arrivals, st[1]
@@ -155,8 +165,10 @@ __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
 template <typename R>
 __global__ void __launch_bounds__(JT)
 k_jacobi_persistent(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int pp, R tol,
-                    int max_sweeps, unsigned int* st) {
+                    const double* anorm2, double skip_rel, int max_sweeps, unsigned int* st) {
   const unsigned int nb = gridDim.x;
+  const double a2 = anorm2 ? *anorm2 : 0.0;
+  const R skip = (R)(skip_rel * a2);
   int* counters = reinterpret_cast<int*>(st + 2);
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int* cnt = counters + (sw & 1);
@@ -164,7 +176,7 @@ k_jacobi_persistent(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, in
       if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[(sw + 1) & 1] = 0;
       for (int k = blockIdx.x; k < pp / 2; k += nb) {
         const int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
-        if (u < p && v < p) jacobi_pair<R>(A, p, q, Q, u, v, tol, cnt);
+        if (u < p && v < p) jacobi_pair<R>(A, p, q, Q, u, v, tol, skip, cnt);
       }
       if (!grid_barrier(st, nb)) return;
     }
@@ -343,7 +355,8 @@ cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
 
 template <typename R>
 cudaError_t jacobi_rows_t(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int max_sweeps,
-                          R tol, unsigned int* dev_state, cudaStream_t st) {
+                          R tol, const double* anorm2, double skip_rel, unsigned int* dev_state,
+                          cudaStream_t st) {
   {
     long long tot = (long long)p * p;
     long long g = (tot + 255) / 256;
@@ -361,7 +374,7 @@ cudaError_t jacobi_rows_t(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T*
     int* cnt = reinterpret_cast<int*>(dev_state + 2);
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<R><<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, cnt);
+      k_jacobi_round<R><<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, anorm2, skip_rel, cnt);
     }
     return cudaGetLastError();
   }
@@ -382,19 +395,21 @@ cudaError_t jacobi_rows_t(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T*
   int nblk = pp / 2;
   if (nblk > max_blocks) nblk = max_blocks;
   if (nblk < 1) return cudaErrorInvalidConfiguration;
-  void* args[] = {&A, &p, &q, &Q, (void*)&pp, &tol, &max_sweeps, &dev_state};
+  void* args[] = {&A, &p, &q, &Q, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &dev_state};
   count_launches(1);
   return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent<R>, dim3(nblk), dim3(JT), args, 0, st);
 }
 
 cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        unsigned int* dev_state, cudaStream_t st) {
-  return jacobi_rows_t<double>(A, p, q, Q, max_sweeps, tol, dev_state, st);
+                        const double* anorm2, double skip_rel, unsigned int* dev_state,
+                        cudaStream_t st) {
+  return jacobi_rows_t<double>(A, p, q, Q, max_sweeps, tol, anorm2, skip_rel, dev_state, st);
 }
 
 cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
-                            unsigned int* dev_state, cudaStream_t st) {
-  return jacobi_rows_t<float>(A, p, q, Q, max_sweeps, tol, dev_state, st);
+                            const double* anorm2, double skip_rel, unsigned int* dev_state,
+                            cudaStream_t st) {
+  return jacobi_rows_t<float>(A, p, q, Q, max_sweeps, tol, anorm2, skip_rel, dev_state, st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

@@ -325,6 +325,21 @@ cudaError_t vec_norm2(const cplx* x, long long n, double* out, double* partial,
   k_reduce_real<<<1, 32, 0, st>>>(partial, g, out, active);
   return cudaGetLastError();
 }
+namespace {
+__global__ void k_scale_scalar(double* v, double s) {
+  if (threadIdx.x == 0) *v *= s;
+}
+}  // namespace
+
+cudaError_t scaled_norm2(const cplx* x, long long n, double scale, double* out, double* partial,
+                         cudaStream_t st) {
+  cudaError_t e = vec_norm2(x, n, out, partial, nullptr, st);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  k_scale_scalar<<<1, 32, 0, st>>>(out, scale);
+  return cudaGetLastError();
+}
+
 cudaError_t vec_scale_dev(cplx* y, const double* scale, long long n, const int* active,
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
