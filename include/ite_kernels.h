@@ -57,17 +57,18 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
  * truncation keeps the discarded squared Schmidt weight below cutoff):
  * X = U S V^dag, kept rank r by the library's truncation rule (chi_max, cutoff,
  * weight floor 1e-24, near-degenerate groups kept whole).  centre_right != 0
- * writes left = U_r (m x r) and right = S_r V_r^dag (r x n); otherwise
- * left = U_r S_r and right = V_r^dag.  left needs m*min(m,n) and right
- * min(m,n)*n complex entries of room.  sigma (device, may be NULL) receives
- * min(m,n) values in descending order: the singular values down to a squared
- * weight of 1e-3 max(cutoff, 1e-25) of the total; below that the rows are
- * never kept and are left unresolved, so those entries are norms of a mixed
- * block whose sum of squares alone is exact.  flags bit 0 selects the
- * tensor-core mode: when min(m,n) is 96 or more, the FP64 Jacobi is
- * preconditioned by fp32 Jacobi (rotations made unitary to FP64 precision by
- * Newton-Schulz steps) and the GEMMs run on the tensor cores.  flags bit 1
- * runs that preconditioned algorithm with FP64-pipe GEMMs. */
+ * writes left = U_r (m x r) and right = S_r V_r^dag = U_r^dag X (r x n);
+ * otherwise left = U_r S_r = X V_r and right = V_r^dag.  left needs m*min(m,n)
+ * and right min(m,n)*n complex entries of room; the output that receives the
+ * projection (right when centre_right, else left) must not overlap X.
+ * sigma (device, may be NULL) receives min(m,n) values in descending order:
+ * the singular values down to a squared weight of 1e-3 max(cutoff, 1e-25) of
+ * the total; below that the rows are never kept and are left unresolved, so
+ * those entries are norms of a mixed block whose sum of squares alone is
+ * exact.  Algorithm: Householder LQ of the rows on the isometry side, one-sided
+ * Jacobi on the triangular factor, projection GEMM.  flags bit 0 runs the
+ * projection GEMM on the tensor cores with FP64-class accuracy (the emulation
+ * of ite_k_zgemm mode 1). */
 ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded, int flags);

@@ -297,10 +297,9 @@ def k_local_solve(ctx, H, i, L_env, R_env, B, X, alpha, c, krylov_dim=10, local_
     return steps.value, res.value
 
 
-def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None, tc=False,
-            mixed_native=False):
+def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None, tc=False):
     r, disc = C.c_int(), C.c_double()
-    flags = (1 if tc else 0) | (2 if mixed_native else 0)
+    flags = 1 if tc else 0
     check(lib.ite_k_split(ctx.h, _p(X), m, n, chi_max, cutoff, 1 if centre_right else 0, _p(left),
                           _p(right), _p(sigma), C.byref(r), C.byref(disc), flags), ctx.h)
     return r.value, disc.value

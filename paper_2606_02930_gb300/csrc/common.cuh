@@ -143,16 +143,22 @@ cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cpl
                           cudaStream_t st);
 
 // ---------------------------------------------------------------- SVD (FP64)
-// One-sided Jacobi SVD of a p x q complex matrix stored row-major in A (rows
-// are the rotated vectors).  Q (p x p) receives the accumulated row rotations:
-// on return Q A_in = A_out with mutually orthogonal rows.  Runs as one
-// cooperative launch; dev_state (8 device words) returns the sweeps done in
-// word 5 and a nonzero word 4 if a grid-barrier wait ran out.  *anorm2
-// (device) is |A|_F^2: pairs of rows whose squared norms are both
-// <= skip_rel |A|_F^2 are left as they are.
-cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
+// Householder LQ of the rows of W (p x q, row-major), in place: row j keeps
+// its part left of the diagonal as L[j][0..j) and beta[j] receives L[j][j].
+// One cooperative launch; dev_state (8 device words) gets a nonzero word 4 if
+// a grid-barrier wait ran out.
+cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, cudaStream_t st);
+// R (k x p, k = min(p, q)) = L^H from the output of svd_lq
+cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cudaStream_t st);
+// One-sided Jacobi on the rows (length len) of A until they are mutually
+// orthogonal; no rotation is accumulated.  One cooperative launch;
+// dev_state (8 device words) returns the sweeps done in word 5 and a nonzero
+// word 4 if a grid-barrier wait ran out; stamps (rows device ints) is
+// scratch.  *anorm2 (device) is |A|_F^2: pairs of rows whose squared norms
+// are both <= skip_rel |A|_F^2 are left as they are.
+cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, unsigned int* dev_state,
-                        cudaStream_t st);
+                        int* stamps, cudaStream_t st);
 // row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
 // by index), and the kept rank by the truncation rule (see engine).
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
@@ -162,27 +168,14 @@ cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, doub
 cudaError_t sort_rank(const double* sigma, int p, int* perm, double* sorted_sigma, int chi_max,
                       double cutoff, double weight_floor, double tie_rel, int* rank_out,
                       double* discarded_out, cudaStream_t st);
-// fp32 one-sided Jacobi (same contract as jacobi_rows)
-cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
-                            const double* anorm2, double skip_rel, unsigned int* dev_state,
-                            cudaStream_t st);
+// Uh (r x len) = rows perm[0..r) of D divided by sorted_sigma (unit vectors
+// for zero rows)
+cudaError_t svd_gather_uh(const cplx* D, int len, const int* perm, const double* sorted_sigma,
+                          int r, cplx* Uh, cudaStream_t st);
 // *out = scale * sum |x|^2 (device), deterministic
 cudaError_t scaled_norm2(const cplx* x, long long n, double scale, double* out, double* partial,
                          cudaStream_t st);
-// mixed-precision SVD pieces (svd_mixed.cu)
-cudaError_t mixsvd_to_f32(const cplx* X, int m, int n, bool ct, float2* out, cudaStream_t st);
-cudaError_t mixsvd_q32_to_w(const float2* Q, int p, cplx* W, cudaStream_t st);
-cudaError_t mixsvd_gather(const cplx* W, const int* perm, int p, int r, bool ct, cplx* out,
-                          cudaStream_t st);
-cudaError_t mixsvd_gather_rows(const cplx* B, const int* perm, int q, int r, bool ct, cplx* out,
-                               cudaStream_t st);
-// write the two factors of a split (see engine for the four cases)
-cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma,
-                     const int* perm, int r, int p, int q, bool transposed, bool centre_right,
-                     cplx* left, cplx* right, cudaStream_t st);
 // out = A^H for a row-major m x n matrix A (out is n x m)
 cudaError_t conj_transpose(const cplx* A, int m, int n, cplx* out, cudaStream_t st);
-// Q = identity (p x p)
-cudaError_t set_identity(cplx* Q, int p, cudaStream_t st);
 
 }  // namespace ite

@@ -43,14 +43,13 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr int kJacobiSweeps = 30;
 constexpr int kMaxKrylov = 32;
 constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay native
-constexpr int kMixedSvdMinP = 96;        // isometry dimension from which the mixed SVD is used
-constexpr int kMixedSweeps = 12;         // fp32 Jacobi sweeps of the mixed SVD (cap)
-constexpr int kPolarSteps = 2;           // Newton-Schulz steps making the fp32 vectors unitary
 // Rows whose squared norm is below skip_weight(cutoff) |A|^2 can never be
 // kept by the truncation rule, so the Jacobi sweeps do not orthogonalise two
 // such rows against each other (their total weight is exact regardless).
-constexpr double kSkipWeight32 = 1e-12;  // fp32 preconditioner: below its resolution
 double skip_weight(double cutoff) { return 1e-3 * std::max(cutoff, kWeightFloor * 0.1); }
+// small SVD workspace for k rows: sigma, sorted (double), beta (complex),
+// perm, stamps (int)
+size_t small_bytes(long long k) { return (size_t)k * (2 * sizeof(double) + sizeof(cplx) + 2 * sizeof(int)) + 256; }
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -58,6 +57,8 @@ struct HostRead {
   int steps;
   int counter;
   int pad;
+  int lq_err;
+  int pad2;
   double disc;
   double res;
   double d[4];
@@ -80,8 +81,7 @@ struct ite_ctx_s {
   std::string err;
   size_t bytes = 0;
   // workspace
-  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu,
-      ws_mix;
+  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu;
   GmresState* gm = nullptr;
   double* dscal = nullptr;     // device scalars
   cplx* dcplx = nullptr;       // device complex scalars
@@ -89,7 +89,6 @@ struct ite_ctx_s {
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
   int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
-  bool mixed_svd = false;      // mixed-precision SVD with native GEMMs (kernel-level tests)
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
   int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
@@ -350,149 +349,83 @@ ite_status merge(ite_ctx ctx, int d, int chl, int chm, int chr, const cplx* K1, 
               (long long)d * chr);
 }
 
-// Mixed-precision truncated SVD (tensor-core mode).  The same one-sided
-// Jacobi as the FP64 path, on the same p = min(m, n) vectors (rows of M, or of
-// M^H when m > n), preconditioned in fp32: fp32 Jacobi gives rotations Q32;
-// two Newton-Schulz steps W <- W (3 I - W^H W) / 2 turn W0 = Q32^H into a
-// unitary matrix to FP64 precision; B = W^H A then has rows that are already
-// orthogonal to fp32 accuracy, and FP64 Jacobi on B finishes in a few sweeps.
-// With Q64 B = B_rot, the rotation of A is Q = Q64 W^H, and the factors are
-// emitted exactly as in the FP64 path.  The products are tensor-core GEMMs
-// with FP64-class accuracy.
-ite_status split_mixed(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
-                       bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
-                       double* sigma_out) {
-  const bool tr = m > n || (m == n && !centre_right);
-  const int p = tr ? n : m, q = tr ? m : n;
-  const long long pp = (long long)p * p;
-  // carve the workspace with every piece on a 256-byte boundary
-  const size_t sizes[] = {(size_t)pp * sizeof(cplx), (size_t)pp * sizeof(cplx),
-                          (size_t)pp * sizeof(cplx), (size_t)pp * sizeof(cplx),
-                          (size_t)p * q * sizeof(cplx), (size_t)p * q * sizeof(float2),
-                          (size_t)pp * sizeof(float2)};
-  const int npieces = (int)(sizeof(sizes) / sizeof(sizes[0]));
-  size_t need = 0;
-  for (int k = 0; k < npieces; ++k) need += (sizes[k] + 255) & ~size_t(255);
-  CS(buf_ensure(ctx, ctx->ws_mix, need));
-  char* pieces[8];
-  {
-    char* at = P<char>(ctx->ws_mix);
-    for (int k = 0; k < npieces; ++k) {
-      pieces[k] = at;
-      at += (sizes[k] + 255) & ~size_t(255);
-    }
-  }
-  cplx* W = reinterpret_cast<cplx*>(pieces[0]);
-  cplx* Wn = reinterpret_cast<cplx*>(pieces[1]);
-  cplx* T = reinterpret_cast<cplx*>(pieces[2]);
-  cplx* Q64 = reinterpret_cast<cplx*>(pieces[3]);
-  cplx* Bm = reinterpret_cast<cplx*>(pieces[4]);
-  float2* A32 = reinterpret_cast<float2*>(pieces[5]);
-  float2* Q32 = reinterpret_cast<float2*>(pieces[6]);
-  unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
-  // 1. fp32 Jacobi on the rows of A = M (or M^H)
-  double* anorm2 = ctx->dscal + 8;
-  CK(scaled_norm2(X, (long long)m * n, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
-  CK(mixsvd_to_f32(X, m, n, tr, A32, ctx->stream));
-  CK(jacobi_rows_f32(A32, p, q, Q32, kMixedSweeps, (float)std::max(1e-6, q * 1.1920929e-7), anorm2,
-                     kSkipWeight32, jstate, ctx->stream));
-  CK(mixsvd_q32_to_w(Q32, p, W, ctx->stream));
-  // 2. unitary W: W <- 1.5 W - 0.5 W (W^H W)
-  for (int it = 0; it < kPolarSteps; ++it) {
-    CS(gemm(ctx, p, p, p, W, 1, p, true, W, p, 1, false, T, p));                         // W^H W
-    CS(gemm(ctx, p, p, p, W, p, 1, false, T, p, 1, false, Wn, p, C(-0.5), C(0), W, C(1.5)));
-    std::swap(W, Wn);
-  }
-  // 3. B = W^H A
-  if (!tr)
-    CS(gemm(ctx, p, n, m, W, 1, p, true, X, n, 1, false, Bm, n));        // W^H M
-  else
-    CS(gemm(ctx, p, m, n, W, 1, p, true, X, 1, n, true, Bm, m));         // W^H M^H
-  // 4. FP64 one-sided Jacobi on the rows of B; the rotation of A is Q64 W^H
-  CK(jacobi_rows(Bm, p, q, Q64, kJacobiSweeps, std::max(1e-15, q * kEps), anorm2, skip_weight(cutoff),
-                 jstate, ctx->stream));
-  CS(gemm(ctx, p, p, p, Q64, p, 1, false, W, 1, p, true, Wn, p));
-  cplx* Qrot = Wn;
-  // 5. singular values (row norms of the rotated B), order and rank
-  double* small = P<double>(ctx->ws_small);
-  double* sigma = small;
-  double* sorted = small + p;
-  int* perm = reinterpret_cast<int*>(small + 2 * p);
-  int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
-  double* disc_dev = ctx->dscal + 7;
-  CK(svd_rank(Bm, p, q, sigma, perm, sorted, chi_max, cutoff, kWeightFloor, kTieRel, rank_dev,
-              disc_dev, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->hr->rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  CS(sync(ctx));
-  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
-  if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
-  ctx->jacobi_sweeps_total += ctx->hr->pad;
-  ctx->jacobi_splits += 1;
-  ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
-  const int r = ctx->hr->rank;
-  if (r < 1 || r > p) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
-  if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
-  if (sigma_out) CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
-  // 6. factors, as in the FP64 path
-  CK(svd_emit(Bm, Qrot, sorted, perm, r, p, q, tr, centre_right, left, right, ctx->stream));
-  *r_out = r;
-  *disc_out = ctx->hr->disc;
-  return ITE_OK;
-}
-
-// Truncated SVD of X (m x n). Writes left (m x r) and right (r x n); returns r.
+// Truncated SVD of X (m x n) into left (m x r) and right (r x n); returns r.
+// The rows of Xr are indexed by the side whose isometry is wanted: Xr = X
+// when centre_right (left = U_r), Xr = X^H otherwise (right = V_r^H).  The
+// LQ-preconditioned Jacobi gives sigma and U_r^H; the other factor is the
+// projection U_r^H Xr (one GEMM, on the tensor cores in the tensor-core mode).
 ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double cutoff,
                  bool centre_right, cplx* left, cplx* right, int* r_out, double* disc_out,
                  double* sigma_out = nullptr) {
   Scope sc(ctx, P_SVD);
-  if ((ctx->gemm_mode == 1 || ctx->mixed_svd) && std::min(m, n) >= kMixedSvdMinP)
-    return split_mixed(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, r_out, disc_out,
-                       sigma_out);
-  cplx* A = P<cplx>(ctx->ws_svdA);
-  cplx* Q = P<cplx>(ctx->ws_svdQ);
-  // rotate the rows of the smaller side; for a square block, the side whose
-  // isometry is wanted, so that it comes from the unitary Q
-  const bool tr = m > n || (m == n && !centre_right);
+  const bool tr = !centre_right;
   const int p = tr ? n : m, q = tr ? m : n;
-  if (tr) CK(conj_transpose(X, m, n, A, ctx->stream));
-  else CK(vec_copy(A, X, (long long)m * n, ctx->stream));
+  const int k = std::min(p, q);
+  CS(buf_ensure(ctx, ctx->ws_svdA, (size_t)m * n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)k * p * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_small, small_bytes(k)));
+  cplx* W = P<cplx>(ctx->ws_svdA);
+  cplx* R = P<cplx>(ctx->ws_svdQ);
+  char* sm = P<char>(ctx->ws_small);
+  double* sigma = reinterpret_cast<double*>(sm);
+  double* sorted = sigma + k;
+  cplx* beta = reinterpret_cast<cplx*>(sorted + k);
+  int* perm = reinterpret_cast<int*>(beta + k);
+  int* stamps = perm + k;
   unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
-  const double jtol = std::max(1e-15, q * kEps);
+  unsigned int* lqstate = jstate + 16;
   double* anorm2 = ctx->dscal + 8;
-  CK(scaled_norm2(A, (long long)p * q, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
-  CK(jacobi_rows(A, p, q, Q, kJacobiSweeps, jtol, anorm2, skip_weight(cutoff), jstate, ctx->stream));
-  double* small = P<double>(ctx->ws_small);
-  double* sigma = small;
-  double* sorted = small + p;
-  int* perm = reinterpret_cast<int*>(small + 2 * p);
+  if (tr) CK(conj_transpose(X, m, n, W, ctx->stream));
+  else CK(vec_copy(W, X, (long long)m * n, ctx->stream));
+  CK(scaled_norm2(W, (long long)p * q, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
+  // 1-2. R = L^H from the Householder LQ of the rows of Xr
+  CK(svd_lq(W, p, q, beta, lqstate, ctx->stream));
+  CK(svd_lq_r(W, beta, p, q, R, ctx->stream));
+  // 3. one-sided Jacobi on the k rows (length p) of R
+  CK(jacobi_rows(R, k, p, kJacobiSweeps, std::max(1e-15, p * kEps), anorm2, skip_weight(cutoff),
+                 jstate, stamps, ctx->stream));
+  // 4. singular values, order and rank
   int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
   double* disc_dev = ctx->dscal + 7;
-  CK(svd_rank(A, p, q, sigma, perm, sorted, chi_max, cutoff, kWeightFloor, kTieRel, rank_dev,
+  CK(svd_rank(R, k, p, sigma, perm, sorted, chi_max, cutoff, kWeightFloor, kTieRel, rank_dev,
               disc_dev, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->disc, disc_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->lq_err, lqstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
-  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
+  if (ctx->hr->counter != 0 || ctx->hr->lq_err != 0)
+    return fail(ctx, ITE_ETIMEOUT, "SVD grid barrier wait ran out");
   if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
   ctx->jacobi_sweeps_total += ctx->hr->pad;
   ctx->jacobi_splits += 1;
   ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
   const int r = ctx->hr->rank;
-  if (r < 1 || r > p) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
-  if (sigma_out) CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(svd_emit(A, Q, sorted, perm, r, p, q, tr, centre_right, left, right, ctx->stream));
+  if (r < 1 || r > k) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
+  if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
+  if (sigma_out) {
+    CK(cudaMemsetAsync(sigma_out, 0, sizeof(double) * std::min(m, n), ctx->stream));
+    CK(cudaMemcpyAsync(sigma_out, sorted, sizeof(double) * k, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  // 5. factors: Uh = U_r^H (r x p) in the LQ workspace (free again), then
+  // the projection.  X is read in full before the isometry side is written,
+  // so X may share memory with that side (the gauge moves do).
+  cplx* Uh = W;
+  CK(svd_gather_uh(R, p, perm, sorted, r, Uh, ctx->stream));
+  if (!centre_right) {
+    // left = X V_r (m x r), right = V_r^H (r x n)
+    CS(gemm(ctx, m, r, n, X, n, 1, false, Uh, 1, n, true, left, r));
+    CK(vec_copy(right, Uh, (long long)r * n, ctx->stream));
+  } else {
+    // right = U_r^H X (r x n), left = U_r (m x r)
+    CS(gemm(ctx, r, n, m, Uh, m, 1, false, X, n, 1, false, right, n));
+    CK(conj_transpose(Uh, r, m, left, ctx->stream));
+  }
   *r_out = r;
   *disc_out = ctx->hr->disc;
-  if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
   return ITE_OK;
 }
 
@@ -754,9 +687,9 @@ ite_status ensure_workspace(ite_ctx ctx, ite_mpo H, const std::vector<int>& cap,
   CS(buf_ensure(ctx, ctx->ws_T1, tmax * cs));
   CS(buf_ensure(ctx, ctx->ws_T2, tmax * cs));
   CS(buf_ensure(ctx, ctx->ws_svdA, nmax * cs));
-  CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)pmax * pmax * cs));
+  CS(buf_ensure(ctx, ctx->ws_svdQ, nmax * cs));
   CS(buf_ensure(ctx, ctx->ws_left, nmax * cs));
-  CS(buf_ensure(ctx, ctx->ws_small, (size_t)pmax * 3 * sizeof(double) + 64));
+  CS(buf_ensure(ctx, ctx->ws_small, small_bytes(pmax)));
   CS(buf_ensure(ctx, ctx->ws_env, (size_t)(2 * envs + 2 * ovs + 16) * cs));
   return ITE_OK;
 }
@@ -910,7 +843,7 @@ ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free
   ctx->dscal = (double*)dev_alloc(ctx, 64 * sizeof(double) + kPartialSlots * sizeof(double));
   ctx->dcplx = (cplx*)dev_alloc(ctx, 512 * sizeof(cplx));
   ctx->partial = (cplx*)dev_alloc(ctx, (size_t)kPartialSlots * sizeof(cplx));
-  ctx->dcounter = (int*)dev_alloc(ctx, 16 * sizeof(int));
+  ctx->dcounter = (int*)dev_alloc(ctx, 32 * sizeof(int));
   if (cudaMallocHost((void**)&ctx->hr, sizeof(HostRead)) != cudaSuccess) ctx->hr = nullptr;
   if (!ctx->gm || !ctx->dscal || !ctx->dcplx || !ctx->partial || !ctx->dcounter || !ctx->hr) {
     ite_ctx_destroy(ctx);
@@ -931,13 +864,13 @@ void ite_ctx_destroy(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu, &ctx->ws_mix};
+                 &ctx->ws_emu};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
   dev_free(ctx, ctx->dcplx, 512 * sizeof(cplx));
   dev_free(ctx, ctx->partial, (size_t)kPartialSlots * sizeof(cplx));
-  dev_free(ctx, ctx->dcounter, 16 * sizeof(int));
+  dev_free(ctx, ctx->dcounter, 32 * sizeof(int));
   if (ctx->hr) cudaFreeHost(ctx->hr);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -1122,7 +1055,10 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
   const long long n0 = (long long)x->chi[0] * x->d * x->chi[1];
   CK(vec_norm2(x->site[0], n0, ctx->dscal + 2, ctx->dscal + 16, nullptr, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->d[1], ctx->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
+  if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
   const double nrm = std::sqrt(ctx->hr->d[1]);
   if (!(nrm > 0.0) || !std::isfinite(nrm)) return fail(ctx, ITE_ESINGULAR, "solution has zero or non-finite norm");
   CK(vec_axpby(x->site[0], x->site[0], C(0), C(1.0 / nrm), n0, ctx->stream));
@@ -1650,18 +1586,10 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
     return ITE_EINVAL;
   struct ModeGuard {
     ite_ctx c;
-    ~ModeGuard() {
-      c->gemm_mode = 0;
-      c->mixed_svd = false;
-    }
+    ~ModeGuard() { c->gemm_mode = 0; }
   } mode_guard{ctx};
   ctx->gemm_mode = (flags & 1) ? 1 : 0;
-  ctx->mixed_svd = (flags & 2) != 0;
   CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
-  const long long p = std::min(m, n);
-  CS(buf_ensure(ctx, ctx->ws_svdA, (size_t)m * n * sizeof(cplx)));
-  CS(buf_ensure(ctx, ctx->ws_svdQ, (size_t)p * p * sizeof(cplx)));
-  CS(buf_ensure(ctx, ctx->ws_small, (size_t)p * 3 * sizeof(double) + 64));
   int r = 0;
   double disc = 0.0;
   CS(split(ctx, (const cplx*)X, m, n, chi_max, cutoff, centre_right != 0, (cplx*)left, (cplx*)right,

@@ -1,14 +1,20 @@
-// FP64 truncated SVD of the two-site blocks and the gauge moves: parallel
-// one-sided (Hestenes) Jacobi on the rows of a p x q complex matrix.
+// FP64 truncated SVD of the two-site blocks and of the gauge moves.
 //
-// Each launch performs one round of a round-robin tournament: the p rows form
-// p/2 disjoint pairs, one CTA per pair.  The CTA forms alpha = |a_u|^2,
-// beta = |a_v|^2 and gamma = a_u^H a_v, and if |gamma| > tol sqrt(alpha beta)
-// applies the complex Jacobi rotation that makes the pair orthogonal to both
-// the pair of rows and to the matching rows of the accumulated unitary Q.  A
-// sweep is p-1 rounds; sweeps repeat until no rotation fires.  On exit
-// Q A_in = A_out, the rows of A_out are orthogonal with norms sigma_i, so
-// A_in = Q^H diag(sigma) V^H with V^H the normalised rows.
+// For a p x q complex matrix Xr (row-major), whose rows are indexed by the
+// side whose isometry is wanted, the split runs
+//   1. a Householder LQ of the rows, Xr H_0 H_1 ... H_{k-1} = L (p x k lower
+//      trapezoidal, k = min(p, q)), all k reflector steps in one cooperative
+//      launch;
+//   2. R = L^H (k x p, upper trapezoidal), so that R^H R = Xr Xr^H: the rows
+//      of R carry the left singular structure of Xr and are graded like its
+//      singular values, which is what lets the Jacobi below converge in few
+//      sweeps (QR preconditioning of the one-sided Jacobi method);
+//   3. one-sided (Hestenes) Jacobi on the rows of R until they are mutually
+//      orthogonal: R_out = Sigma U^H, U the left singular vectors of Xr;
+//   4. row norms, the descending order and the truncation rule; the kept
+//      rows of U^H are the rows of R_out divided by their norms.
+// No rotation is accumulated: the engine forms the other factor as the
+// projection U_r^H Xr with one GEMM.
 #include "common.cuh"
 
 namespace ite {
@@ -22,108 +28,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Sums of a and b over the JT threads of the block, returned to every thread
+// (fixed order, so deterministic).  sh holds JT/32 doubles per value.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double (*sh)[JT / 32]) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();                 // sh may still be read from its previous use
+  if (lane == 0) {
+    sh[0][wid] = a;
+    sh[1][wid] = b;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+#pragma unroll
+  for (int w = 0; w < JT / 32; ++w) {
+    a += sh[0][w];
+    b += sh[1][w];
+  }
+}
+
 __device__ __forceinline__ int player(int pos, int round, int pp) {
   return pos == 0 ? 0 : ((pos - 1 + round) % (pp - 1)) + 1;
-}
-
-// complex helpers over the real type R (double: FP64 path, float: the
-// approximate FP32 stage of the mixed-precision SVD)
-template <typename R> struct Cx;
-template <> struct Cx<double> { typedef double2 T; };
-template <> struct Cx<float> { typedef float2 T; };
-
-template <typename R>
-__device__ __forceinline__ typename Cx<R>::T cx(R a, R b) {
-  typename Cx<R>::T z;
-  z.x = a;
-  z.y = b;
-  return z;
-}
-
-template <typename R>
-__device__ __forceinline__ R warp_sum_t(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// One Jacobi rotation on rows u, v of A (and of Q): make the pair orthogonal
-// if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block.
-template <typename R>
-__device__ void jacobi_pair(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int u, int v,
-                            R tol, R skip, int* counter) {
-  typedef typename Cx<R>::T T;
-  if (u > v) { const int t = u; u = v; v = t; }
-  T* au = A + (long long)u * q;
-  T* av = A + (long long)v * q;
-  R sa = 0, sb = 0, gr = 0, gi = 0;
-  for (int e = threadIdx.x; e < q; e += JT) {
-    const T x = au[e], y = av[e];
-    sa = fma(x.x, x.x, fma(x.y, x.y, sa));
-    sb = fma(y.x, y.x, fma(y.y, y.y, sb));
-    gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // Re(conj(x) y)
-    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));    // Im(conj(x) y)
-  }
-  __shared__ R sh[4][JT / 32];
-  __shared__ R rot[4];
-  sa = warp_sum_t(sa); sb = warp_sum_t(sb); gr = warp_sum_t(gr); gi = warp_sum_t(gi);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sh[0][wid] = sa; sh[1][wid] = sb; sh[2][wid] = gr; sh[3][wid] = gi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R al = 0, be = 0, Gr = 0, Gi = 0;
-    for (int w = 0; w < JT / 32; ++w) { al += sh[0][w]; be += sh[1][w]; Gr += sh[2][w]; Gi += sh[3][w]; }
-    const R gabs = hypot(Gr, Gi);
-    R c = 1, sr = 0, si = 0;   // rotation: c, and s*e^{i theta}
-    // A pair of rows both below the skip weight can never be kept: their
-    // mutual orthogonality does not matter (their total weight does, and
-    // rotations preserve it).
-    if (gabs > tol * sqrt(al * be) && gabs > R(0) && (al > skip || be > skip)) {
-      const R zeta = (be - al) / (R(2) * gabs);
-      const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-      c = R(1) / sqrt(R(1) + t * t);
-      const R sn = c * t;
-      sr = sn * Gr / gabs;
-      si = sn * Gi / gabs;
-      // Only rotations by an angle above tol between two rows that can be
-      // kept keep the sweeps going.  Rotations against rows below the skip
-      // weight are still applied, but those rows are never rotated among
-      // themselves, so they stay a non-orthogonal set, and orthogonalising a
-      // kept row against all of them one pair at a time converges only
-      // slowly; its overlap with them changes the kept product at second order.
-      if (fabs(t) > tol && al > skip && be > skip) atomicAdd(counter, 1);
-    }
-    rot[0] = c; rot[1] = sr; rot[2] = si; rot[3] = (sr != R(0) || si != R(0)) ? R(1) : R(0);
-  }
-  __syncthreads();
-  const R c = rot[0], sr = rot[1], si = rot[2];   // se = s e^{i theta}
-  const bool apply = rot[3] != R(0);
-  __syncthreads();                             // rot[] is reused by the next pair
-  if (!apply) return;
-  // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
-  for (int e = threadIdx.x; e < q; e += JT) {
-    const T x = au[e], y = av[e];
-    au[e] = cx<R>(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
-    av[e] = cx<R>((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
-  }
-  T* qu = Q + (long long)u * p;
-  T* qv = Q + (long long)v * p;
-  for (int e = threadIdx.x; e < p; e += JT) {
-    const T x = qu[e], y = qv[e];
-    qu[e] = cx<R>(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
-    qv[e] = cx<R>((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(JT)
-k_jacobi_round(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int round, int pp, R tol,
-               const double* anorm2, double skip_rel, int* counter) {
-  const int k = blockIdx.x;
-  const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
-  if (u >= p || v >= p) return;
-  const double a2 = anorm2 ? *anorm2 : 0.0;
-  jacobi_pair<R>(A, p, q, Q, u, v, tol, (R)(skip_rel * a2), counter);
 }
 
 // Grid-wide barrier for a cooperative launch.  st[0] arrivals, st[1]
@@ -156,27 +83,168 @@ __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
   return *((volatile unsigned int*)(st + 4)) == 0u;
 }
 
+// ------------------------------------------------------------ Householder LQ
+// Step j takes the tail x = W[j][j..q) of row j and the reflector
+// H = I - c u^H u (u a row vector) with x H = beta e_0:
+//   beta = -e^{i phi} |x|,  u_0 = e^{i phi} (|x_0| + |x|),  u_e = x_e (e > 0),
+//   c = 1 / (|x| (|x| + |x_0|)),  phi = arg x_0,
+// and applies it to every later row: y <- y - c (y u^H) u.  Row j itself is
+// left as it is (it holds u beyond position j); beta goes to beta[j].  Every
+// block recomputes the reflector of step j from row j, which no block writes
+// during step j; one grid barrier separates the steps.
+__global__ void __launch_bounds__(JT)
+k_lq_persistent(cplx* W, int p, int q, cplx* beta, unsigned int* st) {
+  __shared__ double sh[2][JT / 32];
+  __shared__ double hs[3];
+  const int k = p < q ? p : q;
+  const unsigned int nb = gridDim.x;
+  for (int j = 0; j < k; ++j) {
+    const cplx* x = W + (long long)j * q;
+    double s = 0.0, unused = 0.0;
+    for (int e = j + threadIdx.x; e < q; e += JT) s = fma(x[e].x, x[e].x, fma(x[e].y, x[e].y, s));
+    block_sum2(s, unused, sh);
+    if (threadIdx.x == 0) {
+      const cplx x0 = x[j];
+      const double nx = sqrt(s), a0 = hypot(x0.x, x0.y);
+      const double phr = a0 > 0.0 ? x0.x / a0 : 1.0, phi = a0 > 0.0 ? x0.y / a0 : 0.0;
+      if (blockIdx.x == 0) beta[j] = cmake(-phr * nx, -phi * nx);
+      hs[0] = phr * (a0 + nx);
+      hs[1] = phi * (a0 + nx);
+      hs[2] = nx > 0.0 ? 1.0 / (nx * (nx + a0)) : 0.0;
+    }
+    __syncthreads();
+    const double c = hs[2];
+    const cplx u0 = cmake(hs[0], hs[1]);
+    if (c != 0.0) {
+      for (int i = j + 1 + (int)blockIdx.x; i < p; i += (int)nb) {
+        cplx* y = W + (long long)i * q;
+        double dr = 0.0, di = 0.0;     // y u^H
+        for (int e = j + threadIdx.x; e < q; e += JT) {
+          const cplx u = e == j ? u0 : x[e];
+          const cplx v = y[e];
+          dr = fma(v.x, u.x, fma(v.y, u.y, dr));
+          di = fma(v.y, u.x, fma(-v.x, u.y, di));
+        }
+        block_sum2(dr, di, sh);
+        const double fr = c * dr, fi = c * di;
+        for (int e = j + threadIdx.x; e < q; e += JT) {
+          const cplx u = e == j ? u0 : x[e];
+          cplx v = y[e];
+          v.x -= fr * u.x - fi * u.y;
+          v.y -= fr * u.y + fi * u.x;
+          y[e] = v;
+        }
+      }
+    }
+    if (!grid_barrier(st, nb)) return;
+  }
+}
+
+// R (k x p) = L^H: R[j][i] = conj(L[i][j]); L[i][j] = W[i][j] below the
+// diagonal, beta[j] on it, zero above.
+__global__ void k_lq_r(const cplx* W, const cplx* beta, int p, int q, int k, cplx* R) {
+  const long long tot = (long long)k * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / p), i = (int)(e - (long long)j * p);
+    cplx v = cmake(0.0, 0.0);
+    if (i > j) v = cconj(W[(long long)i * q + j]);
+    else if (i == j) v = cconj(beta[j]);
+    R[e] = v;
+  }
+}
+
+// ---------------------------------------------------------- one-sided Jacobi
+// One Jacobi rotation on rows u, v (length len) of A: make the pair orthogonal
+// if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block;
+// returns (to every thread) whether the rows were rotated.
+__device__ bool jacobi_pair(cplx* A, int len, int u, int v, double tol, double skip, int* counter) {
+  __shared__ double sh[2][2][JT / 32];
+  if (u > v) { const int t = u; u = v; v = t; }
+  cplx* au = A + (long long)u * len;
+  cplx* av = A + (long long)v * len;
+  double sa = 0, sb = 0, gr = 0, gi = 0;
+  for (int e = threadIdx.x; e < len; e += JT) {
+    const cplx x = au[e], y = av[e];
+    sa = fma(x.x, x.x, fma(x.y, x.y, sa));
+    sb = fma(y.x, y.x, fma(y.y, y.y, sb));
+    gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // Re(conj(x) y)
+    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));    // Im(conj(x) y)
+  }
+  block_sum2(sa, sb, sh[0]);
+  block_sum2(gr, gi, sh[1]);
+  const double al = sa, be = sb;
+  const double gabs = hypot(gr, gi);
+  // A pair of rows both below the skip weight can never be kept: their
+  // mutual orthogonality does not matter (their total weight does, and
+  // rotations preserve it).
+  if (!(gabs > tol * sqrt(al * be) && gabs > 0.0 && (al > skip || be > skip))) return false;
+  const double zeta = (be - al) / (2.0 * gabs);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  const double sn = c * t;
+  const double sr = sn * gr / gabs, si = sn * gi / gabs;   // s e^{i theta}
+  // Only rotations by an angle above tol between two rows that can be kept
+  // keep the sweeps going.  Rotations against rows below the skip weight are
+  // still applied, but those rows are never rotated among themselves, so they
+  // stay a non-orthogonal set, and orthogonalising a kept row against all of
+  // them one pair at a time converges only slowly; its overlap with them
+  // changes the kept product at second order.
+  if (threadIdx.x == 0 && fabs(t) > tol && al > skip && be > skip) atomicAdd(counter, 1);
+  // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
+  for (int e = threadIdx.x; e < len; e += JT) {
+    const cplx x = au[e], y = av[e];
+    au[e] = cmake(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
+    av[e] = cmake((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(JT)
+k_jacobi_round(cplx* A, int rows, int len, int round, int pp, double tol, const double* anorm2,
+               double skip_rel, int* counter) {
+  const int k = blockIdx.x;
+  const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
+  if (u >= rows || v >= rows) return;
+  const double a2 = anorm2 ? *anorm2 : 0.0;
+  jacobi_pair(A, len, u, v, tol, skip_rel * a2, counter);
+}
+
 // All sweeps of the round-robin one-sided Jacobi in one cooperative launch.
 // st[2], st[3]: rotation counters of even / odd sweeps; st[5]: sweeps done.
 // A sweep's counter is read by every block after the sweep's last barrier;
 // the counter of the following sweep is cleared by block 0 in round 1 of the
 // current sweep, after every block has passed round 0 (and so has finished
 // reading it two sweeps ago).
-template <typename R>
+// stamps[row] holds the global round at which the row was last rotated.  The
+// tournament repeats every sweep, so a pair was last examined pp-1 rounds ago;
+// if neither row has been rotated since then (a rotation at that very round
+// left the pair orthogonal), examining it again cannot fire and is skipped.
 __global__ void __launch_bounds__(JT)
-k_jacobi_persistent(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int pp, R tol,
-                    const double* anorm2, double skip_rel, int max_sweeps, unsigned int* st) {
+k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double* anorm2,
+                    double skip_rel, int max_sweeps, unsigned int* st, int* stamps) {
   const unsigned int nb = gridDim.x;
-  const double a2 = anorm2 ? *anorm2 : 0.0;
-  const R skip = (R)(skip_rel * a2);
+  const double skip = skip_rel * (anorm2 ? *anorm2 : 0.0);
   int* counters = reinterpret_cast<int*>(st + 2);
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int* cnt = counters + (sw & 1);
     for (int r = 0; r < pp - 1; ++r) {
       if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[(sw + 1) & 1] = 0;
+      const int g = sw * (pp - 1) + r;
       for (int k = blockIdx.x; k < pp / 2; k += nb) {
         const int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
-        if (u < p && v < p) jacobi_pair<R>(A, p, q, Q, u, v, tol, skip, cnt);
+        if (u >= rows || v >= rows) continue;
+        if (sw > 0) {
+          const int last = g - (pp - 1);
+          // read through L2 so that every thread of the block sees the same
+          // stamps and takes the same branch
+          if (__ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) continue;
+        }
+        const bool rotated = jacobi_pair(A, len, u, v, tol, skip, cnt);
+        if (rotated && threadIdx.x == 0) {
+          stamps[u] = g;
+          stamps[v] = g;
+        }
       }
       if (!grid_barrier(st, nb)) return;
     }
@@ -186,25 +254,7 @@ k_jacobi_persistent(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, in
   }
 }
 
-template <typename R>
-__global__ void k_identity_t(typename Cx<R>::T* Q, int p) {
-  const long long tot = (long long)p * p;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / p, j = e - i * p;
-    Q[e] = cx<R>(i == j ? R(1) : R(0), R(0));
-  }
-}
-
-__global__ void k_identity(cplx* Q, int p) {
-  const long long tot = (long long)p * p;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / p, j = e - i * p;
-    Q[e] = cmake(i == j ? 1.0 : 0.0, 0.0);
-  }
-}
-
+// ------------------------------------------------------- ranks and factors
 __global__ void k_row_norms(const cplx* A, int p, int q, double* sigma) {
   const int i = blockIdx.x;
   const cplx* a = A + (long long)i * q;
@@ -284,46 +334,17 @@ __global__ void k_sort_rank(const double* sigma, int p, int* perm, double* sorte
   *disc_out = tail / total;
 }
 
-// transposed == false: A = M (m x n, m <= n), Q is m x m, u_k = conj(Q row), s_k v_k^H = A row
-// transposed == true : A = M^H (n x m),     Q is n x n, s_k u_k = conj(A row), v_k^H = Q row
-__global__ void k_emit(const cplx* Arot, const cplx* Q, const double* sorted, const int* perm,
-                       int r, int p, int q, bool transposed, bool centre_right, cplx* left,
-                       cplx* right) {
-  // left: (m x r), right: (r x n); m = transposed ? q : p; n = transposed ? p : q
-  const int m = transposed ? q : p, n = transposed ? p : q;
-  const long long totL = (long long)m * r, totR = (long long)r * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totL + totR;
+// Uh[k][i] = D[perm[k]][i] / sorted[k]; a zero row (only for X = 0, rank 1)
+// becomes the unit vector e_k, so that Uh keeps orthonormal rows.
+__global__ void k_gather_uh(const cplx* D, int len, const int* perm, const double* sorted, int r,
+                            cplx* Uh) {
+  const long long tot = (long long)r * len;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
-    if (e < totL) {
-      const long long i = e / r;
-      const int k = (int)(e - i * r);
-      const int src = perm[k];
-      const double s = sorted[k];
-      cplx v;
-      if (!transposed) {
-        v = cconj(Q[(long long)src * p + i]);
-        if (!centre_right) v = cscale(v, s);
-      } else {
-        v = cconj(Arot[(long long)src * q + i]);
-        if (centre_right) v = cscale(v, 1.0 / s);
-      }
-      left[e] = v;
-    } else {
-      const long long f = e - totL;
-      const int k = (int)(f / n);
-      const long long j = f - (long long)k * n;
-      const int src = perm[k];
-      const double s = sorted[k];
-      cplx v;
-      if (!transposed) {
-        v = Arot[(long long)src * q + j];
-        if (!centre_right) v = cscale(v, 1.0 / s);
-      } else {
-        v = Q[(long long)src * p + j];
-        if (centre_right) v = cscale(v, s);
-      }
-      right[f] = v;
-    }
+    const int k = (int)(e / len), i = (int)(e - (long long)k * len);
+    const double s = sorted[k];
+    Uh[e] = s > 0.0 ? cscale(D[(long long)perm[k] * len + i], 1.0 / s)
+                    : cmake(i == k ? 1.0 : 0.0, 0.0);
   }
 }
 
@@ -341,75 +362,88 @@ __global__ void k_conj_transpose(const cplx* A, int m, int n, cplx* out) {
   }
 }
 
-}  // namespace
-
-cudaError_t set_identity(cplx* Q, int p, cudaStream_t st) {
-  long long tot = (long long)p * p;
+int grid_for(long long tot) {
   long long g = (tot + 255) / 256;
   if (g > 1216) g = 1216;
   if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Blocks of JT threads of a kernel that can be co-resident on the current
+// device (the grid of a cooperative launch), cached per kernel and device.
+struct Coresident {
+  int dev = -1, blocks = 0;
+  cudaError_t get(const void* kernel, int* out) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d != dev) {
+      int per_sm = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, JT, 0);
+      if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+      if (e != cudaSuccess) return e;
+      blocks = per_sm * sms;
+      dev = d;
+    }
+    *out = blocks;
+    return blocks > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+  }
+};
+Coresident g_lq_blocks, g_jacobi_blocks;
+
+}  // namespace
+
+cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
+  if (p < 1 || q < 1) return cudaSuccess;
+  int max_blocks = 0;
+  err = g_lq_blocks.get((const void*)k_lq_persistent, &max_blocks);
+  if (err != cudaSuccess) return err;
+  int nblk = p - 1;
+  if (nblk > max_blocks) nblk = max_blocks;
+  if (nblk < 1) nblk = 1;
+  void* args[] = {&W, &p, &q, &beta, &dev_state};
   count_launches(1);
-  k_identity<<<(int)g, 256, 0, st>>>(Q, p);
+  return cudaLaunchCooperativeKernel((void*)k_lq_persistent, dim3(nblk), dim3(JT), args, 0, st);
+}
+
+cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cudaStream_t st) {
+  const int k = p < q ? p : q;
+  if (k < 1) return cudaSuccess;
+  count_launches(1);
+  k_lq_r<<<grid_for((long long)k * p), 256, 0, st>>>(W, beta, p, q, k, R);
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t jacobi_rows_t(typename Cx<R>::T* A, int p, int q, typename Cx<R>::T* Q, int max_sweeps,
-                          R tol, const double* anorm2, double skip_rel, unsigned int* dev_state,
-                          cudaStream_t st) {
-  {
-    long long tot = (long long)p * p;
-    long long g = (tot + 255) / 256;
-    if (g > 1216) g = 1216;
-    if (g < 1) g = 1;
-    count_launches(1);
-    k_identity_t<R><<<(int)g, 256, 0, st>>>(Q, p);
-  }
+cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
+                        const double* anorm2, double skip_rel, unsigned int* dev_state,
+                        int* stamps, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
-  if (p < 2) return cudaSuccess;
-  const int pp = p + (p & 1);
+  if (rows < 2) return cudaSuccess;
+  err = cudaMemsetAsync(stamps, 0, sizeof(int) * rows, st);
+  if (err != cudaSuccess) return err;
+  const int pp = rows + (rows & 1);
   if (pp == 2) {
     // a single pair: one rotation makes it orthogonal; a second launch confirms
     int* cnt = reinterpret_cast<int*>(dev_state + 2);
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<R><<<1, JT, 0, st>>>(A, p, q, Q, 0, pp, tol, anorm2, skip_rel, cnt);
+      k_jacobi_round<<<1, JT, 0, st>>>(A, rows, len, 0, pp, tol, anorm2, skip_rel, cnt);
     }
     return cudaGetLastError();
   }
-  // co-resident grid for the cooperative launch (cached per device and type)
-  static int cached_dev = -1, max_blocks = 0;
-  int dev = 0;
-  err = cudaGetDevice(&dev);
+  int max_blocks = 0;
+  err = g_jacobi_blocks.get((const void*)k_jacobi_persistent, &max_blocks);
   if (err != cudaSuccess) return err;
-  if (dev != cached_dev) {
-    int per_sm = 0, sms = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_persistent<R>, JT, 0);
-    if (err != cudaSuccess) return err;
-    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (err != cudaSuccess) return err;
-    max_blocks = per_sm * sms;
-    cached_dev = dev;
-  }
   int nblk = pp / 2;
   if (nblk > max_blocks) nblk = max_blocks;
-  if (nblk < 1) return cudaErrorInvalidConfiguration;
-  void* args[] = {&A, &p, &q, &Q, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &dev_state};
+  void* args[] = {&A, &rows, &len, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &dev_state,
+                  &stamps};
   count_launches(1);
-  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent<R>, dim3(nblk), dim3(JT), args, 0, st);
-}
-
-cudaError_t jacobi_rows(cplx* A, int p, int q, cplx* Q, int max_sweeps, double tol,
-                        const double* anorm2, double skip_rel, unsigned int* dev_state,
-                        cudaStream_t st) {
-  return jacobi_rows_t<double>(A, p, q, Q, max_sweeps, tol, anorm2, skip_rel, dev_state, st);
-}
-
-cudaError_t jacobi_rows_f32(float2* A, int p, int q, float2* Q, int max_sweeps, float tol,
-                            const double* anorm2, double skip_rel, unsigned int* dev_state,
-                            cudaStream_t st) {
-  return jacobi_rows_t<float>(A, p, q, Q, max_sweeps, tol, anorm2, skip_rel, dev_state, st);
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JT), args, 0, st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,
@@ -434,16 +468,11 @@ cudaError_t sort_rank(const double* sigma, int p, int* perm, double* sorted_sigm
   return cudaGetLastError();
 }
 
-cudaError_t svd_emit(const cplx* Arot, const cplx* Q, const double* sorted_sigma,
-                     const int* perm, int r, int p, int q, bool transposed, bool centre_right,
-                     cplx* left, cplx* right, cudaStream_t st) {
-  const long long tot = (long long)r * (p + q);
-  long long g = (tot + 255) / 256;
-  if (g > 1216) g = 1216;
-  if (g < 1) g = 1;
+cudaError_t svd_gather_uh(const cplx* D, int len, const int* perm, const double* sorted_sigma,
+                          int r, cplx* Uh, cudaStream_t st) {
+  if (r < 1) return cudaSuccess;
   count_launches(1);
-  k_emit<<<(int)g, 256, 0, st>>>(Arot, Q, sorted_sigma, perm, r, p, q, transposed, centre_right,
-                                  left, right);
+  k_gather_uh<<<grid_for((long long)r * len), 256, 0, st>>>(D, len, perm, sorted_sigma, r, Uh);
   return cudaGetLastError();
 }
 

@@ -205,8 +205,8 @@ def test_local_solve_matches_oracle_gmres(api, ctx, model, N, chi, i):
 @pytest.mark.parametrize("m,n,kind", [(128, 128, "decay"), (512, 512, "decay"), (200, 160, "ties"),
                                       (160, 200, "decay"), (256, 512, "decay")])
 def test_split_tensor_core_mode(api, ctx, m, n, kind):
-    # mixed-precision split (fp32 Jacobi, FP64 polish on the tensor-core GEMMs
-    # and FP64 Jacobi): same rank and truncated product as the oracle's SVD
+    # split with the projection GEMM on the tensor cores (FP64-class
+    # emulation): same rank and truncated product as the oracle's SVD
     import torch
     rng = np.random.default_rng(m * 31 + n)
     p = min(m, n)
