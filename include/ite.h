@@ -124,12 +124,20 @@ unsigned long long ite_kernel_launches(void);
  * returns, per category, the summed milliseconds, the summed algorithmic FLOPs
  * and the number of stages: 0 two-site H_eff, 1 environment updates, 2 local
  * solves (GMRES, H_eff included), 3 truncated SVD splits, 4 gauge moves (SVDs
- * included), 5 local right-hand sides and two-site merges, 6 whole steps. */
+ * included), 5 local right-hand sides and two-site merges, 6 whole steps,
+ * 7 the Householder LQ launches of the splits, 8 the Jacobi launches of the
+ * splits (7 and 8 are inside 3 and 4).  The arrays have ITE_PROFILE_SLOTS
+ * entries; unused ones are zero. */
+#define ITE_PROFILE_SLOTS 16
 ite_status ite_profile_start(ite_ctx ctx);
-/* Jacobi SVD statistics since the last call (then reset): splits performed,
- * total and largest number of sweeps. */
-ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max);
-ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long long counts[8]);
+ite_status ite_profile_stop(ite_ctx ctx, double ms[ITE_PROFILE_SLOTS],
+                            double flops[ITE_PROFILE_SLOTS], long long counts[ITE_PROFILE_SLOTS]);
+/* SVD statistics since the last call (then reset): splits performed, total
+ * and largest number of Jacobi sweeps, and (fp64_flops, may be NULL) the
+ * algorithmic FP64 flops of the Householder LQ ([0]) and of the Jacobi
+ * rotations and inner products actually executed ([1]). */
+ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max,
+                         double fp64_flops[2]);
 
 /* MPO from explicit site tensors: d[N] site dimensions (all equal), D[N+1]
  * bond dimensions with D[0] = D[N] = 1, W the concatenated W_i (interleaved

@@ -62,10 +62,10 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
  * and right min(m,n)*n complex entries of room; the output that receives the
  * projection (right when centre_right, else left) must not overlap X.
  * sigma (device, may be NULL) receives min(m,n) values in descending order:
- * the singular values down to a squared weight of 1e-3 max(cutoff, 1e-25) of
- * the total; below that the rows are never kept and are left unresolved, so
- * those entries are norms of a mixed block whose sum of squares alone is
- * exact.  Algorithm: Householder LQ of the rows on the isometry side, one-sided
+ * singular values for the first chi_max entries down to a squared weight of
+ * 1e-3 max(cutoff, 1e-25) of the total.  Rows that cannot be kept (below that
+ * weight, or far below the chi_max-th) are not resolved among themselves, so
+ * beyond those entries only the sum of squares is exact.  Algorithm: Householder LQ of the rows on the isometry side, one-sided
  * Jacobi on the triangular factor, projection GEMM.  flags bit 0 runs the
  * projection GEMM on the tensor cores with FP64-class accuracy (the emulation
  * of ite_k_zgemm mode 1). */

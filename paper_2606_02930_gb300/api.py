@@ -306,7 +306,8 @@ def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None
 
 
 # ------------------------------------------------------------------ profiling
-PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step")
+PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step", "lq", "jacobi")
+PROFILE_SLOTS = 16
 
 
 def kernel_launches():
@@ -318,9 +319,9 @@ def profile_start(ctx):
 
 
 def profile_stop(ctx):
-    ms = np.zeros(8)
-    fl = np.zeros(8)
-    cnt = np.zeros(8, np.int64)
+    ms = np.zeros(PROFILE_SLOTS)
+    fl = np.zeros(PROFILE_SLOTS)
+    cnt = np.zeros(PROFILE_SLOTS, np.int64)
     check(lib.ite_profile_stop(ctx.h, _dptr(ms), _dptr(fl),
                                cnt.ctypes.data_as(C.POINTER(C.c_longlong))), ctx.h)
     return {k: {"ms": float(ms[i]), "flops": float(fl[i]), "count": int(cnt[i])}
@@ -329,9 +330,11 @@ def profile_stop(ctx):
 
 def svd_stats(ctx):
     splits, total, mx = C.c_longlong(), C.c_longlong(), C.c_int()
-    check(lib.ite_svd_stats(ctx.h, C.byref(splits), C.byref(total), C.byref(mx)), ctx.h)
+    fl = np.zeros(2)
+    check(lib.ite_svd_stats(ctx.h, C.byref(splits), C.byref(total), C.byref(mx), _dptr(fl)), ctx.h)
     return {"splits": splits.value, "sweeps_mean": total.value / max(1, splits.value),
-            "sweeps_max": mx.value}
+            "sweeps_max": mx.value, "lq_fp64_flops": float(fl[0]),
+            "jacobi_fp64_flops": float(fl[1])}
 
 
 def k_gemm_bf16(ctx, A, B, Cout, k_tile=64):

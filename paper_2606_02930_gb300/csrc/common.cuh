@@ -152,13 +152,16 @@ cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, c
 cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cudaStream_t st);
 // One-sided Jacobi on the rows (length len) of A until they are mutually
 // orthogonal; no rotation is accumulated.  One cooperative launch;
-// dev_state (8 device words) returns the sweeps done in word 5 and a nonzero
-// word 4 if a grid-barrier wait ran out; stamps (rows device ints) is
-// scratch.  *anorm2 (device) is |A|_F^2: pairs of rows whose squared norms
-// are both <= skip_rel |A|_F^2 are left as they are.
+// dev_state (16 device words) returns the sweeps done in word 5, the pairs
+// examined and rotated in words 6 and 7, and a nonzero word 4 if a
+// grid-barrier wait ran out; stamps (rows ints) and wts (rows doubles) are
+// device scratch.  *anorm2 (device) is |A|_F^2: pairs of rows whose squared
+// norms are both <= skip_rel |A|_F^2 are left as they are.  keep_rank is the
+// most rows the caller will keep: the sweeps stop once only rows that cannot
+// be among them are still rotating (keep_rank >= rows disables this).
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
-                        const double* anorm2, double skip_rel, unsigned int* dev_state,
-                        int* stamps, cudaStream_t st);
+                        const double* anorm2, double skip_rel, int keep_rank,
+                        unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st);
 // row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
 // by index), and the kept rank by the truncation rule (see engine).
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

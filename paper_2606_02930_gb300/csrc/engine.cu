@@ -48,8 +48,8 @@ constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay 
 // such rows against each other (their total weight is exact regardless).
 double skip_weight(double cutoff) { return 1e-3 * std::max(cutoff, kWeightFloor * 0.1); }
 // small SVD workspace for k rows: sigma, sorted (double), beta (complex),
-// perm, stamps (int)
-size_t small_bytes(long long k) { return (size_t)k * (2 * sizeof(double) + sizeof(cplx) + 2 * sizeof(int)) + 256; }
+// wts (double), perm, stamps (int)
+size_t small_bytes(long long k) { return (size_t)k * (3 * sizeof(double) + sizeof(cplx) + 2 * sizeof(int)) + 256; }
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -59,6 +59,7 @@ struct HostRead {
   int pad;
   int lq_err;
   int pad2;
+  unsigned int pairs[2];
   double disc;
   double res;
   double d[4];
@@ -90,6 +91,7 @@ struct ite_ctx_s {
   HostRead* hr = nullptr;      // pinned
   int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
+  double jacobi_flops = 0.0, lq_flops = 0.0;
   int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
   bool prof = false;
@@ -188,7 +190,8 @@ ite_status sync(ite_ctx ctx) {
 }
 
 // ------------------------------------------------------------------ profiling
-enum { P_HEFF = 0, P_ENV, P_SOLVE, P_SVD, P_GAUGE, P_PROJ, P_STEP, P_NCAT };
+enum { P_HEFF = 0, P_ENV, P_SOLVE, P_SVD, P_GAUGE, P_PROJ, P_STEP, P_LQ, P_JACOBI, P_NCAT };
+static_assert(P_NCAT <= ITE_PROFILE_SLOTS, "profile categories exceed the ABI's slots");
 
 size_t prof_event(ite_ctx ctx) {
   if (ctx->evused == ctx->evpool.size()) {
@@ -370,20 +373,33 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   double* sigma = reinterpret_cast<double*>(sm);
   double* sorted = sigma + k;
   cplx* beta = reinterpret_cast<cplx*>(sorted + k);
-  int* perm = reinterpret_cast<int*>(beta + k);
+  double* wts = reinterpret_cast<double*>(beta + k);
+  int* perm = reinterpret_cast<int*>(wts + k);
   int* stamps = perm + k;
-  unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter);
-  unsigned int* lqstate = jstate + 16;
+  // dcounter words: 8-10 GEMM error flags, 16-31 Jacobi state, 32-39 LQ state
+  unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 16;
+  unsigned int* lqstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 32;
   double* anorm2 = ctx->dscal + 8;
   if (tr) CK(conj_transpose(X, m, n, W, ctx->stream));
   else CK(vec_copy(W, X, (long long)m * n, ctx->stream));
   CK(scaled_norm2(W, (long long)p * q, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
   // 1-2. R = L^H from the Householder LQ of the rows of Xr
-  CK(svd_lq(W, p, q, beta, lqstate, ctx->stream));
+  {
+    // algorithmic FP64 flops: per step j the norm of the tail (4 (q-j)) and,
+    // per later row, the product with the reflector and the update (16 (q-j))
+    double f = 0.0;
+    for (int j = 0; j < k; ++j) f += 4.0 * (q - j) + 16.0 * (q - j) * (p - j - 1);
+    ctx->lq_flops += f;
+    Scope lq_scope(ctx, P_LQ, f);
+    CK(svd_lq(W, p, q, beta, lqstate, ctx->stream));
+  }
   CK(svd_lq_r(W, beta, p, q, R, ctx->stream));
   // 3. one-sided Jacobi on the k rows (length p) of R
-  CK(jacobi_rows(R, k, p, kJacobiSweeps, std::max(1e-15, p * kEps), anorm2, skip_weight(cutoff),
-                 jstate, stamps, ctx->stream));
+  {
+    Scope jacobi_scope(ctx, P_JACOBI);
+    CK(jacobi_rows(R, k, p, kJacobiSweeps, std::max(1e-15, p * kEps), anorm2, skip_weight(cutoff),
+                   chi_max, jstate, stamps, wts, ctx->stream));
+  }
   // 4. singular values, order and rank
   int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
   double* disc_dev = ctx->dscal + 7;
@@ -394,6 +410,8 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   CK(cudaMemcpyAsync(&ctx->hr->counter, jstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->pad, jstate + 5, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->lq_err, lqstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->hr->pairs, jstate + 6, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));
@@ -403,6 +421,9 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   ctx->jacobi_sweeps_total += ctx->hr->pad;
   ctx->jacobi_splits += 1;
   ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
+  // algorithmic FP64 flops of the Jacobi: 16 per element and examined pair
+  // (three inner products), 20 per element and rotated pair (the rotation)
+  ctx->jacobi_flops += (16.0 * ctx->hr->pairs[0] + 20.0 * ctx->hr->pairs[1]) * p;
   const int r = ctx->hr->rank;
   if (r < 1 || r > k) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
   if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
@@ -843,7 +864,7 @@ ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free
   ctx->dscal = (double*)dev_alloc(ctx, 64 * sizeof(double) + kPartialSlots * sizeof(double));
   ctx->dcplx = (cplx*)dev_alloc(ctx, 512 * sizeof(cplx));
   ctx->partial = (cplx*)dev_alloc(ctx, (size_t)kPartialSlots * sizeof(cplx));
-  ctx->dcounter = (int*)dev_alloc(ctx, 32 * sizeof(int));
+  ctx->dcounter = (int*)dev_alloc(ctx, 64 * sizeof(int));
   if (cudaMallocHost((void**)&ctx->hr, sizeof(HostRead)) != cudaSuccess) ctx->hr = nullptr;
   if (!ctx->gm || !ctx->dscal || !ctx->dcplx || !ctx->partial || !ctx->dcounter || !ctx->hr) {
     ite_ctx_destroy(ctx);
@@ -870,7 +891,7 @@ void ite_ctx_destroy(ite_ctx ctx) {
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
   dev_free(ctx, ctx->dcplx, 512 * sizeof(cplx));
   dev_free(ctx, ctx->partial, (size_t)kPartialSlots * sizeof(cplx));
-  dev_free(ctx, ctx->dcounter, 32 * sizeof(int));
+  dev_free(ctx, ctx->dcounter, 64 * sizeof(int));
   if (ctx->hr) cudaFreeHost(ctx->hr);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -882,13 +903,19 @@ size_t ite_ctx_device_bytes(ite_ctx ctx) { return ctx ? ctx->bytes : 0; }
 
 unsigned long long ite_kernel_launches(void) { return ite::launches(); }
 
-ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max) {
+ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max,
+                         double fp64_flops[2]) {
   if (!ctx) return ITE_EINVAL;
   if (splits) *splits = ctx->jacobi_splits;
   if (sweeps_total) *sweeps_total = ctx->jacobi_sweeps_total;
   if (sweeps_max) *sweeps_max = ctx->jacobi_sweeps_max;
+  if (fp64_flops) {
+    fp64_flops[0] = ctx->lq_flops;
+    fp64_flops[1] = ctx->jacobi_flops;
+  }
   ctx->jacobi_splits = ctx->jacobi_sweeps_total = 0;
   ctx->jacobi_sweeps_max = 0;
+  ctx->jacobi_flops = ctx->lq_flops = 0.0;
   return ITE_OK;
 }
 
@@ -900,11 +927,12 @@ ite_status ite_profile_start(ite_ctx ctx) {
   return ITE_OK;
 }
 
-ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long long counts[8]) {
+ite_status ite_profile_stop(ite_ctx ctx, double ms[ITE_PROFILE_SLOTS],
+                            double flops[ITE_PROFILE_SLOTS], long long counts[ITE_PROFILE_SLOTS]) {
   if (!ctx) return ITE_EINVAL;
   ctx->prof = false;
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < ITE_PROFILE_SLOTS; ++k) {
     if (ms) ms[k] = 0.0;
     if (flops) flops[k] = 0.0;
     if (counts) counts[k] = 0;
@@ -912,7 +940,7 @@ ite_status ite_profile_stop(ite_ctx ctx, double ms[8], double flops[8], long lon
   for (const auto& r : ctx->recs) {
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, ctx->evpool[r.e0], ctx->evpool[r.e1]));
-    if (r.cat < 0 || r.cat >= 8) continue;
+    if (r.cat < 0 || r.cat >= ITE_PROFILE_SLOTS) continue;
     if (ms) ms[r.cat] += t;
     if (flops) flops[r.cat] += r.flops;
     if (counts) counts[r.cat] += 1;

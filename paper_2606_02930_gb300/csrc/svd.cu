@@ -20,7 +20,8 @@
 namespace ite {
 namespace {
 
-constexpr int JT = 128;
+constexpr int JT = 128;   // threads of the LQ and row-norm blocks
+constexpr int JW = 2;     // warps (pairs in flight) per Jacobi block
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -155,102 +156,268 @@ __global__ void k_lq_r(const cplx* W, const cplx* beta, int p, int q, int k, cpl
 }
 
 // ---------------------------------------------------------- one-sided Jacobi
-// One Jacobi rotation on rows u, v (length len) of A: make the pair orthogonal
-// if |gamma| > tol sqrt(alpha beta).  Called by all JT threads of a block;
-// returns (to every thread) whether the rows were rotated.
-__device__ bool jacobi_pair(cplx* A, int len, int u, int v, double tol, double skip, int* counter) {
-  __shared__ double sh[2][2][JT / 32];
-  if (u > v) { const int t = u; u = v; v = t; }
+// GB300 runs FP64 on a narrow pipe (2 DFMA per clock per SM), so the Jacobi
+// is arranged to issue little besides the inner products and the rotation
+// itself: one warp per pair of rows, each lane holding its len/32 elements of
+// both rows in registers (one load, one store), warp-shuffle reductions (no
+// block barrier), and the rotation parameters computed by lane 0 alone.
+
+// words of the Jacobi state (dev_state, 16 words)
+constexpr int S_ARRIVE = 0, S_GEN = 1, S_CNT = 2, S_ERR = 4, S_SWEEPS = 5, S_EXAMINED = 6,
+              S_ROTATED = 7, S_MAXW = 8;   // S_CNT: 2 counters; S_MAXW: 2 doubles (4 words)
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct PairOut {
+  bool rotated, counted;
+  double al, be;       // squared norms before the rotation (lane 0)
+};
+
+// Rotation of one pair given the lane-0 sums; fills c, sr, si (lane 0) and
+// the flags broadcast to the warp.
+__device__ __forceinline__ void pair_decide(double sa, double sb, double gr, double gi, double tol,
+                                            double skip, double& c, double& sr, double& si,
+                                            PairOut& out) {
+  const int lane = threadIdx.x & 31;
+  int flags = 0;                               // bit 0 rotate, bit 1 counted
+  c = 1.0;
+  sr = si = 0.0;
+  if (lane == 0) {
+    const double al = sa, be = sb;
+    const double gabs = hypot(gr, gi);
+    // A pair of rows both below the skip weight can never be kept: their
+    // mutual orthogonality does not matter (their total weight does, and
+    // rotations preserve it).
+    if (gabs > tol * sqrt(al * be) && gabs > 0.0 && (al > skip || be > skip)) {
+      const double zeta = (be - al) / (2.0 * gabs);
+      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      c = 1.0 / sqrt(1.0 + t * t);
+      const double sn = c * t / gabs;
+      sr = sn * gr;
+      si = sn * gi;                            // s e^{i theta}
+      flags = 1;
+      // Only rotations by an angle above tol between two rows above the skip
+      // weight count towards another sweep.  Rotations against rows below it
+      // are still applied, but those rows are never rotated among themselves,
+      // so they stay a non-orthogonal set, and orthogonalising a kept row
+      // against all of them one pair at a time converges only slowly; its
+      // overlap with them changes the kept product at second order.
+      if (fabs(t) > tol && al > skip && be > skip) flags |= 2;
+    }
+    out.al = al;
+    out.be = be;
+  }
+  flags = __shfl_sync(0xffffffffu, flags, 0);
+  out.rotated = (flags & 1) != 0;
+  out.counted = (flags & 2) != 0;
+  if (out.rotated) {
+    c = __shfl_sync(0xffffffffu, c, 0);
+    sr = __shfl_sync(0xffffffffu, sr, 0);
+    si = __shfl_sync(0xffffffffu, si, 0);
+  }
+}
+
+// a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
+__device__ __forceinline__ void rotate(cplx& x, cplx& y, double c, double sr, double si) {
+  const cplx x0 = x, y0 = y;
+  x = cmake(c * x0.x - (sr * y0.x + si * y0.y), c * x0.y - (sr * y0.y - si * y0.x));
+  y = cmake((sr * x0.x - si * x0.y) + c * y0.x, (sr * x0.y + si * x0.x) + c * y0.y);
+}
+
+// One Jacobi rotation on rows u < v (length len <= 32 EPL) of A by the 32
+// lanes of a warp, the rows held in registers.
+template <int EPL>
+__device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double skip) {
+  const int lane = threadIdx.x & 31;
+  cplx* au = A + (long long)u * len;
+  cplx* av = A + (long long)v * len;
+  cplx x[EPL], y[EPL];
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    const int e = lane + 32 * i;
+    x[i] = e < len ? au[e] : cmake(0.0, 0.0);
+    y[i] = e < len ? av[e] : cmake(0.0, 0.0);
+  }
+  double sa = 0, sb = 0, gr = 0, gi = 0;
+#pragma unroll
+  for (int i = 0; i < EPL; ++i) {
+    sa = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, sa));
+    sb = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, sb));
+    gr = fma(x[i].x, y[i].x, fma(x[i].y, y[i].y, gr));     // Re(conj(x) y)
+    gi = fma(x[i].x, y[i].y, fma(-x[i].y, y[i].x, gi));    // Im(conj(x) y)
+  }
+  sa = warp_allsum(sa);
+  sb = warp_allsum(sb);
+  gr = warp_allsum(gr);
+  gi = warp_allsum(gi);
+  PairOut out;
+  double c, sr, si;
+  pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
+  if (out.rotated) {
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+      const int e = lane + 32 * i;
+      rotate(x[i], y[i], c, sr, si);
+      if (e < len) {
+        au[e] = x[i];
+        av[e] = y[i];
+      }
+    }
+  }
+  return out;
+}
+
+// The same for rows of any length, streamed from memory twice.
+__device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, double skip) {
+  const int lane = threadIdx.x & 31;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   double sa = 0, sb = 0, gr = 0, gi = 0;
-  for (int e = threadIdx.x; e < len; e += JT) {
+#pragma unroll 4
+  for (int e = lane; e < len; e += 32) {
     const cplx x = au[e], y = av[e];
     sa = fma(x.x, x.x, fma(x.y, x.y, sa));
     sb = fma(y.x, y.x, fma(y.y, y.y, sb));
-    gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // Re(conj(x) y)
-    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));    // Im(conj(x) y)
+    gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
   }
-  block_sum2(sa, sb, sh[0]);
-  block_sum2(gr, gi, sh[1]);
-  const double al = sa, be = sb;
-  const double gabs = hypot(gr, gi);
-  // A pair of rows both below the skip weight can never be kept: their
-  // mutual orthogonality does not matter (their total weight does, and
-  // rotations preserve it).
-  if (!(gabs > tol * sqrt(al * be) && gabs > 0.0 && (al > skip || be > skip))) return false;
-  const double zeta = (be - al) / (2.0 * gabs);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t);
-  const double sn = c * t;
-  const double sr = sn * gr / gabs, si = sn * gi / gabs;   // s e^{i theta}
-  // Only rotations by an angle above tol between two rows that can be kept
-  // keep the sweeps going.  Rotations against rows below the skip weight are
-  // still applied, but those rows are never rotated among themselves, so they
-  // stay a non-orthogonal set, and orthogonalising a kept row against all of
-  // them one pair at a time converges only slowly; its overlap with them
-  // changes the kept product at second order.
-  if (threadIdx.x == 0 && fabs(t) > tol && al > skip && be > skip) atomicAdd(counter, 1);
-  // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
-  for (int e = threadIdx.x; e < len; e += JT) {
-    const cplx x = au[e], y = av[e];
-    au[e] = cmake(c * x.x - (sr * y.x + si * y.y), c * x.y - (sr * y.y - si * y.x));
-    av[e] = cmake((sr * x.x - si * x.y) + c * y.x, (sr * x.y + si * x.x) + c * y.y);
+  sa = warp_allsum(sa);
+  sb = warp_allsum(sb);
+  gr = warp_allsum(gr);
+  gi = warp_allsum(gi);
+  PairOut out;
+  double c, sr, si;
+  pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
+  if (out.rotated) {
+#pragma unroll 4
+    for (int e = lane; e < len; e += 32) {
+      cplx x = au[e], y = av[e];
+      rotate(x, y, c, sr, si);
+      au[e] = x;
+      av[e] = y;
+    }
   }
-  return true;
+  return out;
 }
 
-__global__ void __launch_bounds__(JT)
-k_jacobi_round(cplx* A, int rows, int len, int round, int pp, double tol, const double* anorm2,
-               double skip_rel, int* counter) {
-  const int k = blockIdx.x;
-  const int u = player(k, round, pp), v = player(pp - 1 - k, round, pp);
-  if (u >= rows || v >= rows) return;
+__device__ __forceinline__ PairOut jacobi_pair(cplx* A, int len, int u, int v, double tol,
+                                               double skip) {
+  if (u > v) { const int t = u; u = v; v = t; }
+  if (len <= 128) return pair_regs<4>(A, len, u, v, tol, skip);
+  if (len <= 256) return pair_regs<8>(A, len, u, v, tol, skip);
+  if (len <= 512) return pair_regs<16>(A, len, u, v, tol, skip);
+  return pair_stream(A, len, u, v, tol, skip);
+}
+
+// A single pair (rows == 2), one warp.
+__global__ void __launch_bounds__(32)
+k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_rel,
+               unsigned int* st) {
   const double a2 = anorm2 ? *anorm2 : 0.0;
-  jacobi_pair(A, len, u, v, tol, skip_rel * a2, counter);
+  const PairOut o = jacobi_pair(A, len, 0, 1, tol, skip_rel * a2);
+  if (threadIdx.x == 0) {
+    if (o.counted) atomicAdd(st + S_CNT, 1u);
+    atomicAdd(st + S_EXAMINED, 1u);
+    if (o.rotated) atomicAdd(st + S_ROTATED, 1u);
+  }
 }
 
-// All sweeps of the round-robin one-sided Jacobi in one cooperative launch.
-// st[2], st[3]: rotation counters of even / odd sweeps; st[5]: sweeps done.
-// A sweep's counter is read by every block after the sweep's last barrier;
-// the counter of the following sweep is cleared by block 0 in round 1 of the
-// current sweep, after every block has passed round 0 (and so has finished
-// reading it two sweeps ago).
+// All sweeps of the round-robin one-sided Jacobi in one cooperative launch;
+// pair k of a round goes to warp k of the grid (and k + warps, ...).
+//
+// Termination.  A sweep whose rotations all left the pairs orthogonal to tol
+// ends the iteration.  So does a sweep in which every rotation that still
+// counted involved a row too light to be kept: with maxw the largest
+// min(alpha, beta) over the counted rotations of the sweep, if at least
+// keep_rank rows weigh more than maxw / kKeepMargin the truncation, which
+// keeps at most keep_rank rows, keeps none of the light ones, and finishing
+// those rotations would change each heavier row by only |t| sqrt(beta/alpha).
+// wts[row] holds the row's squared norm when it was last examined.
+//
+// Words of st: S_CNT, S_CNT+1 rotation counters of even / odd sweeps and
+// S_MAXW.. their maxw (as ordered bit patterns); S_SWEEPS sweeps done;
+// S_EXAMINED, S_ROTATED the work done.  A sweep's counter is read by every
+// block after the sweep's last barrier; the counter of the following sweep is
+// cleared by block 0 in round 1 of the current sweep, after every block has
+// passed round 0 (and so has finished reading it two sweeps ago).
 // stamps[row] holds the global round at which the row was last rotated.  The
 // tournament repeats every sweep, so a pair was last examined pp-1 rounds ago;
 // if neither row has been rotated since then (a rotation at that very round
 // left the pair orthogonal), examining it again cannot fire and is skipped.
-__global__ void __launch_bounds__(JT)
+constexpr double kKeepMargin = 1e-2;
+__global__ void __launch_bounds__(JW * 32)
 k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double* anorm2,
-                    double skip_rel, int max_sweeps, unsigned int* st, int* stamps) {
+                    double skip_rel, int max_sweeps, int keep_rank, unsigned int* st, int* stamps,
+                    double* wts) {
   const unsigned int nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * JW + (threadIdx.x >> 5), nw = (int)nb * JW;
   const double skip = skip_rel * (anorm2 ? *anorm2 : 0.0);
-  int* counters = reinterpret_cast<int*>(st + 2);
+  int* counters = reinterpret_cast<int*>(st + S_CNT);
+  unsigned long long* maxws = reinterpret_cast<unsigned long long*>(st + S_MAXW);
+  unsigned int examined = 0, rotations_done = 0;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int* cnt = counters + (sw & 1);
+    unsigned long long* maxw = maxws + (sw & 1);
     for (int r = 0; r < pp - 1; ++r) {
-      if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[(sw + 1) & 1] = 0;
+      if (r == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        counters[(sw + 1) & 1] = 0;
+        maxws[(sw + 1) & 1] = 0ull;
+      }
       const int g = sw * (pp - 1) + r;
-      for (int k = blockIdx.x; k < pp / 2; k += nb) {
-        const int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
+      for (int k = wid; k < pp / 2; k += nw) {
+        int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
         if (u >= rows || v >= rows) continue;
+        if (u > v) { const int t = u; u = v; v = t; }
         if (sw > 0) {
+          // read through L2 so that every lane sees the same stamps and the
+          // warp takes one branch
           const int last = g - (pp - 1);
-          // read through L2 so that every thread of the block sees the same
-          // stamps and takes the same branch
           if (__ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) continue;
         }
-        const bool rotated = jacobi_pair(A, len, u, v, tol, skip, cnt);
-        if (rotated && threadIdx.x == 0) {
-          stamps[u] = g;
-          stamps[v] = g;
+        const PairOut o = jacobi_pair(A, len, u, v, tol, skip);
+        ++examined;
+        if (lane == 0) {
+          wts[u] = o.al;
+          wts[v] = o.be;
+        }
+        if (o.rotated) {
+          ++rotations_done;
+          if (lane == 0) {
+            stamps[u] = g;
+            stamps[v] = g;
+            if (o.counted) {
+              atomicAdd(cnt, 1);
+              // squared norms are non-negative: their bit patterns order like them
+              atomicMax(maxw, (unsigned long long)__double_as_longlong(fmin(o.al, o.be)));
+            }
+          }
         }
       }
-      if (!grid_barrier(st, nb)) return;
+      if (!grid_barrier(st, nb)) break;
     }
+    if (*((volatile unsigned int*)(st + S_ERR)) != 0u) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[S_SWEEPS] = (unsigned int)(sw + 1);
     const int rotations = *((volatile int*)cnt);
-    if (blockIdx.x == 0 && threadIdx.x == 0) st[5] = (unsigned int)(sw + 1);
     if (rotations == 0) break;
+    if (keep_rank < rows) {
+      // same data and order in every block, so every block decides alike
+      const double thr = __longlong_as_double((long long)__ldcg(maxw)) / kKeepMargin;
+      int heavy = 0;
+      for (int i0 = 0; i0 < rows; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        heavy += __syncthreads_count(i < rows && __ldcg(wts + i) > thr);
+      }
+      if (heavy >= keep_rank) break;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(st + S_EXAMINED, examined);
+    atomicAdd(st + S_ROTATED, rotations_done);
   }
 }
 
@@ -373,13 +540,13 @@ int grid_for(long long tot) {
 // device (the grid of a cooperative launch), cached per kernel and device.
 struct Coresident {
   int dev = -1, blocks = 0;
-  cudaError_t get(const void* kernel, int* out) {
+  cudaError_t get(const void* kernel, int threads, int* out) {
     int d = 0;
     cudaError_t e = cudaGetDevice(&d);
     if (e != cudaSuccess) return e;
     if (d != dev) {
       int per_sm = 0, sms = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, JT, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
       if (e != cudaSuccess) return e;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
       if (e != cudaSuccess) return e;
@@ -399,7 +566,7 @@ cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, c
   if (err != cudaSuccess) return err;
   if (p < 1 || q < 1) return cudaSuccess;
   int max_blocks = 0;
-  err = g_lq_blocks.get((const void*)k_lq_persistent, &max_blocks);
+  err = g_lq_blocks.get((const void*)k_lq_persistent, JT, &max_blocks);
   if (err != cudaSuccess) return err;
   int nblk = p - 1;
   if (nblk > max_blocks) nblk = max_blocks;
@@ -418,9 +585,9 @@ cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cud
 }
 
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
-                        const double* anorm2, double skip_rel, unsigned int* dev_state,
-                        int* stamps, cudaStream_t st) {
-  cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
+                        const double* anorm2, double skip_rel, int keep_rank,
+                        unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, 16 * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (rows < 2) return cudaSuccess;
   err = cudaMemsetAsync(stamps, 0, sizeof(int) * rows, st);
@@ -428,22 +595,22 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
   const int pp = rows + (rows & 1);
   if (pp == 2) {
     // a single pair: one rotation makes it orthogonal; a second launch confirms
-    int* cnt = reinterpret_cast<int*>(dev_state + 2);
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<<<1, JT, 0, st>>>(A, rows, len, 0, pp, tol, anorm2, skip_rel, cnt);
+      k_jacobi_round<<<1, 32, 0, st>>>(A, len, tol, anorm2, skip_rel, dev_state);
     }
     return cudaGetLastError();
   }
   int max_blocks = 0;
-  err = g_jacobi_blocks.get((const void*)k_jacobi_persistent, &max_blocks);
+  err = g_jacobi_blocks.get((const void*)k_jacobi_persistent, JW * 32, &max_blocks);
   if (err != cudaSuccess) return err;
-  int nblk = pp / 2;
+  int nblk = (pp / 2 + JW - 1) / JW;
   if (nblk > max_blocks) nblk = max_blocks;
-  void* args[] = {&A, &rows, &len, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &dev_state,
-                  &stamps};
+  void* args[] = {&A, &rows, &len, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &keep_rank,
+                  &dev_state, &stamps, &wts};
   count_launches(1);
-  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JT), args, 0, st);
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JW * 32), args, 0,
+                                     st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

@@ -139,12 +139,13 @@ def test_split_matches_oracle(api, ctx, m, n, kind):
                                   sig)
             assert r == r_ref
             assert abs(disc - disc_ref) <= 1e-12 * max(disc_ref, 1e-12) + 1e-15
-            # singular values are resolved down to the skip weight
-            # 1e-3 max(cutoff, 1e-25) of the total; below it only the block's
-            # total weight is exact
+            # singular values are resolved for the first chi_max entries down
+            # to the skip weight 1e-3 max(cutoff, 1e-25) of the total; beyond
+            # them only the total weight is exact
             sg = sig.cpu().numpy()
             tot = np.sum(S_ref ** 2)
             res = S_ref ** 2 > 1e-3 * max(cutoff, 1e-25) * tot * 10
+            res[chi_max:] = False
             assert np.allclose(sg[res], S_ref[res], rtol=0, atol=1e-13 * S_ref[0])
             assert abs(np.sum(sg[~res] ** 2) - np.sum(S_ref[~res] ** 2)) <= 1e-13 * tot
             Lh = to_host(left)[: m * r].reshape(m, r)
