@@ -147,18 +147,33 @@ cudaError_t gmres_collect(GmresState* s, int j, int m, const cplx* h1, const cpl
 // its part left of the diagonal as L[j][0..j) and beta[j] receives L[j][j].
 // One cooperative launch; dev_state (8 device words) gets a nonzero word 4 if
 // a grid-barrier wait ran out.
-cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, cudaStream_t st);
+// refl (device, 3 k doubles, may be NULL) receives each reflector's
+// (Re u_0, Im u_0, c) for lq_formq.
+cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, double* refl, unsigned int* dev_state,
+                   cudaStream_t st);
+// L (p x k, row-major) with Xr = L Q^H from the output of svd_lq
+cudaError_t lq_left(const cplx* W, const cplx* beta, int p, int q, cplx* Lout, cudaStream_t st);
+// *out = |L1^{-1}|_F^2 for the leading k x k triangle L1 of svd_lq's L (+inf
+// if a pivot is zero); colnorm2 (k doubles) is scratch.  sigma_min(Xr)^2 >=
+// 1 / *out.
+cudaError_t lq_inv_fnorm2(const cplx* W, const cplx* beta, int q, int k, double* colnorm2,
+                          double* out, cudaStream_t st);
+// Qh (k x q) = Q^H, the orthonormal rows with Xr = L Q^H, from svd_lq's
+// output and refl.  One cooperative launch; dev_state (8 words) as svd_lq.
+cudaError_t lq_formq(const cplx* W, const double* refl, int q, int k, cplx* Qh,
+                     unsigned int* dev_state, cudaStream_t st);
 // R (k x p, k = min(p, q)) = L^H from the output of svd_lq
 cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cudaStream_t st);
 // One-sided Jacobi on the rows (length len) of A until they are mutually
 // orthogonal; no rotation is accumulated.  One cooperative launch;
-// dev_state (16 device words) returns the sweeps done in word 5, the pairs
-// examined and rotated in words 6 and 7, and a nonzero word 4 if a
-// grid-barrier wait ran out; stamps (rows ints) and wts (rows doubles) are
-// device scratch.  *anorm2 (device) is |A|_F^2: pairs of rows whose squared
-// norms are both <= skip_rel |A|_F^2 are left as they are.  keep_rank is the
-// most rows the caller will keep: the sweeps stop once only rows that cannot
-// be among them are still rotating (keep_rank >= rows disables this).
+// dev_state (24 device words) returns the sweeps done in word 5, the pairs
+// examined and rotated in words 6 and 7, and a nonzero word 4 if a bounded
+// wait ran out; stamps (rows ints) and wts (rows doubles) are device
+// scratch.  *anorm2 (device) is |A|_F^2: pairs of
+// rows whose squared norms are both <= skip_rel |A|_F^2 are left as they are.
+// keep_rank is the most rows the caller will keep: the sweeps stop once only
+// rows that cannot be among them are still rotating (keep_rank >= rows
+// disables this).
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
                         unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st);

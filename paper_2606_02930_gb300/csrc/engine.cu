@@ -48,8 +48,8 @@ constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay 
 // such rows against each other (their total weight is exact regardless).
 double skip_weight(double cutoff) { return 1e-3 * std::max(cutoff, kWeightFloor * 0.1); }
 // small SVD workspace for k rows: sigma, sorted (double), beta (complex),
-// wts (double), perm, stamps (int)
-size_t small_bytes(long long k) { return (size_t)k * (3 * sizeof(double) + sizeof(cplx) + 2 * sizeof(int)) + 256; }
+// wts (double), perm, stamps, done (int)
+size_t small_bytes(long long k) { return (size_t)k * (3 * sizeof(double) + sizeof(cplx) + 3 * sizeof(int)) + 256; }
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -376,9 +376,9 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   double* wts = reinterpret_cast<double*>(beta + k);
   int* perm = reinterpret_cast<int*>(wts + k);
   int* stamps = perm + k;
-  // dcounter words: 8-10 GEMM error flags, 16-31 Jacobi state, 32-39 LQ state
+  // dcounter words: 8-10 GEMM error flags, 16-39 Jacobi state, 40-47 LQ state
   unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 16;
-  unsigned int* lqstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 32;
+  unsigned int* lqstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 40;
   double* anorm2 = ctx->dscal + 8;
   if (tr) CK(conj_transpose(X, m, n, W, ctx->stream));
   else CK(vec_copy(W, X, (long long)m * n, ctx->stream));
@@ -391,7 +391,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
     for (int j = 0; j < k; ++j) f += 4.0 * (q - j) + 16.0 * (q - j) * (p - j - 1);
     ctx->lq_flops += f;
     Scope lq_scope(ctx, P_LQ, f);
-    CK(svd_lq(W, p, q, beta, lqstate, ctx->stream));
+    CK(svd_lq(W, p, q, beta, nullptr, lqstate, ctx->stream));
   }
   CK(svd_lq_r(W, beta, p, q, R, ctx->stream));
   // 3. one-sided Jacobi on the k rows (length p) of R
@@ -742,6 +742,46 @@ ite_status set_one(ite_ctx ctx, cplx* p) {
 }
 
 // gauge move: sites N-1..1 right-orthonormal by SVD (weight floor only)
+// Gauge move of one site tensor X (m x n, rows = left bond) when it has full
+// rank: X = L Q^H by the Householder LQ, right = Q^H (orthonormal rows),
+// left = L.  The SVD split that the gauge move is defined by keeps every
+// singular value above the weight floor; when sigma_min(X)^2 is certified
+// above 1e-20 |X|^2 (four decades over the floor) it keeps all min(m, n) of
+// them, and its factors (V^dag, U S) differ from (Q^H, L) only by a unitary on
+// the new bond, under which the sweep that follows is covariant.  The
+// certificate is 1 / |L1^{-1}|_F^2 <= sigma_min(L1)^2 <= sigma_min(X)^2 for
+// the leading triangle L1.  *ok = false (nothing written) when it fails.
+constexpr double kGaugeCertRel = 1e-20;
+ite_status gauge_lq(ite_ctx ctx, const cplx* X, int m, int n, cplx* left, cplx* right, bool* ok) {
+  *ok = false;
+  const int k = std::min(m, n);
+  CS(buf_ensure(ctx, ctx->ws_svdA, (size_t)m * n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_small, small_bytes(k)));
+  cplx* W = P<cplx>(ctx->ws_svdA);
+  cplx* beta = P<cplx>(ctx->ws_small);
+  double* refl = reinterpret_cast<double*>(beta + k);
+  double* colnorm = refl + 3 * k;
+  unsigned int* lqstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 40;
+  double* anorm2 = ctx->dscal + 8;
+  double* inv2 = ctx->dscal + 10;
+  CK(vec_copy(W, X, (long long)m * n, ctx->stream));
+  CK(scaled_norm2(W, (long long)m * n, 1.0, anorm2, ctx->dscal + 16, ctx->stream));
+  CK(svd_lq(W, m, n, beta, refl, lqstate, ctx->stream));
+  CK(lq_inv_fnorm2(W, beta, n, k, colnorm, inv2, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->d[2], anorm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->d[3], inv2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->lq_err, lqstate + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->lq_err != 0) return fail(ctx, ITE_ETIMEOUT, "LQ grid barrier wait ran out");
+  const double total = ctx->hr->d[2], inv = ctx->hr->d[3];
+  if (!(total > 0.0) || !std::isfinite(inv) || !(inv > 0.0) || 1.0 / inv <= kGaugeCertRel * total)
+    return ITE_OK;
+  CK(lq_left(W, beta, m, n, left, ctx->stream));
+  CK(lq_formq(W, refl, n, k, right, lqstate, ctx->stream));
+  *ok = true;
+  return ITE_OK;
+}
+
 ite_status right_canonicalize(ite_ctx ctx, ite_mps x) {
   Scope sc(ctx, P_GAUGE);
   const int d = x->d;
@@ -750,7 +790,10 @@ ite_status right_canonicalize(ite_ctx ctx, ite_mps x) {
     int r = 0;
     double disc = 0.0;
     cplx* left = P<cplx>(ctx->ws_left);
-    CS(split(ctx, x->site[i], chl, d * chr, 1 << 30, 0.0, false, left, x->site[i], &r, &disc));
+    bool done = false;
+    CS(gauge_lq(ctx, x->site[i], chl, d * chr, left, x->site[i], &done));
+    if (done) r = std::min(chl, d * chr);
+    else CS(split(ctx, x->site[i], chl, d * chr, 1 << 30, 0.0, false, left, x->site[i], &r, &disc));
     // x_{i-1} <- x_{i-1} (U S)
     const int chll = x->chi[i - 1];
     cplx* T = P<cplx>(ctx->ws_X2);

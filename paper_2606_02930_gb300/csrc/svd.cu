@@ -56,7 +56,8 @@ __device__ __forceinline__ int player(int pos, int round, int pp) {
 
 // Grid-wide barrier for a cooperative launch.  st[0] arrivals, st[1]
 // generation, st[4] error flag.  Waits are bounded: after ~2^24 polls the
-// error flag is set and the block leaves (the caller then exits).
+// error flag is set and the block leaves (the caller then exits); a wait also
+// gives up as soon as another block has set the flag.
 __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -71,6 +72,7 @@ __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
     } else {
       unsigned long long spins = 0;
       while (*gen == g) {
+        if (*((volatile unsigned int*)(st + 4)) != 0u) break;
         if (++spins > (1ull << 24)) {
           atomicExch(st + 4, 1u);
           break;
@@ -94,7 +96,7 @@ __device__ bool grid_barrier(unsigned int* st, unsigned int nblocks) {
 // block recomputes the reflector of step j from row j, which no block writes
 // during step j; one grid barrier separates the steps.
 __global__ void __launch_bounds__(JT)
-k_lq_persistent(cplx* W, int p, int q, cplx* beta, unsigned int* st) {
+k_lq_persistent(cplx* W, int p, int q, cplx* beta, double* refl, unsigned int* st) {
   __shared__ double sh[2][JT / 32];
   __shared__ double hs[3];
   const int k = p < q ? p : q;
@@ -108,10 +110,17 @@ k_lq_persistent(cplx* W, int p, int q, cplx* beta, unsigned int* st) {
       const cplx x0 = x[j];
       const double nx = sqrt(s), a0 = hypot(x0.x, x0.y);
       const double phr = a0 > 0.0 ? x0.x / a0 : 1.0, phi = a0 > 0.0 ? x0.y / a0 : 0.0;
-      if (blockIdx.x == 0) beta[j] = cmake(-phr * nx, -phi * nx);
       hs[0] = phr * (a0 + nx);
       hs[1] = phi * (a0 + nx);
       hs[2] = nx > 0.0 ? 1.0 / (nx * (nx + a0)) : 0.0;
+      if (blockIdx.x == 0) {
+        beta[j] = cmake(-phr * nx, -phi * nx);
+        if (refl) {
+          refl[3 * j] = hs[0];
+          refl[3 * j + 1] = hs[1];
+          refl[3 * j + 2] = hs[2];
+        }
+      }
     }
     __syncthreads();
     const double c = hs[2];
@@ -155,6 +164,127 @@ __global__ void k_lq_r(const cplx* W, const cplx* beta, int p, int q, int k, cpl
   }
 }
 
+// L (p x k, row-major, lower trapezoidal) from the output of the LQ
+__global__ void k_lq_left(const cplx* W, const cplx* beta, int p, int q, int k, cplx* Lout) {
+  const long long tot = (long long)p * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    cplx v = cmake(0.0, 0.0);
+    if (j < i) v = W[(long long)i * q + j];
+    else if (j == i) v = beta[i];
+    Lout[e] = v;
+  }
+}
+
+// |column c of L1^{-1}|^2 for the leading k x k triangle L1 of the LQ, by
+// forward substitution (one warp per column, the solution in shared memory):
+// z_c = 1 / L_cc, z_i = -(sum_{c <= j < i} L_ij z_j) / L_ii.  A zero pivot
+// gives +inf.
+__global__ void __launch_bounds__(32)
+k_tri_inv_colnorm(const cplx* W, const cplx* beta, int q, int k, double* colnorm2) {
+  extern __shared__ cplx zs[];
+  const int c = blockIdx.x, lane = threadIdx.x;
+  double acc = 0.0;
+  bool singular = false;
+  for (int i = c; i < k && !singular; ++i) {
+    double sr = 0.0, si = 0.0;
+    if (i > c) {
+      const cplx* row = W + (long long)i * q;
+      for (int j = c + lane; j < i; j += 32) {
+        const cplx l = row[j], z = zs[j];
+        sr = fma(l.x, z.x, fma(-l.y, z.y, sr));
+        si = fma(l.x, z.y, fma(l.y, z.x, si));
+      }
+      sr = warp_sum(sr);
+      si = warp_sum(si);
+    }
+    if (lane == 0) {
+      const cplx b = beta[i];
+      const double bb = b.x * b.x + b.y * b.y;
+      cplx z;
+      if (bb == 0.0) {
+        z = cmake(0.0, 0.0);
+      } else if (i == c) {
+        z = cmake(b.x / bb, -b.y / bb);                    // 1 / b
+      } else {
+        // -(s / b) = -s conj(b) / |b|^2
+        z = cmake(-(sr * b.x + si * b.y) / bb, -(si * b.x - sr * b.y) / bb);
+      }
+      zs[i] = z;
+      acc += z.x * z.x + z.y * z.y;
+      if (bb == 0.0) acc = INFINITY;
+    }
+    singular = __shfl_sync(0xffffffffu, isinf(acc) ? 1 : 0, 0) != 0;
+    __syncwarp();
+  }
+  if (lane == 0) colnorm2[c] = acc;
+}
+
+// *out = sum of x[0..n) in a fixed order (one block)
+__global__ void k_sum_small(const double* x, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+// rows of the k x q identity
+__global__ void k_eye_rows(cplx* Q, int k, int q) {
+  const long long tot = (long long)k * q;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / q), j = (int)(e - (long long)i * q);
+    Q[e] = cmake(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// Q^H (k x q, orthonormal rows) with X = L Q^H, from the reflectors of the
+// LQ: the reflectors are Hermitian, so Q^H is the first k rows of
+// H_{k-1} ... H_0, accumulated backwards: starting from identity rows, step
+// j = k-1, ..., 0 applies y <- y - c_j (y u_j^H) u_j to rows j..k-1 (rows
+// above j are still unit vectors that H_j leaves alone).  One grid barrier
+// separates the steps.
+__global__ void __launch_bounds__(JT)
+k_lq_formq(const cplx* W, const double* refl, int q, int k, cplx* Qh, unsigned int* st) {
+  __shared__ double sh[2][JT / 32];
+  const unsigned int nb = gridDim.x;
+  for (int j = k - 1; j >= 0; --j) {
+    const double c = refl[3 * j + 2];
+    const cplx u0 = cmake(refl[3 * j], refl[3 * j + 1]);
+    const cplx* x = W + (long long)j * q;
+    if (c != 0.0) {
+      for (int i = j + (int)blockIdx.x; i < k; i += (int)nb) {
+        cplx* y = Qh + (long long)i * q;
+        double dr = 0.0, di = 0.0;     // y u^H
+        for (int e = j + threadIdx.x; e < q; e += JT) {
+          const cplx u = e == j ? u0 : x[e];
+          const cplx v = y[e];
+          dr = fma(v.x, u.x, fma(v.y, u.y, dr));
+          di = fma(v.y, u.x, fma(-v.x, u.y, di));
+        }
+        block_sum2(dr, di, sh);
+        const double fr = c * dr, fi = c * di;
+        for (int e = j + threadIdx.x; e < q; e += JT) {
+          const cplx u = e == j ? u0 : x[e];
+          cplx v = y[e];
+          v.x -= fr * u.x - fi * u.y;
+          v.y -= fr * u.y + fi * u.x;
+          y[e] = v;
+        }
+      }
+    }
+    if (!grid_barrier(st, nb)) return;
+  }
+}
+
 // ---------------------------------------------------------- one-sided Jacobi
 // GB300 runs FP64 on a narrow pipe (2 DFMA per clock per SM), so the Jacobi
 // is arranged to issue little besides the inner products and the rotation
@@ -162,9 +292,12 @@ __global__ void k_lq_r(const cplx* W, const cplx* beta, int p, int q, int k, cpl
 // both rows in registers (one load, one store), warp-shuffle reductions (no
 // block barrier), and the rotation parameters computed by lane 0 alone.
 
-// words of the Jacobi state (dev_state, 16 words)
-constexpr int S_ARRIVE = 0, S_GEN = 1, S_CNT = 2, S_ERR = 4, S_SWEEPS = 5, S_EXAMINED = 6,
-              S_ROTATED = 7, S_MAXW = 8;   // S_CNT: 2 counters; S_MAXW: 2 doubles (4 words)
+// words of the Jacobi state (dev_state, 24 words): grid barrier (0, 1), error
+// flag, sweeps done, pairs examined and rotated, two per-sweep rotation
+// counters and two per-sweep maxw values (64-bit, 8-byte aligned)
+constexpr int S_ARRIVE = 0, S_GEN = 1, S_ERR = 4, S_SWEEPS = 5, S_EXAMINED = 6, S_ROTATED = 7,
+              S_CNT = 8, S_MAXW = 12, S_WORDS = 24;
+static_assert(S_ERR == 4, "grid_barrier uses word 4 as its error flag");
 
 __device__ __forceinline__ double warp_allsum(double v) {
 #pragma unroll
@@ -188,15 +321,16 @@ __device__ __forceinline__ void pair_decide(double sa, double sb, double gr, dou
   sr = si = 0.0;
   if (lane == 0) {
     const double al = sa, be = sb;
-    const double gabs = hypot(gr, gi);
+    const double gabs = sqrt(fma(gr, gr, gi * gi));
     // A pair of rows both below the skip weight can never be kept: their
     // mutual orthogonality does not matter (their total weight does, and
     // rotations preserve it).
     if (gabs > tol * sqrt(al * be) && gabs > 0.0 && (al > skip || be > skip)) {
-      const double zeta = (be - al) / (2.0 * gabs);
-      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      c = 1.0 / sqrt(1.0 + t * t);
-      const double sn = c * t / gabs;
+      const double ig = 1.0 / gabs;
+      const double zeta = 0.5 * (be - al) * ig;
+      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+      c = rsqrt(fma(t, t, 1.0));
+      const double sn = c * t * ig;
       sr = sn * gr;
       si = sn * gi;                            // s e^{i theta}
       flags = 1;
@@ -236,19 +370,34 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   cplx x[EPL], y[EPL];
+  // rows come from other SMs' rotations: read them through L2
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const int e = lane + 32 * i;
-    x[i] = e < len ? au[e] : cmake(0.0, 0.0);
-    y[i] = e < len ? av[e] : cmake(0.0, 0.0);
+    x[i] = e < len ? __ldcg(au + e) : cmake(0.0, 0.0);
+    y[i] = e < len ? __ldcg(av + e) : cmake(0.0, 0.0);
   }
-  double sa = 0, sb = 0, gr = 0, gi = 0;
+  // four independent partial sums per quantity keep the dependent FP64
+  // chains short (the pipe's latency, not its rate, bounds one warp)
+  constexpr int NP = EPL < 4 ? EPL : 4;
+  double pa[NP], pb[NP], pr[NP], pi[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) pa[a] = pb[a] = pr[a] = pi[a] = 0.0;
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
-    sa = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, sa));
-    sb = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, sb));
-    gr = fma(x[i].x, y[i].x, fma(x[i].y, y[i].y, gr));     // Re(conj(x) y)
-    gi = fma(x[i].x, y[i].y, fma(-x[i].y, y[i].x, gi));    // Im(conj(x) y)
+    const int a = i % NP;
+    pa[a] = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, pa[a]));
+    pb[a] = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, pb[a]));
+    pr[a] = fma(x[i].x, y[i].x, fma(x[i].y, y[i].y, pr[a]));     // Re(conj(x) y)
+    pi[a] = fma(x[i].x, y[i].y, fma(-x[i].y, y[i].x, pi[a]));    // Im(conj(x) y)
+  }
+  double sa = 0.0, sb = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    sa += pa[a];
+    sb += pb[a];
+    gr += pr[a];
+    gi += pi[a];
   }
   sa = warp_allsum(sa);
   sb = warp_allsum(sb);
@@ -279,7 +428,7 @@ __device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, doubl
   double sa = 0, sb = 0, gr = 0, gi = 0;
 #pragma unroll 4
   for (int e = lane; e < len; e += 32) {
-    const cplx x = au[e], y = av[e];
+    const cplx x = __ldcg(au + e), y = __ldcg(av + e);
     sa = fma(x.x, x.x, fma(x.y, x.y, sa));
     sb = fma(y.x, y.x, fma(y.y, y.y, sb));
     gr = fma(x.x, y.x, fma(x.y, y.y, gr));
@@ -295,7 +444,7 @@ __device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, doubl
   if (out.rotated) {
 #pragma unroll 4
     for (int e = lane; e < len; e += 32) {
-      cplx x = au[e], y = av[e];
+      cplx x = __ldcg(au + e), y = __ldcg(av + e);
       rotate(x, y, c, sr, si);
       au[e] = x;
       av[e] = y;
@@ -327,7 +476,10 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
 }
 
 // All sweeps of the round-robin one-sided Jacobi in one cooperative launch;
-// pair k of a round goes to warp k of the grid (and k + warps, ...).
+// pair slot k of every round goes to warp k of the grid (and k + warps, ...),
+// one grid barrier after every round.  (Tracking each row's completed round
+// instead, so that a pair waits only for its own two rows, measured slower on
+// GB300: the per-pair fence and flag round trip cost more than the barrier.)
 //
 // Termination.  A sweep whose rotations all left the pairs orthogonal to tol
 // ends the iteration.  So does a sweep in which every rotation that still
@@ -338,12 +490,11 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
 // those rotations would change each heavier row by only |t| sqrt(beta/alpha).
 // wts[row] holds the row's squared norm when it was last examined.
 //
-// Words of st: S_CNT, S_CNT+1 rotation counters of even / odd sweeps and
-// S_MAXW.. their maxw (as ordered bit patterns); S_SWEEPS sweeps done;
-// S_EXAMINED, S_ROTATED the work done.  A sweep's counter is read by every
-// block after the sweep's last barrier; the counter of the following sweep is
-// cleared by block 0 in round 1 of the current sweep, after every block has
-// passed round 0 (and so has finished reading it two sweeps ago).
+// The counters and maxw of sweep sw live in slot sw % 2.  A sweep's slot is
+// read by every block after the sweep's last barrier; the slot of the
+// following sweep is cleared by block 0 in round 1 of the current sweep,
+// after every block has passed round 0 (and so has finished reading it two
+// sweeps ago).
 // stamps[row] holds the global round at which the row was last rotated.  The
 // tournament repeats every sweep, so a pair was last examined pp-1 rounds ago;
 // if neither row has been rotated since then (a rotation at that very round
@@ -557,11 +708,12 @@ struct Coresident {
     return blocks > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
   }
 };
-Coresident g_lq_blocks, g_jacobi_blocks;
+Coresident g_lq_blocks, g_jacobi_blocks, g_formq_blocks;
 
 }  // namespace
 
-cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, cudaStream_t st) {
+cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, double* refl, unsigned int* dev_state,
+                   cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (p < 1 || q < 1) return cudaSuccess;
@@ -571,9 +723,49 @@ cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, unsigned int* dev_state, c
   int nblk = p - 1;
   if (nblk > max_blocks) nblk = max_blocks;
   if (nblk < 1) nblk = 1;
-  void* args[] = {&W, &p, &q, &beta, &dev_state};
+  void* args[] = {&W, &p, &q, &beta, &refl, &dev_state};
   count_launches(1);
   return cudaLaunchCooperativeKernel((void*)k_lq_persistent, dim3(nblk), dim3(JT), args, 0, st);
+}
+
+cudaError_t lq_left(const cplx* W, const cplx* beta, int p, int q, cplx* Lout, cudaStream_t st) {
+  const int k = p < q ? p : q;
+  if (k < 1) return cudaSuccess;
+  count_launches(1);
+  k_lq_left<<<grid_for((long long)p * k), 256, 0, st>>>(W, beta, p, q, k, Lout);
+  return cudaGetLastError();
+}
+
+cudaError_t lq_inv_fnorm2(const cplx* W, const cplx* beta, int q, int k, double* colnorm2,
+                          double* out, cudaStream_t st) {
+  if (k < 1) return cudaSuccess;
+  const size_t smem = sizeof(cplx) * (size_t)k;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tri_inv_colnorm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(2);
+  k_tri_inv_colnorm<<<k, 32, smem, st>>>(W, beta, q, k, colnorm2);
+  k_sum_small<<<1, 1024, 0, st>>>(colnorm2, k, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lq_formq(const cplx* W, const double* refl, int q, int k, cplx* Qh,
+                     unsigned int* dev_state, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, 8 * sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
+  if (k < 1) return cudaSuccess;
+  count_launches(1);
+  k_eye_rows<<<grid_for((long long)k * q), 256, 0, st>>>(Qh, k, q);
+  int max_blocks = 0;
+  err = g_formq_blocks.get((const void*)k_lq_formq, JT, &max_blocks);
+  if (err != cudaSuccess) return err;
+  int nblk = k;
+  if (nblk > max_blocks) nblk = max_blocks;
+  void* args[] = {&W, &refl, &q, &k, &Qh, &dev_state};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel((void*)k_lq_formq, dim3(nblk), dim3(JT), args, 0, st);
 }
 
 cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cudaStream_t st) {
@@ -587,7 +779,7 @@ cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cud
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
                         unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st) {
-  cudaError_t err = cudaMemsetAsync(dev_state, 0, 16 * sizeof(unsigned int), st);
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, S_WORDS * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (rows < 2) return cudaSuccess;
   err = cudaMemsetAsync(stamps, 0, sizeof(int) * rows, st);

@@ -279,3 +279,29 @@ def test_edge_cases(api, ctx):
     with pytest.raises(IteError) as ei:
         api.implicit_step(ctx, H6, psi_bad, 0.5, "be", 0.0, 4, 0.0)
     assert ei.value.status in (3, 6)
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_rank_deficient_start_takes_the_svd_gauge(api, ctx, precision):
+    # A start state whose bond 3 carries two identical directions (rank 1 on
+    # a bond of dimension 2) and whose bond 5 carries an exactly zero
+    # direction: the gauge move must drop them as the oracle's SVD does (the
+    # LQ fast path cannot certify full rank there), and the fixed-mode step
+    # must then match the oracle.  Full-rank bonds take the LQ path.
+    N = 8
+    rng = np.random.default_rng(77)
+    chis = [1, 2, 4, 2, 4, 2, 4, 2, 1]
+    A = []
+    for i in range(N):
+        g = rng.standard_normal((chis[i], 2, chis[i + 1], 2))
+        A.append(g[..., 0] + 1j * g[..., 1])
+    A[2][:, :, 1] = A[2][:, :, 0]
+    A[4][:, :, 1] = 0.0
+    Ws = ompo.heisenberg_mpo(N)
+    H = api.mpo_create_heisenberg(ctx, N)
+    opts = api.solver_opts(precision=precision)
+    nodes = ogrid.geometric_grid(1e-1, 1e1, 3)
+    pairs = run_pair(api, ctx, Ws, H, A, nodes, "be", 16, 0.0, shift_mode="energy", opts=opts)
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
+        assert infid(ost, gst) <= TOL
+        assert ginfo["max_chi"] == oinfo.max_chi
