@@ -40,6 +40,10 @@ UNIT = "tau-steps/s"
 # 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s, in line with the nominal
 # 1.25 TFLOP/s (a DFMA probe measured 1.19 at 1995 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_jacobi_persistent launch on the bulk
+# 512 x 512 split, from the ncu capture summarised in
+# profiles/k_jacobi_persistent_split512.md (same kernel source as this build).
+JACOBI_TRAFFIC_BYTES = 4.286976e6 + 1.106432e6
 WORKLOAD = ("heisenberg_bulk: XXX chain N=64 J=1 OBC, D=5, chi_max=256, cutoff 1e-10, "
             "backward Euler on geometric grid 1e-3->1e3 (40 steps), shift=current energy, "
             "saturated synthetic start (chi=256 bulk)")
@@ -298,7 +302,11 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": {"kernel": "k_jacobi_persistent (one-sided Jacobi of the SVD splits)",
                          "bound": "alu", "achieved": jac_tf, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": jac_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": jac_tf / FP64_PEAK_TFLOPS,
+                         "traffic": JACOBI_TRAFFIC_BYTES,
+                         "traffic_note": ("dram bytes per launch on the 512 x 512 bulk split "
+                                          "(ncu, profiles/k_jacobi_persistent_split512.md); the "
+                                          "matrix is L2-resident, the kernel is FP64-bound"),
                          "launches": jac["count"], "ms_per_launch": jac["ms"] / max(1, jac["count"]),
                          "flops_per_launch": svd["jacobi_fp64_flops"] / max(1, jac["count"]),
                          "peak_note": ("FP64 pipe peak derived from unit counts and clocks "
@@ -340,6 +348,7 @@ def run_only(args):
         return torch.from_numpy(a).to("cuda")
 
     H = api.mpo_create_heisenberg(ctx, N_SITES)
+    api.set_kernel_precision(ctx, args.precision)
     if args.only == "heff":
         L, R, X = dev(D_MPO, CHI, CHI), dev(D_MPO, CHI, CHI), dev(CHI, D_SITE, D_SITE, CHI)
         Y = torch.empty_like(X)

@@ -19,6 +19,12 @@
 extern "C" {
 #endif
 
+/* Precision of the contractions inside the kernel-level calls below
+ * (ite_k_heff, ite_k_env_left/right, ite_k_local_solve): ITE_FP64 (default)
+ * or ITE_FP64_TC (FP64-class products on the tensor cores, as in the step's
+ * tensor-core mode).  ITE_EINVAL for any other value. */
+ite_status ite_ctx_set_kernel_precision(ite_ctx ctx, int precision);
+
 /* Two-site effective Hamiltonian on sites (i, i+1) of the MPO (the dominant
  * operation of the local solves, App. B):
  *   Y[a,s',t',b] = alpha * sum L[w,a,a'] W_i[w,s',s,v] W_{i+1}[v,t',t,w'']

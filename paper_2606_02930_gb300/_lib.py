@@ -49,6 +49,7 @@ SIGNATURES = {
     "ite_ctx_device_bytes": (_sz, [_vp]),
     "ite_kernel_launches": (C.c_ulonglong, []),
     "ite_profile_start": (_i, [_vp]),
+    "ite_ctx_set_kernel_precision": (_i, [_vp, C.c_int]),
     "ite_svd_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _pi, _pd]),
     "ite_profile_stop": (_i, [_vp, _pd, _pd, C.POINTER(C.c_longlong)]),
     "ite_mpo_create": (_i, [_vp, _i, _pi, _pi, _pd, C.POINTER(_vp)]),

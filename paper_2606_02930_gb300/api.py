@@ -270,6 +270,12 @@ def _cpair(z):
     return a
 
 
+def set_kernel_precision(ctx, precision):
+    """Precision of the kernel-level contractions ("fp64" or "fp64_tc")."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    check(lib.ite_ctx_set_kernel_precision(ctx.h, p), ctx.h)
+
+
 def k_heff(ctx, H, i, L_env, R_env, X, Y, alpha=1.0, Z=None, gamma=0.0):
     """Device tensors (torch complex128): L (D, chl_bra, chl_ket), R (D, chr_ket,
     chr_bra), X (chl_ket, d, d, chr_ket), Y/Z (chl_bra, d, d, chr_bra)."""

@@ -90,6 +90,7 @@ struct ite_ctx_s {
   int* dcounter = nullptr;
   HostRead* hr = nullptr;      // pinned
   int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
+  int kernel_precision = 0;    // precision of the kernel-level entry points (ite_precision)
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
   double jacobi_flops = 0.0, lq_flops = 0.0;
   int jacobi_sweeps_max = 0;
@@ -220,6 +221,26 @@ struct Scope {
     }
   }
 };
+
+// Kernel-level entry points run their contractions in the precision set by
+// ite_ctx_set_kernel_precision; the emulated GEMMs' wait-error word is
+// cleared on entry and checked by kernel_finish.
+struct KernelMode {
+  ite_ctx c;
+  explicit KernelMode(ite_ctx ctx) : c(ctx) {
+    c->gemm_mode = c->kernel_precision == ITE_FP64_TC ? 1 : 0;
+    cudaMemsetAsync(reinterpret_cast<int*>(c->dcounter) + 10, 0, sizeof(int), c->stream);
+  }
+  ~KernelMode() { c->gemm_mode = 0; }
+};
+
+ite_status kernel_finish(ite_ctx ctx) {
+  CK(cudaMemcpyAsync(&ctx->hr->steps, reinterpret_cast<int*>(ctx->dcounter) + 10, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->steps != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
+  return ITE_OK;
+}
 
 // ------------------------------------------------------------------ contractions
 // Plain GEMM helpers.  Row-major matrices; strides in complex units.
@@ -1544,12 +1565,19 @@ ite_status ite_correlator(ite_ctx ctx, ite_mps psi, const double* O, int i, cons
 }
 
 // ------------------------------------------------------------------ kernel-level entry points
+ite_status ite_ctx_set_kernel_precision(ite_ctx ctx, int precision) {
+  if (!ctx || (precision != ITE_FP64 && precision != ITE_FP64_TC)) return ITE_EINVAL;
+  ctx->kernel_precision = precision;
+  return ITE_OK;
+}
+
 ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_ket,
                       int chr_bra, const double* L, const double* R, const double* X, double* Y,
                       const double alpha[2], const double* Z, const double gamma[2]) {
   if (!ctx || !H || !L || !R || !X || !Y || !alpha || i < 0 || i + 1 >= H->N || chl_bra < 1 ||
       chl_ket < 1 || chr_ket < 1 || chr_bra < 1)
     return ITE_EINVAL;
+  KernelMode km(ctx);
   const long long d2 = (long long)H->d * H->d;
   const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * d2 * std::max(chr_ket, chr_bra);
   CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
@@ -1557,7 +1585,7 @@ ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, i
   const cplx g = gamma ? C(gamma[0], gamma[1]) : C(0);
   CS(heff(ctx, H, i, chl_bra, chl_ket, chr_ket, chr_bra, (const cplx*)L, (const cplx*)R,
           (const cplx*)X, (cplx*)Y, C(alpha[0], alpha[1]), (const cplx*)Z, g));
-  return sync(ctx);
+  return kernel_finish(ctx);
 }
 
 ite_status ite_k_env_left(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
@@ -1566,12 +1594,13 @@ ite_status ite_k_env_left(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ke
   if (!ctx || !H || !Lin || !bra || !ket || !Lout || i < 0 || i >= H->N || chl_bra < 1 ||
       chl_ket < 1 || chr_bra < 1 || chr_ket < 1)
     return ITE_EINVAL;
+  KernelMode km(ctx);
   const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * H->d * std::max(chr_bra, chr_ket);
   CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
   CS(buf_ensure(ctx, ctx->ws_T2, t * sizeof(cplx)));
   CS(env_left(ctx, H, i, chl_bra, chl_ket, chr_bra, chr_ket, (const cplx*)Lin, (const cplx*)bra,
               (const cplx*)ket, (cplx*)Lout));
-  return sync(ctx);
+  return kernel_finish(ctx);
 }
 
 ite_status ite_k_env_right(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_bra,
@@ -1580,12 +1609,13 @@ ite_status ite_k_env_right(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_k
   if (!ctx || !H || !Rin || !bra || !ket || !Rout || i < 0 || i >= H->N || chl_bra < 1 ||
       chl_ket < 1 || chr_bra < 1 || chr_ket < 1)
     return ITE_EINVAL;
+  KernelMode km(ctx);
   const long long t = (long long)H->Dmax * std::max(chl_bra, chl_ket) * H->d * std::max(chr_bra, chr_ket);
   CS(buf_ensure(ctx, ctx->ws_T1, t * sizeof(cplx)));
   CS(buf_ensure(ctx, ctx->ws_T2, t * sizeof(cplx)));
   CS(env_right(ctx, H, i, chl_bra, chl_ket, chr_bra, chr_ket, (const cplx*)Rin, (const cplx*)bra,
                (const cplx*)ket, (cplx*)Rout));
-  return sync(ctx);
+  return kernel_finish(ctx);
 }
 
 ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const double* L,
@@ -1594,6 +1624,7 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   if (!ctx || !H || !L || !R || !B || !X || i < 0 || i + 1 >= H->N || chl < 1 || chr < 1 ||
       krylov_dim < 1 || krylov_dim > kMaxKrylov)
     return ITE_EINVAL;
+  KernelMode km(ctx);
   const long long n = (long long)chl * H->d * H->d * chr;
   CS(buf_ensure(ctx, ctx->ws_V, (size_t)(krylov_dim + 1) * n * sizeof(cplx)));
   CS(buf_ensure(ctx, ctx->ws_T1, (size_t)H->Dmax * n * sizeof(cplx)));
@@ -1604,7 +1635,7 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
                  alpha, c, krylov_dim, local_tol, &s, &r));
   if (steps) *steps = s;
   if (rel_res) *rel_res = r;
-  return ITE_OK;
+  return kernel_finish(ctx);
 }
 
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,

@@ -58,6 +58,36 @@ def test_heff_matches_oracle(api, ctx, model, dims):
     assert rel_err(to_host(Y), want) < 1e-12
 
 
+@pytest.mark.parametrize("model,dims", [("heisenberg", (128, 128, 128, 128)),
+                                        ("heisenberg", (200, 136, 160, 190)),
+                                        ("anderson", (96, 96, 80, 96))])
+def test_heff_and_env_tensor_core_mode(api, model, dims):
+    # kernel-level H_eff and environment update with the contractions on the
+    # tensor cores (FP64-class slicing): same results as the oracle within
+    # the emulation's bound K 2^-48 relative to the largest products
+    kctx = api.ctx_create(0)
+    api.set_kernel_precision(kctx, "fp64_tc")
+    Ws = _models()[model]
+    H = api.mpo_create(kctx, Ws)
+    rng = np.random.default_rng(sum(dims) + len(model))
+    chlB, chlK, chrK, chrB = dims
+    i = 2
+    D0, D2, d = Ws[i].shape[0], Ws[i + 1].shape[3], Ws[i].shape[1]
+    L = crandn(rng, chlB, D0, chlK)
+    R = crandn(rng, chrB, D2, chrK)
+    X = crandn(rng, chlK, d, d, chrK)
+    want = ls.heff_apply(L, Ws[i], Ws[i + 1], R, X)
+    Y = to_dev(np.zeros((chlB, d, d, chrB), complex))
+    api.k_heff(kctx, H, i, to_dev(L_to_lib(L)), to_dev(R_to_lib(R)), to_dev(X), Y)
+    assert rel_err(to_host(Y), want) < 1e-10
+    bra = crandn(rng, chlB, d, chrB)
+    ket = crandn(rng, chlK, d, chrK)
+    want_l = ls.left_env_update(L, bra, Ws[i], ket)
+    Lout = to_dev(np.zeros((Ws[i].shape[3], chrB, chrK), complex))
+    api.k_env_left(kctx, H, i, to_dev(L_to_lib(L)), to_dev(bra), to_dev(ket), Lout)
+    assert rel_err(L_from_lib(to_host(Lout)), want_l) < 1e-10
+
+
 @pytest.mark.parametrize("model,chi,nsamp", [("heisenberg", 256, 6), ("anderson", 512, 3)])
 def test_heff_workload_size_sampled(api, ctx, model, chi, nsamp):
     # bulk two-site block of the N=64 chi=256 Heisenberg chain and of the
