@@ -21,7 +21,6 @@ namespace ite {
 namespace {
 
 constexpr int JT = 128;   // threads of the LQ and row-norm blocks
-constexpr int JW = 2;     // warps (pairs in flight) per Jacobi block
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -288,9 +287,11 @@ k_lq_formq(const cplx* W, const double* refl, int q, int k, cplx* Qh, unsigned i
 // ---------------------------------------------------------- one-sided Jacobi
 // GB300 runs FP64 on a narrow pipe (2 DFMA per clock per SM), so the Jacobi
 // is arranged to issue little besides the inner products and the rotation
-// itself: one warp per pair of rows, each lane holding its len/32 elements of
-// both rows in registers (one load, one store), warp-shuffle reductions (no
-// block barrier), and the rotation parameters computed by lane 0 alone.
+// itself, with enough independent FP64 work in flight to hide the pipe's
+// latency: one team of TPP threads (two warps) per pair of rows, each thread
+// holding its len/TPP elements of both rows in registers (one load, one
+// store), four independent partial sums per quantity, warp shuffles plus one
+// shared-memory exchange, and the rotation parameters formed by thread 0.
 
 // words of the Jacobi state (dev_state, 24 words): grid barrier (0, 1), error
 // flag, sweeps done, pairs examined and rotated, two per-sweep rotation
@@ -298,6 +299,9 @@ k_lq_formq(const cplx* W, const double* refl, int q, int k, cplx* Qh, unsigned i
 constexpr int S_ARRIVE = 0, S_GEN = 1, S_ERR = 4, S_SWEEPS = 5, S_EXAMINED = 6, S_ROTATED = 7,
               S_CNT = 8, S_MAXW = 12, S_WORDS = 24;
 static_assert(S_ERR == 4, "grid_barrier uses word 4 as its error flag");
+
+constexpr int TPP = 64;                 // threads per pair (one block)
+constexpr int TPW = TPP / 32;           // warps per pair
 
 __device__ __forceinline__ double warp_allsum(double v) {
 #pragma unroll
@@ -307,20 +311,41 @@ __device__ __forceinline__ double warp_allsum(double v) {
 
 struct PairOut {
   bool rotated, counted;
-  double al, be;       // squared norms before the rotation (lane 0)
+  double al, be;       // squared norms before the rotation (every thread)
 };
 
-// Rotation of one pair given the lane-0 sums; fills c, sr, si (lane 0) and
-// the flags broadcast to the warp.
+// Team-wide sums of the four per-thread quantities, then the rotation of the
+// pair formed by thread 0 and shared with the team.  Two block barriers;
+// every read of the shared scratch precedes the barrier before its next write.
 __device__ __forceinline__ void pair_decide(double sa, double sb, double gr, double gi, double tol,
                                             double skip, double& c, double& sr, double& si,
                                             PairOut& out) {
-  const int lane = threadIdx.x & 31;
-  int flags = 0;                               // bit 0 rotate, bit 1 counted
-  c = 1.0;
-  sr = si = 0.0;
+  __shared__ double red[TPW][4];
+  __shared__ double par[4];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  sa = warp_allsum(sa);
+  sb = warp_allsum(sb);
+  gr = warp_allsum(gr);
+  gi = warp_allsum(gi);
   if (lane == 0) {
-    const double al = sa, be = sb;
+    red[w][0] = sa;
+    red[w][1] = sb;
+    red[w][2] = gr;
+    red[w][3] = gi;
+  }
+  __syncthreads();
+  sa = sb = gr = gi = 0.0;
+#pragma unroll
+  for (int k = 0; k < TPW; ++k) {
+    sa += red[k][0];
+    sb += red[k][1];
+    gr += red[k][2];
+    gi += red[k][3];
+  }
+  const double al = sa, be = sb;
+  if (tid == 0) {
+    double cc = 1.0, r0 = 0.0, i0 = 0.0;
+    int flags = 0;                             // bit 0 rotate, bit 1 counted
     const double gabs = sqrt(fma(gr, gr, gi * gi));
     // A pair of rows both below the skip weight can never be kept: their
     // mutual orthogonality does not matter (their total weight does, and
@@ -329,10 +354,10 @@ __device__ __forceinline__ void pair_decide(double sa, double sb, double gr, dou
       const double ig = 1.0 / gabs;
       const double zeta = 0.5 * (be - al) * ig;
       const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-      c = rsqrt(fma(t, t, 1.0));
-      const double sn = c * t * ig;
-      sr = sn * gr;
-      si = sn * gi;                            // s e^{i theta}
+      cc = rsqrt(fma(t, t, 1.0));
+      const double sn = cc * t * ig;
+      r0 = sn * gr;
+      i0 = sn * gi;                            // s e^{i theta}
       flags = 1;
       // Only rotations by an angle above tol between two rows above the skip
       // weight count towards another sweep.  Rotations against rows below it
@@ -342,17 +367,20 @@ __device__ __forceinline__ void pair_decide(double sa, double sb, double gr, dou
       // overlap with them changes the kept product at second order.
       if (fabs(t) > tol && al > skip && be > skip) flags |= 2;
     }
-    out.al = al;
-    out.be = be;
+    par[0] = cc;
+    par[1] = r0;
+    par[2] = i0;
+    par[3] = (double)flags;
   }
-  flags = __shfl_sync(0xffffffffu, flags, 0);
+  __syncthreads();
+  c = par[0];
+  sr = par[1];
+  si = par[2];
+  const int flags = (int)par[3];
   out.rotated = (flags & 1) != 0;
   out.counted = (flags & 2) != 0;
-  if (out.rotated) {
-    c = __shfl_sync(0xffffffffu, c, 0);
-    sr = __shfl_sync(0xffffffffu, sr, 0);
-    si = __shfl_sync(0xffffffffu, si, 0);
-  }
+  out.al = al;
+  out.be = be;
 }
 
 // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
@@ -362,23 +390,22 @@ __device__ __forceinline__ void rotate(cplx& x, cplx& y, double c, double sr, do
   y = cmake((sr * x0.x - si * x0.y) + c * y0.x, (sr * x0.y + si * x0.x) + c * y0.y);
 }
 
-// One Jacobi rotation on rows u < v (length len <= 32 EPL) of A by the 32
-// lanes of a warp, the rows held in registers.
+// One Jacobi rotation on rows u < v (length len <= TPP EPL) of A by the team,
+// the rows held in registers.
 template <int EPL>
 __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double skip) {
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   cplx x[EPL], y[EPL];
   // rows come from other SMs' rotations: read them through L2
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
-    const int e = lane + 32 * i;
+    const int e = tid + TPP * i;
     x[i] = e < len ? __ldcg(au + e) : cmake(0.0, 0.0);
     y[i] = e < len ? __ldcg(av + e) : cmake(0.0, 0.0);
   }
-  // four independent partial sums per quantity keep the dependent FP64
-  // chains short (the pipe's latency, not its rate, bounds one warp)
+  // independent partial sums keep the dependent FP64 chains short
   constexpr int NP = EPL < 4 ? EPL : 4;
   double pa[NP], pb[NP], pr[NP], pi[NP];
 #pragma unroll
@@ -399,17 +426,13 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
     gr += pr[a];
     gi += pi[a];
   }
-  sa = warp_allsum(sa);
-  sb = warp_allsum(sb);
-  gr = warp_allsum(gr);
-  gi = warp_allsum(gi);
   PairOut out;
   double c, sr, si;
   pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
   if (out.rotated) {
 #pragma unroll
     for (int i = 0; i < EPL; ++i) {
-      const int e = lane + 32 * i;
+      const int e = tid + TPP * i;
       rotate(x[i], y[i], c, sr, si);
       if (e < len) {
         au[e] = x[i];
@@ -422,28 +445,24 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
 
 // The same for rows of any length, streamed from memory twice.
 __device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, double skip) {
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   double sa = 0, sb = 0, gr = 0, gi = 0;
 #pragma unroll 4
-  for (int e = lane; e < len; e += 32) {
+  for (int e = tid; e < len; e += TPP) {
     const cplx x = __ldcg(au + e), y = __ldcg(av + e);
     sa = fma(x.x, x.x, fma(x.y, x.y, sa));
     sb = fma(y.x, y.x, fma(y.y, y.y, sb));
     gr = fma(x.x, y.x, fma(x.y, y.y, gr));
     gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
   }
-  sa = warp_allsum(sa);
-  sb = warp_allsum(sb);
-  gr = warp_allsum(gr);
-  gi = warp_allsum(gi);
   PairOut out;
   double c, sr, si;
   pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
   if (out.rotated) {
 #pragma unroll 4
-    for (int e = lane; e < len; e += 32) {
+    for (int e = tid; e < len; e += TPP) {
       cplx x = __ldcg(au + e), y = __ldcg(av + e);
       rotate(x, y, c, sr, si);
       au[e] = x;
@@ -456,14 +475,15 @@ __device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, doubl
 __device__ __forceinline__ PairOut jacobi_pair(cplx* A, int len, int u, int v, double tol,
                                                double skip) {
   if (u > v) { const int t = u; u = v; v = t; }
-  if (len <= 128) return pair_regs<4>(A, len, u, v, tol, skip);
-  if (len <= 256) return pair_regs<8>(A, len, u, v, tol, skip);
-  if (len <= 512) return pair_regs<16>(A, len, u, v, tol, skip);
+  if (len <= 2 * TPP) return pair_regs<2>(A, len, u, v, tol, skip);
+  if (len <= 4 * TPP) return pair_regs<4>(A, len, u, v, tol, skip);
+  if (len <= 8 * TPP) return pair_regs<8>(A, len, u, v, tol, skip);
+  if (len <= 16 * TPP) return pair_regs<16>(A, len, u, v, tol, skip);
   return pair_stream(A, len, u, v, tol, skip);
 }
 
-// A single pair (rows == 2), one warp.
-__global__ void __launch_bounds__(32)
+// A single pair (rows == 2), one team.
+__global__ void __launch_bounds__(TPP)
 k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_rel,
                unsigned int* st) {
   const double a2 = anorm2 ? *anorm2 : 0.0;
@@ -476,8 +496,8 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
 }
 
 // All sweeps of the round-robin one-sided Jacobi in one cooperative launch;
-// pair slot k of every round goes to warp k of the grid (and k + warps, ...),
-// one grid barrier after every round.  (Tracking each row's completed round
+// pair slot k of every round goes to block k of the grid (and k + blocks,
+// ...), one grid barrier after every round.  (Tracking each row's completed round
 // instead, so that a pair waits only for its own two rows, measured slower on
 // GB300: the per-pair fence and flag round trip cost more than the barrier.)
 //
@@ -500,13 +520,12 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
 // if neither row has been rotated since then (a rotation at that very round
 // left the pair orthogonal), examining it again cannot fire and is skipped.
 constexpr double kKeepMargin = 1e-2;
-__global__ void __launch_bounds__(JW * 32)
+__global__ void __launch_bounds__(TPP)
 k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double* anorm2,
                     double skip_rel, int max_sweeps, int keep_rank, unsigned int* st, int* stamps,
                     double* wts) {
   const unsigned int nb = gridDim.x;
-  const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * JW + (threadIdx.x >> 5), nw = (int)nb * JW;
+  const int tid = threadIdx.x;
   const double skip = skip_rel * (anorm2 ? *anorm2 : 0.0);
   int* counters = reinterpret_cast<int*>(st + S_CNT);
   unsigned long long* maxws = reinterpret_cast<unsigned long long*>(st + S_MAXW);
@@ -520,25 +539,25 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
         maxws[(sw + 1) & 1] = 0ull;
       }
       const int g = sw * (pp - 1) + r;
-      for (int k = wid; k < pp / 2; k += nw) {
+      for (int k = blockIdx.x; k < pp / 2; k += (int)nb) {
         int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
         if (u >= rows || v >= rows) continue;
         if (u > v) { const int t = u; u = v; v = t; }
         if (sw > 0) {
-          // read through L2 so that every lane sees the same stamps and the
-          // warp takes one branch
+          // read through L2 so that every thread sees the same stamps and the
+          // block takes one branch
           const int last = g - (pp - 1);
           if (__ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) continue;
         }
         const PairOut o = jacobi_pair(A, len, u, v, tol, skip);
         ++examined;
-        if (lane == 0) {
+        if (tid == 0) {
           wts[u] = o.al;
           wts[v] = o.be;
         }
         if (o.rotated) {
           ++rotations_done;
-          if (lane == 0) {
+          if (tid == 0) {
             stamps[u] = g;
             stamps[v] = g;
             if (o.counted) {
@@ -566,7 +585,7 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
       if (heavy >= keep_rank) break;
     }
   }
-  if (lane == 0) {
+  if (tid == 0) {
     atomicAdd(st + S_EXAMINED, examined);
     atomicAdd(st + S_ROTATED, rotations_done);
   }
@@ -789,19 +808,19 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
     // a single pair: one rotation makes it orthogonal; a second launch confirms
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<<<1, 32, 0, st>>>(A, len, tol, anorm2, skip_rel, dev_state);
+      k_jacobi_round<<<1, TPP, 0, st>>>(A, len, tol, anorm2, skip_rel, dev_state);
     }
     return cudaGetLastError();
   }
   int max_blocks = 0;
-  err = g_jacobi_blocks.get((const void*)k_jacobi_persistent, JW * 32, &max_blocks);
+  err = g_jacobi_blocks.get((const void*)k_jacobi_persistent, TPP, &max_blocks);
   if (err != cudaSuccess) return err;
-  int nblk = (pp / 2 + JW - 1) / JW;
+  int nblk = pp / 2;
   if (nblk > max_blocks) nblk = max_blocks;
   void* args[] = {&A, &rows, &len, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &keep_rank,
                   &dev_state, &stamps, &wts};
   count_launches(1);
-  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(JW * 32), args, 0,
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(TPP), args, 0,
                                      st);
 }
 
