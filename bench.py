@@ -61,6 +61,10 @@ def parse():
                     help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores")
     ap.add_argument("--only", choices=["heff", "split"], default=None,
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
+    ap.add_argument("--workload", choices=["chain", "batch"], default="chain",
+                    help="batch: a bounded sample of the batched workload served side by side")
+    ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
+    ap.add_argument("--slots", type=int, default=4, help="concurrent jobs in the batch sample")
     return ap.parse_args()
 
 
@@ -334,6 +338,42 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Served execution of a bounded sample of the batched workload: Heisenberg
+    chains with N drawn from {16, 24, 32, 48, 64} and chi_max from {32, 64, 128}
+    (seed 4000; the chi = 256 draws of the full workload are left out of this
+    sample to bound its time), random product starts (seed 4000 + i), backward
+    Euler on the geometric grid 1e-2 -> 1e2 in --steps steps, tensor-core mode.
+    Runs the same jobs one at a time (1 slot) and side by side (--slots) and
+    prints one JSON line (not the benchmark line): tau-steps/s, p50/p99
+    latency, and the speed-up of serving over one-at-a-time."""
+    import torch
+    from paper_2606_02930_gb300 import api, inputs
+    torch.cuda.init()
+    rng = np.random.default_rng(4000)
+    Ns = rng.choice([16, 24, 32, 48, 64], size=args.jobs)
+    chis = rng.choice([32, 64, 128], size=args.jobs)
+    opts = api.solver_opts(precision=args.precision)
+
+    def make():
+        return [api.Job("heisenberg", int(N), inputs.random_product_state(int(N), 2, 4000 + i),
+                        int(chi), 1e-10, 1e-2, 1e2, args.steps, scheme="be", opts=opts)
+                for i, (N, chi) in enumerate(zip(Ns, chis))]
+
+    api.evolve_batch(make()[:2], n_slots=2)          # warm-up: build caches, page in kernels
+    out = {"workload": "batch", "metric": "tau-steps/s and p50/p99 latency of served jobs",
+           "jobs": int(args.jobs), "steps_per_job": args.steps, "precision": args.precision,
+           "sample": ("Heisenberg N in {16,24,32,48,64}, chi_max in {32,64,128} (seed 4000), "
+                      "BE 1e-2 -> 1e2")}
+    for slots in (1, args.slots):
+        res, st = api.evolve_batch(make(), n_slots=slots)
+        assert all(r["status"] == 0 for r in res)
+        out[f"slots{slots}"] = {k: st[k] for k in ("tau_steps_per_s", "p50_latency_ms",
+                                                   "p99_latency_ms", "wall_ms", "peak_running")}
+    out["speedup"] = out[f"slots{args.slots}"]["tau_steps_per_s"] / out["slots1"]["tau_steps_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def run_only(args):
     """Time one kernel-level entry point at the workload's bulk shape: the
     two-site H_eff (chi = 256, d = 2, D = 5) or the truncated SVD split of a
@@ -380,6 +420,9 @@ def main():
     args = parse()
     if args.only:
         run_only(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -62,7 +62,8 @@ typedef enum {
   ITE_ESINGULAR = 3,
   ITE_ENOTCONV = 4,
   ITE_ETIMEOUT = 5,
-  ITE_ECUDA = 6
+  ITE_ECUDA = 6,
+  ITE_PENDING = 7     /* a served job has not finished yet (ite_server.h) */
 } ite_status;
 
 /* Time stepper.  Trapezoid: Eq. 4 (A-stable, App. A).  Backward Euler: the

@@ -1,0 +1,119 @@
+/*
+ * ite_server.h -- many imaginary-time evolutions at once on one GPU.
+ *
+ * The paper evolves one state at a time (Method; App. B, App. D).  Its
+ * Anderson-impurity study needs many independent evolutions (METTS samples,
+ * parameter scans: Anderson-impurity section), and one evolution's kernels
+ * leave most of a GB300 idle: the sweep is a chain of small dependent steps
+ * whose largest cost, the truncated SVD, is bound by FP64 latency.  This
+ * server runs independent evolutions side by side.  Each worker owns a
+ * library context on its own CUDA stream, so the kernels of different jobs
+ * overlap on the device.  The paper has no counterpart; it is this library's
+ * addition.
+ *
+ *   - Admission: a job is started only when its device-memory estimate
+ *     (ite_job_device_bytes) fits the server's budget next to the jobs
+ *     already running.  Jobs start in submission order, so a large job at the
+ *     head of the queue waits rather than being overtaken.  A job whose
+ *     estimate alone exceeds the budget is refused at submission
+ *     (ITE_ENOMEM).
+ *   - Memory: workers allocate stream-ordered (cudaMallocAsync on their own
+ *     stream), so no job's allocation waits for the whole device, and release
+ *     a job's workspaces when it ends.
+ *   - Each job is the same computation as ite_evolve_loggrid on a product
+ *     start state: its results do not depend on what else runs (the kernels
+ *     are deterministic and jobs share no data).
+ *   - Host arrays in ite_job are copied by ite_server_submit; the output
+ *     buffers (energies, state) must stay valid until the job has finished.
+ *   - All calls are thread-safe.  Errors: ITE_EINVAL for invalid arguments,
+ *     ITE_ENOMEM as above, ITE_ECUDA if a worker cannot set up its device.
+ */
+#ifndef ITE_SERVER_H
+#define ITE_SERVER_H
+
+#include "ite.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { ITE_MODEL_HEISENBERG = 0, ITE_MODEL_ANDERSON = 1 } ite_model;
+
+/* One evolution: model, product start state, truncation and the geometric
+ * tau grid (tau0 -> tau_max in n_steps steps, as ite_evolve_loggrid). */
+typedef struct {
+  int model;                  /* ite_model                                          */
+  int n;                      /* Heisenberg: sites N; Anderson: bath sites (N = n+1) */
+  double J, Jz;               /* Heisenberg couplings                               */
+  double U, eps_d;            /* Anderson impurity                                  */
+  const double* eps;          /* Anderson bath energies [n] (copied at submit)      */
+  const double* V;            /* Anderson hybridisations [n] (copied at submit)     */
+  const double* site_vecs;    /* start state [N][d], interleaved complex (copied)   */
+  int chi_max;
+  double cutoff;
+  int scheme;                 /* ite_scheme                                         */
+  int shift_mode;             /* ite_shift_mode                                     */
+  double shift0;
+  double tau0, tau_max;
+  int n_steps;
+  ite_solver_opts opts;
+  double* energies;           /* optional out [n_steps]: energy after each step     */
+  double* state;              /* optional out: final tensors as ite_mps_get writes  */
+  size_t state_cap;           /* capacity of state in doubles                       */
+  int* state_chi;             /* optional out [N+1]: final bond dimensions          */
+} ite_job;
+
+typedef struct {
+  int status;                 /* ite_status of the evolution                         */
+  int steps_done;
+  double energy;              /* energy after the last step                          */
+  double max_discarded_weight;
+  int max_chi;
+  double queue_ms;            /* submission -> start                                 */
+  double run_ms;              /* start -> finish                                     */
+  double latency_ms;          /* submission -> finish                                */
+  size_t device_bytes;        /* the admission estimate                              */
+} ite_job_result;
+
+typedef struct {
+  long long submitted, completed, failed;
+  int peak_running;           /* most jobs ever running at once                      */
+  double p50_latency_ms, p99_latency_ms;   /* over completed jobs                    */
+  double wall_ms;             /* first submission -> last completion                 */
+  double tau_steps;           /* steps completed over all jobs                       */
+  double tau_steps_per_s;     /* tau_steps / wall                                    */
+} ite_server_stats;
+
+typedef struct ite_server_s* ite_server;
+
+/* Device-memory estimate of one job (host arithmetic, no device needed): the
+ * MPS and its two work copies at the capacity set by chi_max, the
+ * environments, the Krylov basis and the sweep's workspaces, and the
+ * tensor-core scratch in ITE_FP64_TC mode.  0 for an invalid job. */
+size_t ite_job_device_bytes(const ite_job* job);
+
+/* n_slots workers (1..64) on `device`, admitting jobs while their estimates
+ * sum to at most mem_budget bytes (0: 90% of the device's free memory). */
+ite_status ite_server_create(int device, int n_slots, size_t mem_budget, ite_server* out);
+/* Queue a job; *ticket identifies it. */
+ite_status ite_server_submit(ite_server s, const ite_job* job, long long* ticket);
+/* ITE_OK and *out when the job has finished, ITE_PENDING before. */
+ite_status ite_server_poll(ite_server s, long long ticket, ite_job_result* out);
+/* Block until the job has finished. */
+ite_status ite_server_wait(ite_server s, long long ticket, ite_job_result* out);
+/* Block until every submitted job has finished. */
+ite_status ite_server_drain(ite_server s);
+ite_status ite_server_stats_get(ite_server s, ite_server_stats* out);
+/* Drains, then stops the workers. */
+void ite_server_destroy(ite_server s);
+
+/* n jobs through a temporary server: create, submit all, drain, destroy.
+ * out[n] receives the results in job order; stats may be NULL. */
+ite_status ite_evolve_batch(int device, int n_slots, size_t mem_budget, int n, const ite_job* jobs,
+                            ite_job_result* out, ite_server_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

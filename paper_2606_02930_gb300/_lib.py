@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/ite.h and include/ite_kernels.h.
+"""ctypes declarations of the C ABI in include/ite.h, include/ite_kernels.h and
+include/ite_server.h.
 
 Argument marshalling only: every computation happens in libite.so.  Importing
 this module loads the library and fails loudly if it has not been built
@@ -10,12 +11,14 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libite.so")
 
-ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA = range(7)
+(ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA,
+ ITE_PENDING) = range(8)
+ITE_MODEL_HEISENBERG, ITE_MODEL_ANDERSON = 0, 1
 ITE_BACKWARD_EULER, ITE_TRAPEZOID = 0, 1
 ITE_FP64, ITE_FP64_TC = 0, 1
 ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
 STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",
-                4: "ITE_ENOTCONV", 5: "ITE_ETIMEOUT", 6: "ITE_ECUDA"}
+                4: "ITE_ENOTCONV", 5: "ITE_ETIMEOUT", 6: "ITE_ECUDA", 7: "ITE_PENDING"}
 
 
 class ite_solver_opts(C.Structure):
@@ -28,6 +31,38 @@ class ite_step_info(C.Structure):
                 ("max_discarded_weight", C.c_double), ("max_local_residual", C.c_double),
                 ("shift", C.c_double), ("max_chi", C.c_int), ("gmres_steps", C.c_int),
                 ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ite_job(C.Structure):
+    _fields_ = [("model", C.c_int), ("n", C.c_int), ("J", C.c_double), ("Jz", C.c_double),
+                ("U", C.c_double), ("eps_d", C.c_double), ("eps", C.POINTER(C.c_double)),
+                ("V", C.POINTER(C.c_double)), ("site_vecs", C.POINTER(C.c_double)),
+                ("chi_max", C.c_int), ("cutoff", C.c_double), ("scheme", C.c_int),
+                ("shift_mode", C.c_int), ("shift0", C.c_double), ("tau0", C.c_double),
+                ("tau_max", C.c_double), ("n_steps", C.c_int), ("opts", ite_solver_opts),
+                ("energies", C.POINTER(C.c_double)), ("state", C.POINTER(C.c_double)),
+                ("state_cap", C.c_size_t), ("state_chi", C.POINTER(C.c_int))]
+
+
+class ite_job_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps_done", C.c_int), ("energy", C.c_double),
+                ("max_discarded_weight", C.c_double), ("max_chi", C.c_int),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("device_bytes", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ite_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong),
+                ("failed", C.c_longlong), ("peak_running", C.c_int),
+                ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
+                ("wall_ms", C.c_double), ("tau_steps", C.c_double),
+                ("tau_steps_per_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +120,16 @@ SIGNATURES = {
     "ite_k_zgemm": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _i, _vp,
                          C.c_longlong, C.c_longlong, _i, _vp, C.c_longlong, _pd, _pd]),
     "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd, _i]),
+    "ite_job_device_bytes": (_sz, [C.POINTER(ite_job)]),
+    "ite_server_create": (_i, [_i, _i, _sz, C.POINTER(_vp)]),
+    "ite_server_submit": (_i, [_vp, C.POINTER(ite_job), C.POINTER(C.c_longlong)]),
+    "ite_server_poll": (_i, [_vp, C.c_longlong, C.POINTER(ite_job_result)]),
+    "ite_server_wait": (_i, [_vp, C.c_longlong, C.POINTER(ite_job_result)]),
+    "ite_server_drain": (_i, [_vp]),
+    "ite_server_stats_get": (_i, [_vp, C.POINTER(ite_server_stats)]),
+    "ite_server_destroy": (None, [_vp]),
+    "ite_evolve_batch": (_i, [_i, _i, _sz, _i, C.POINTER(ite_job), C.POINTER(ite_job_result),
+                              C.POINTER(ite_server_stats)]),
 }
 
 

@@ -366,3 +366,129 @@ def k_zgemm(ctx, A, B, Cout, mode=1, conjA=False, conjB=False, alpha=1.0, beta=0
     check(lib.ite_k_zgemm(ctx.h, mode, M, N, K, C.c_void_p(A.data_ptr()), sAm, sAk,
                           1 if conjA else 0, C.c_void_p(B.data_ptr()), sBk, sBn, 1 if conjB else 0,
                           C.c_void_p(Cout.data_ptr()), Cout.stride(0), _dptr(a), _dptr(b)), ctx.h)
+
+
+# ------------------------------------------------------------------ served / batched execution
+MODELS = {"heisenberg": L.ITE_MODEL_HEISENBERG, "anderson": L.ITE_MODEL_ANDERSON}
+
+
+def _bond_caps(N, d, chi_max):
+    caps = []
+    for b in range(N + 1):
+        c = chi_max
+        if b * np.log(d) < np.log(chi_max) + 1e-12:
+            c = min(c, d ** b)
+        if (N - b) * np.log(d) < np.log(chi_max) + 1e-12:
+            c = min(c, d ** (N - b))
+        caps.append(int(c))
+    return caps
+
+
+class Job:
+    """One evolution for the server (ite_job): model, product start state
+    site_vecs (N, d), truncation, geometric grid.  The arrays referenced by the
+    C struct live as long as this object."""
+
+    def __init__(self, model, n, site_vecs, chi_max, cutoff, tau0, tau_max, n_steps, scheme="be",
+                 shift_mode=SHIFT_CURRENT_ENERGY, shift0=0.0, J=1.0, Jz=None, U=0.0, eps_d=0.0,
+                 eps=None, V=None, opts=None, want_state=False):
+        j = L.ite_job()
+        j.model = MODELS[model] if isinstance(model, str) else int(model)
+        j.n = n
+        j.J, j.Jz = J, (J if Jz is None else Jz)
+        j.U, j.eps_d = U, eps_d
+        self.sv = _c128(site_vecs)
+        self.N, self.d = self.sv.shape
+        j.site_vecs = _dptr(self.sv.view(np.float64))
+        if eps is not None:
+            self.eps = np.ascontiguousarray(eps, dtype=np.float64)
+            self.V = np.ascontiguousarray(V, dtype=np.float64)
+            j.eps, j.V = _dptr(self.eps), _dptr(self.V)
+        j.chi_max, j.cutoff = chi_max, cutoff
+        j.scheme, j.shift_mode, j.shift0 = _scheme(scheme), shift_mode, shift0
+        j.tau0, j.tau_max, j.n_steps = tau0, tau_max, n_steps
+        j.opts = opts if opts is not None else solver_opts()
+        self.energies = np.zeros(n_steps)
+        j.energies = _dptr(self.energies)
+        if want_state:
+            caps = _bond_caps(self.N, self.d, chi_max)
+            cap = sum(2 * caps[i] * self.d * caps[i + 1] for i in range(self.N))
+            self.state = np.zeros(cap)
+            self.state_chi = np.zeros(self.N + 1, np.int32)
+            j.state, j.state_cap = _dptr(self.state), cap
+            j.state_chi = self.state_chi.ctypes.data_as(C.POINTER(C.c_int))
+        else:
+            self.state = None
+        self.c = j
+
+    def device_bytes(self):
+        return int(lib.ite_job_device_bytes(C.byref(self.c)))
+
+    def tensors(self):
+        """Final state as site tensors (chi_i, d, chi_{i+1}) when want_state."""
+        z = self.state.view(np.complex128)
+        out, pos = [], 0
+        for i in range(self.N):
+            cnt = self.state_chi[i] * self.d * self.state_chi[i + 1]
+            out.append(z[pos:pos + cnt].reshape(self.state_chi[i], self.d,
+                                                self.state_chi[i + 1]).copy())
+            pos += cnt
+        return out
+
+
+class Server:
+    """Independent evolutions side by side on one GPU (ite_server.h)."""
+
+    def __init__(self, device=0, n_slots=4, mem_budget=0):
+        h = C.c_void_p()
+        check(lib.ite_server_create(device, n_slots, mem_budget, C.byref(h)))
+        self.h = h
+        self.jobs = {}
+
+    def submit(self, job):
+        t = C.c_longlong()
+        check(lib.ite_server_submit(self.h, C.byref(job.c), C.byref(t)))
+        self.jobs[t.value] = job
+        return t.value
+
+    def poll(self, ticket):
+        r = L.ite_job_result()
+        st = lib.ite_server_poll(self.h, ticket, C.byref(r))
+        if st == L.ITE_PENDING:
+            return None
+        check(st)
+        return r.as_dict()
+
+    def wait(self, ticket):
+        r = L.ite_job_result()
+        check(lib.ite_server_wait(self.h, ticket, C.byref(r)))
+        return r.as_dict()
+
+    def drain(self):
+        check(lib.ite_server_drain(self.h))
+
+    def stats(self):
+        s = L.ite_server_stats()
+        check(lib.ite_server_stats_get(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            lib.ite_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def evolve_batch(jobs, n_slots=4, mem_budget=0, device=0):
+    """Run Job objects through a temporary server; returns (results, stats)."""
+    n = len(jobs)
+    arr = (L.ite_job * n)(*[j.c for j in jobs])
+    res = (L.ite_job_result * n)()
+    st = L.ite_server_stats()
+    check(lib.ite_evolve_batch(device, n_slots, mem_budget, n, arr, res, C.byref(st)))
+    return [r.as_dict() for r in res], st.as_dict()

@@ -1728,4 +1728,15 @@ bool internal_bond_info(ite_mpo H, int i, int* d, int* D0, int* D1, int* D2, con
 
 ite_status internal_fail(ite_ctx ctx, ite_status st, const char* msg) { return fail(ctx, st, msg); }
 
+// Frees the context's reusable workspaces (they grow again on demand), so
+// that a long-lived context holds only its small fixed state between jobs.
+void internal_release_workspace(ite_ctx ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
+                 &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
+                 &ctx->ws_emu};
+  for (Buf* b : bufs) buf_free(ctx, *b);
+}
+
 }  // namespace ite

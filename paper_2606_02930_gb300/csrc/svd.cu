@@ -15,6 +15,8 @@
 //      rows of U^H are the rows of R_out divided by their norms.
 // No rotation is accumulated: the engine forms the other factor as the
 // projection U_r^H Xr with one GEMM.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ite {
@@ -706,25 +708,28 @@ int grid_for(long long tot) {
   return (int)g;
 }
 
-// Blocks of JT threads of a kernel that can be co-resident on the current
-// device (the grid of a cooperative launch), cached per kernel and device.
+// Blocks of a kernel that can be co-resident on the current device (the grid
+// of a cooperative launch), cached per kernel and device; several host
+// threads may ask at once.
 struct Coresident {
-  int dev = -1, blocks = 0;
+  std::mutex mu;
+  int blocks[64] = {0};
   cudaError_t get(const void* kernel, int threads, int* out) {
     int d = 0;
     cudaError_t e = cudaGetDevice(&d);
     if (e != cudaSuccess) return e;
-    if (d != dev) {
+    std::lock_guard<std::mutex> lock(mu);
+    int& b = blocks[d & 63];
+    if (b == 0) {
       int per_sm = 0, sms = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
       if (e != cudaSuccess) return e;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
       if (e != cudaSuccess) return e;
-      blocks = per_sm * sms;
-      dev = d;
+      b = per_sm * sms;
     }
-    *out = blocks;
-    return blocks > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    *out = b;
+    return b > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
   }
 };
 Coresident g_lq_blocks, g_jacobi_blocks, g_formq_blocks;

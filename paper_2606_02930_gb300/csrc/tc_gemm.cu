@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -186,12 +187,20 @@ size_t smem_bytes() {
 template <int BN, int BK>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int M, int N, int K,
                    long long ldc, int* err, cudaStream_t st) {
-  static bool attr_done = false;
+  // the shared-memory attribute is per device; setting it twice from two
+  // threads is harmless
+  static std::atomic<unsigned long long> attr_done{0};
   const size_t sm = smem_bytes<BN, BK>();
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_bf16<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_done.load() & bit)) {
+      e = cudaFuncSetAttribute(k_tc_gemm_bf16<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      attr_done.fetch_or(bit);
+    }
   }
   dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM);
   count_launches(1);

@@ -32,6 +32,8 @@
 
 #include <cstdint>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
@@ -375,12 +377,20 @@ cudaError_t zgemm_emu(const GemmArgs& g, void* scratch, size_t scratch_bytes, in
   __nv_bfloat16* Bs = As + (size_t)S * Mr * Kp;
   int* eA = reinterpret_cast<int*>(Bs + (size_t)S * g.N * Kp);
   int* eB = eA + g.M;
-  static bool attr_done = false;
+  // the shared-memory attribute is per device; setting it twice from two
+  // threads is harmless
+  static std::atomic<unsigned long long> attr_done{0};
   const size_t smem = 1024 + STAGES * STAGE_BYTES + (2 * STAGES + 4) * 8 + 16;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_zgemm_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_done.load() & bit)) {
+      e = cudaFuncSetAttribute(k_zgemm_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_done.fetch_or(bit);
+    }
   }
   for (int b = 0; b < g.batch; ++b) {
     const cplx* A = g.A + (long long)b * g.sAb;

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     names = set()
-    for h in ("ite.h", "ite_kernels.h"):
+    for h in ("ite.h", "ite_kernels.h", "ite_server.h"):
         with open(os.path.join(ROOT, "include", h)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
