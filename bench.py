@@ -41,9 +41,9 @@ UNIT = "tau-steps/s"
 # 1.25 TFLOP/s (a DFMA probe measured 1.19 at 1995 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_jacobi_persistent launch on the bulk
-# 512 x 512 split from an ncu capture of this kernel source, or None when the
-# kernel has changed since the last capture.
-JACOBI_TRAFFIC_BYTES = None
+# 512 x 512 split from the ncu capture of this kernel source summarised in
+# profiles/k_jacobi_persistent_split512.md (None once the kernel changes).
+JACOBI_TRAFFIC_BYTES = 4.334592e6 + 1.230848e6
 WORKLOAD = ("heisenberg_bulk: XXX chain N=64 J=1 OBC, D=5, chi_max=256, cutoff 1e-10, "
             "backward Euler on geometric grid 1e-3->1e3 (40 steps), shift=current energy, "
             "saturated synthetic start (chi=256 bulk)")
