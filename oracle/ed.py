@@ -104,10 +104,46 @@ def single_particle_matrix(eps_d, eps, V):
 
 
 # ---------------------------------------------------------------- propagators
+def pade_denominator(q):
+    """Coefficients p_0..p_q of the denominator of the (q, q) Pade approximant
+    of e^{-z}: P_q(z) = sum_k (2q-k)! q! / ((2q)! k! (q-k)!) z^k, so that
+    e^{-z} ~ P_q(-z) / P_q(z) with error O(z^{2q+1})."""
+    from math import factorial
+    return np.array([factorial(2 * q - k) * factorial(q)
+                     / (factorial(2 * q) * factorial(k) * factorial(q - k)) for k in range(q + 1)])
+
+
+def gl_stages(scheme):
+    """Number of Gauss-Legendre stages q of a scheme name 'gl<q>'."""
+    return int(scheme[2:])
+
+
+def pade_partial_fractions(q):
+    """R_q(z) = P_q(-z)/P_q(z) = r_inf + sum_j a_j / (z - z_j): the poles z_j
+    (roots of P_q), the residues a_j = P_q(-z_j) / P_q'(z_j) and r_inf =
+    (-1)^q.  For a linear ODE the q-stage Gauss-Legendre collocation step is
+    this rational function of z = dtau (H - s) (Method: Gauss-Legendre
+    collocation on each panel)."""
+    p = pade_denominator(q)
+    poly = np.polynomial.Polynomial(p)
+    num = np.polynomial.Polynomial(p * (-1.0) ** np.arange(q + 1))
+    z = np.roots(p[::-1]).astype(complex)
+    a = num(z) / poly.deriv()(z)
+    return z, a, (-1.0) ** q
+
+
 def amplification(z, scheme):
     """One-step amplification factor of the linear test problem y' = -lambda y
     at z = lambda * dtau (App. A).  'be': backward Euler; 'tr': implicit
-    trapezoid rule (Eq. 4); 'fe': forward Euler (the explicit counter-example)."""
+    trapezoid rule (Eq. 4); 'fe': forward Euler (the explicit counter-example);
+    'gl<q>': q-stage Gauss-Legendre collocation, the (q, q) Pade approximant
+    P_q(-z) / P_q(z) of e^{-z}."""
+    if str(scheme).startswith("gl"):
+        p = pade_denominator(gl_stages(scheme))
+        zz = np.asarray(z)
+        num = sum(c * (-zz) ** k for k, c in enumerate(p))
+        den = sum(c * zz ** k for k, c in enumerate(p))
+        return num / den
     z = np.asarray(z, dtype=float)
     if scheme == "be":
         return 1.0 / (1.0 + z)

@@ -291,3 +291,24 @@ def fit_affine(Ws, psi, alpha, beta, chi_max, cutoff, sweeps=1):
     for _ in range(max(1, sweeps)):
         f = _sweep(Ws, f, local_block, [("op", psi), ("ov", psi)], chi_max, cutoff, info)
     return f, info
+
+
+def fit_combination(targets, coefs, chi_max, cutoff, sweeps=1):
+    """Two-site variational fit f ~ sum_t coefs[t] |targets[t]>, starting from
+    f = targets[0] (right-canonicalised).  Each local block is the exact
+    projection of the combination onto the current environments of f: the
+    sum of the targets' two-site blocks, each contracted with its own overlap
+    environments.  Forms the Gauss-Legendre step from its partial-fraction
+    solves."""
+    f = right_canonicalize_svd(targets[0])
+    info = SweepInfo()
+
+    def local_block(i, EL, ER, X0):
+        out = 0.0
+        for c, t, Lov, Rov in zip(coefs, targets, EL, ER):
+            out = out + c * project_two_site(Lov, t[i], t[i + 1], Rov)
+        return out
+
+    for _ in range(max(1, sweeps)):
+        f = _sweep(None, f, local_block, [("ov", t) for t in targets], chi_max, cutoff, info)
+    return f, info

@@ -7,6 +7,13 @@ Schemes (H' = H - s):
           (I - c H') psi_{k-1} and is also the initial guess (App. B).
 * 'be' -- backward Euler: (I + c H') psi_k = psi_{k-1} with c = dtau; b = psi_{k-1}
           and the initial guess is psi_{k-1}.
+* 'gl<q>' -- q-stage Gauss-Legendre collocation (Method: the spectral panel
+          method), which for this linear ODE is psi_k = R_q(dtau H') psi_{k-1}
+          with R_q the (q, q) Pade approximant of e^{-z}.  By partial fractions
+          R_q(z) = r_inf + sum_j a_j / (z - z_j), so psi_k = r_inf psi_{k-1} +
+          sum_j w_j x_j with (I + c_j H') x_j = psi_{k-1}, c_j = -dtau / z_j,
+          w_j = -a_j / z_j: q independent shifted solves with complex c_j (each
+          from the initial guess psi_{k-1}), then a two-site fit of the sum.
 After the solve the state is normalised (Heisenberg section, App. D).  The
 shift s is either fixed or, in 'energy' mode, the energy of the current state
 (App. D: shift the spectrum by the energy of the new time-evolved state).
@@ -43,16 +50,37 @@ def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
         b, finfo = ls.fit_affine(Ws, psi, 1.0 + c * shift, -c, chi_max, cutoff, fit_sweeps)
         info.max_discarded = finfo.max_discarded
         x0 = mpsmod.copy(b)
+    elif str(scheme).startswith("gl"):
+        from .ed import pade_partial_fractions, gl_stages
+        z, a, r_inf = pade_partial_fractions(gl_stages(scheme))
+        xs, ws = [], []
+        for zj, aj in zip(z, a):
+            cj = -dtau / zj
+            xj, sinfo = ls.linsolve(Ws, mpsmod.copy(psi), psi, cj, shift, chi_max, cutoff,
+                                    krylov_dim, local_tol, sweeps, sweep_tol)
+            info.max_discarded = max(info.max_discarded, sinfo.max_discarded)
+            info.max_local_residual = max(info.max_local_residual, sinfo.max_local_residual)
+            info.gmres_steps += sinfo.gmres_steps
+            xs.append(xj)
+            ws.append(-aj / zj)
+        x, finfo = ls.fit_combination([psi] + xs, [r_inf] + ws, chi_max, cutoff, fit_sweeps)
+        info.max_discarded = max(info.max_discarded, finfo.max_discarded)
+        return _finish(x, info, Ws)
     else:
         raise ValueError(scheme)
     x, sinfo = ls.linsolve(Ws, x0, b, c, shift, chi_max, cutoff, krylov_dim,
                            local_tol, sweeps, sweep_tol)
-    nrm = float(np.linalg.norm(x[0]))          # centre on site 1, the rest right-orthonormal
-    x[0] = x[0] / nrm
-    info.norm_before = nrm
     info.max_discarded = max(info.max_discarded, sinfo.max_discarded)
     info.max_local_residual = sinfo.max_local_residual
     info.gmres_steps = sinfo.gmres_steps
+    return _finish(x, info, Ws)
+
+
+def _finish(x, info, Ws):
+    """Normalise (centre on site 1, the rest right-orthonormal), energy."""
+    nrm = float(np.linalg.norm(x[0]))
+    x[0] = x[0] / nrm
+    info.norm_before = nrm
     info.max_chi = max(mpsmod.bond_dims(x) + [1])
     info.energy = mpsmod.expect_mpo(x, Ws)
     return x, info

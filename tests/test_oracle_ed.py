@@ -250,3 +250,50 @@ def test_backward_euler_energy_monotone_dense():
     states, _, _ = ed.propagate_discrete(H, v0, dt, "be", shifts=e0)
     es = [ed.energy(H, v0)] + [ed.energy(H, v) for v in states]
     assert all(b <= a + 1e-13 for a, b in zip(es, es[1:]))
+
+
+def _collocation_amplification(z, A, b):
+    """Runge-Kutta stability function R(z) = 1 - z b^T (I + z A)^{-1} 1 of a
+    Butcher tableau (A, b), for y' = -lambda y at z = lambda dtau."""
+    A = np.asarray(A, float)
+    one = np.ones(len(b))
+    return np.array([1.0 - zz * np.asarray(b) @ np.linalg.solve(np.eye(len(b)) + zz * A, one)
+                     for zz in np.atleast_1d(z)])
+
+
+def test_gauss_legendre_amplification_equals_collocation_tableau():
+    # 2- and 3-stage Gauss-Legendre collocation tableaux (nodes at the
+    # Legendre roots on [0, 1]); their stability functions are the
+    # diagonal Pade approximants of e^{-z}
+    r3, r15 = np.sqrt(3.0), np.sqrt(15.0)
+    A2 = [[0.25, 0.25 - r3 / 6], [0.25 + r3 / 6, 0.25]]
+    b2 = [0.5, 0.5]
+    A3 = [[5 / 36, 2 / 9 - r15 / 15, 5 / 36 - r15 / 30],
+          [5 / 36 + r15 / 24, 2 / 9, 5 / 36 - r15 / 24],
+          [5 / 36 + r15 / 30, 2 / 9 + r15 / 15, 5 / 36]]
+    b3 = [5 / 18, 4 / 9, 5 / 18]
+    z = np.array([1e-3, 0.1, 0.7, 2.0, 9.0, 60.0, 1e4])
+    assert np.allclose(ed.amplification(z, "gl2"), _collocation_amplification(z, A2, b2),
+                       rtol=1e-12, atol=1e-15)
+    assert np.allclose(ed.amplification(z, "gl3"), _collocation_amplification(z, A3, b3),
+                       rtol=1e-12, atol=1e-15)
+    # one stage is the implicit midpoint rule, i.e. the trapezoid amplification
+    assert np.allclose(ed.amplification(z, "gl1"), ed.amplification(z, "tr"), rtol=1e-15)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_gauss_legendre_order_and_a_stability(q):
+    # local error e^{-z} - R_q(z) = O(z^{2q+1}): halving z divides it by 2^{2q+1}
+    z = np.array([0.08, 0.04])
+    err = np.abs(np.exp(-z) - ed.amplification(z, f"gl{q}"))
+    assert abs(np.log2(err[0] / err[1]) - (2 * q + 1)) < 0.1
+    # A-stability: |R| <= 1 on the closed right half plane, |R| = 1 on the axis
+    x, y = np.meshgrid(np.linspace(0, 50, 41), np.linspace(-50, 50, 41))
+    zz = x + 1j * y
+    assert np.all(np.abs(ed.amplification(zz, f"gl{q}")) <= 1 + 1e-12)
+    assert np.allclose(np.abs(ed.amplification(1j * np.linspace(-40, 40, 17), f"gl{q}")), 1.0)
+    # partial fractions reproduce the rational function
+    zp, a, r_inf = ed.pade_partial_fractions(q)
+    t = np.array([0.3, 2.0, 17.0, 1e3])
+    assert np.allclose(r_inf + sum(aj / (t - zj) for zj, aj in zip(zp, a)),
+                       ed.amplification(t, f"gl{q}"), rtol=1e-12, atol=1e-14)

@@ -210,7 +210,7 @@ def _exact_run(model, N, chi, scheme, K, seed):
     return H, dense, states, infos
 
 
-@pytest.mark.parametrize("scheme", ["be", "tr"])
+@pytest.mark.parametrize("scheme", ["be", "tr", "gl2", "gl3"])
 def test_converged_linsolve_equals_dense_propagator(scheme):
     # Converged sweeps at full bond dimension solve each implicit step exactly,
     # so the MPS path must reproduce prod_k R(dtau_k (H - E0)) psi0.
