@@ -67,8 +67,19 @@ typedef enum {
 } ite_status;
 
 /* Time stepper.  Trapezoid: Eq. 4 (A-stable, App. A).  Backward Euler: the
- * first-order A-stable (and L-stable) implicit step, R(z) = 1/(1+z). */
-typedef enum { ITE_BACKWARD_EULER = 0, ITE_TRAPEZOID = 1 } ite_scheme;
+ * first-order A-stable (and L-stable) implicit step, R(z) = 1/(1+z).
+ * Gauss-Legendre q = 2, 3: the paper's Gauss-Legendre collocation (Method,
+ * spectral panel scheme); for this linear ODE the q-stage collocation step is
+ * R_q(z) = P_q(-z)/P_q(z), the (q, q) Pade approximant of e^{-z} (order 2q,
+ * A-stable), evaluated as q complex-shifted solves (I + c_j (H - s)) x_j = psi
+ * and a two-site fit of r_inf psi + sum_j w_j x_j (see
+ * ite_gl_partial_fractions); opts.fit_sweeps sweeps of that fit. */
+typedef enum {
+  ITE_BACKWARD_EULER = 0,
+  ITE_TRAPEZOID = 1,
+  ITE_GAUSS_LEGENDRE_2 = 2,
+  ITE_GAUSS_LEGENDRE_3 = 3
+} ite_scheme;
 
 /* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere on the
  * FP64 pipes.  ITE_FP64_TC: the same algorithm, with every large contraction
@@ -182,6 +193,11 @@ ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, i
  * k = 1..n_steps, and evolution over it.  per_step[n_steps], nodes[n_steps+1]
  * may be NULL. */
 ite_status ite_grid_geometric(double tau0, double tau_max, int n_steps, double* nodes);
+/* Partial fractions of the q-stage Gauss-Legendre step (host only, q = 1..8):
+ * R_q(z) = r_inf + sum_j a_j / (z - z_j); poles[2q] and residues[2q] receive
+ * z_j and a_j (interleaved complex).  The step with dtau uses the shifts
+ * c_j = -dtau / z_j and the weights w_j = -a_j / z_j. */
+ite_status ite_gl_partial_fractions(int q, double* poles, double* residues, double* r_inf);
 ite_status ite_evolve_loggrid(ite_ctx ctx, ite_mpo H, ite_mps psi, double tau0, double tau_max,
                               int n_steps, int scheme, int shift_mode, double shift0,
                               int chi_max, double cutoff, const ite_solver_opts* opts,

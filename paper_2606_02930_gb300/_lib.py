@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libite.so")
 (ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA,
  ITE_PENDING) = range(8)
 ITE_MODEL_HEISENBERG, ITE_MODEL_ANDERSON = 0, 1
-ITE_BACKWARD_EULER, ITE_TRAPEZOID = 0, 1
+ITE_BACKWARD_EULER, ITE_TRAPEZOID, ITE_GAUSS_LEGENDRE_2, ITE_GAUSS_LEGENDRE_3 = 0, 1, 2, 3
 ITE_FP64, ITE_FP64_TC = 0, 1
 ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
 STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",
@@ -102,6 +102,7 @@ SIGNATURES = {
     "ite_implicit_step": (_i, [_vp, _vp, _vp, _d, _i, _d, _i, _d, C.POINTER(ite_solver_opts),
                                C.POINTER(ite_step_info)]),
     "ite_grid_geometric": (_i, [_d, _d, _i, _pd]),
+    "ite_gl_partial_fractions": (_i, [_i, _pd, _pd, _pd]),
     "ite_evolve_loggrid": (_i, [_vp, _vp, _vp, _d, _d, _i, _i, _i, _d, _i, _d,
                                 C.POINTER(ite_solver_opts), C.POINTER(ite_step_info), _pd]),
     "ite_grid_panels": (_i, [_d, _i, _i, _pd]),

@@ -16,7 +16,9 @@ from ._lib import lib, check
 
 BACKWARD_EULER, TRAPEZOID = L.ITE_BACKWARD_EULER, L.ITE_TRAPEZOID
 SHIFT_FIXED, SHIFT_CURRENT_ENERGY = L.ITE_SHIFT_FIXED, L.ITE_SHIFT_CURRENT_ENERGY
-SCHEMES = {"be": BACKWARD_EULER, "tr": TRAPEZOID}
+GAUSS_LEGENDRE_2, GAUSS_LEGENDRE_3 = L.ITE_GAUSS_LEGENDRE_2, L.ITE_GAUSS_LEGENDRE_3
+SCHEMES = {"be": BACKWARD_EULER, "tr": TRAPEZOID, "gl2": GAUSS_LEGENDRE_2,
+           "gl3": GAUSS_LEGENDRE_3}
 
 
 def _scheme(s):
@@ -224,6 +226,15 @@ def evolve_panels(ctx, H, psi, tau_max, P, n, scheme, chi_max, cutoff, shift_mod
                   shift0=0.0, opts=None):
     return _evolve(lib.ite_evolve_panels, ctx, H, psi, (tau_max, P, n), P * n, scheme, shift_mode,
                    shift0, chi_max, cutoff, opts)
+
+
+def gl_partial_fractions(q):
+    """(poles z_j, residues a_j, r_inf) of the q-stage Gauss-Legendre step."""
+    z = np.zeros(2 * q)
+    a = np.zeros(2 * q)
+    r = C.c_double()
+    check(lib.ite_gl_partial_fractions(q, _dptr(z), _dptr(a), C.byref(r)))
+    return z.view(np.complex128), a.view(np.complex128), r.value
 
 
 def grid_geometric(tau0, tau_max, n_steps):

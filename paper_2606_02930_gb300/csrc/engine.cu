@@ -82,7 +82,8 @@ struct ite_ctx_s {
   std::string err;
   size_t bytes = 0;
   // workspace
-  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu;
+  Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu,
+      ws_ovm;
   GmresState* gm = nullptr;
   double* dscal = nullptr;     // device scalars
   cplx* dcplx = nullptr;       // device complex scalars
@@ -121,6 +122,7 @@ struct ite_mps_s {
   Buf mem;
   std::vector<cplx*> site;
   ite_mps work_x = nullptr, work_b = nullptr, work_p = nullptr;  // internal copies for the step
+  std::vector<ite_mps> work_gl;            // Gauss-Legendre partial-fraction solutions
 };
 
 // ------------------------------------------------------------------ memory
@@ -473,7 +475,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
 
 // One GMRES cycle on (alpha I + c H_eff) X = B; X updated in place.
 ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
-                       const cplx* R, const cplx* B, cplx* X, double alpha, double c, int m,
+                       const cplx* R, const cplx* B, cplx* X, cplx alpha, cplx c, int m,
                        double local_tol, int* steps, double* res) {
   Scope sc(ctx, P_SOLVE);
   const long long n = (long long)chl * H->d * H->d * chr;
@@ -482,7 +484,7 @@ ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cp
   int* active = &gs->active;
   double* r0n2 = ctx->dscal + 0;
   double* bn2 = ctx->dscal + 1;
-  const cplx ca = C(alpha), cc = C(c);
+  const cplx ca = alpha, cc = c;
   // r0 = B - A X0
   CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, X, V, cc, X, ca));
   CK(vec_axpby(V, B, C(1), C(-1), n, ctx->stream));
@@ -679,6 +681,7 @@ void mps_free(ite_mps m) {
   if (m->work_x) mps_free(m->work_x);
   if (m->work_b) mps_free(m->work_b);
   if (m->work_p) mps_free(m->work_p);
+  for (ite_mps w : m->work_gl) mps_free(w);
   buf_free(m->ctx, m->mem);
   delete m;
 }
@@ -831,7 +834,7 @@ struct SweepStats {
 };
 
 // Two-site sweep solving (alpha I + c H) x = b, or (fit mode) x ~ alpha b + beta H b.
-ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, double alpha, double cbeta,
+ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, cplx alpha, cplx cbeta,
                  int chi_max, double cutoff, const ite_solver_opts& o, SweepStats& stats) {
   const int N = x->N, d = x->d;
   EnvSet e = carve_envs(ctx, H, x->cap);
@@ -869,7 +872,7 @@ ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, double 
         CS(project(ctx, d, chl, bl, bm, br, chr, e.LO[i], b->site[i], b->site[i + 1], e.RO[i + 2], B));
         cplx* theta = P<cplx>(ctx->ws_X2);
         CS(merge(ctx, d, bl, bm, br, b->site[i], b->site[i + 1], theta));
-        CS(heff(ctx, H, i, chl, bl, br, chr, e.LE[i], e.RE[i + 2], theta, X, C(cbeta), B, C(alpha)));
+        CS(heff(ctx, H, i, chl, bl, br, chr, e.LE[i], e.RE[i + 2], theta, X, cbeta, B, alpha));
       }
       int r = 0;
       double disc = 0.0;
@@ -890,6 +893,138 @@ ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, double 
     }
   }
   return ITE_OK;
+}
+
+// Two-site variational fit y ~ sum_t coef[t] targets[t], starting from y
+// as given (right-canonical): each local block is the exact projection of
+// the combination onto y's current environments, i.e. the sum of the
+// targets' two-site blocks, each contracted with its own pair of overlap
+// environments.  Forms the Gauss-Legendre step from its partial-fraction
+// solutions.
+ite_status fit_combination(ite_ctx ctx, ite_mps y, const std::vector<ite_mps>& tg,
+                           const std::vector<cplx>& coef, int chi_max, double cutoff, int sweeps,
+                           SweepStats& stats) {
+  const int N = y->N, d = y->d, T = (int)tg.size();
+  long long ovs = 0;
+  for (int b = 0; b <= N; ++b) ovs += (long long)y->cap[b] * y->cap[b];
+  CS(buf_ensure(ctx, ctx->ws_ovm, (size_t)2 * T * ovs * sizeof(cplx)));
+  std::vector<std::vector<cplx*>> LO(T, std::vector<cplx*>(N + 1)), RO(T, std::vector<cplx*>(N + 1));
+  {
+    cplx* p = P<cplx>(ctx->ws_ovm);
+    for (int t = 0; t < T; ++t)
+      for (int b = 0; b <= N; ++b) {
+        const long long ov = (long long)y->cap[b] * y->cap[b];
+        LO[t][b] = p; p += ov;
+        RO[t][b] = p; p += ov;
+      }
+  }
+  cplx* X = P<cplx>(ctx->ws_X);
+  cplx* B = P<cplx>(ctx->ws_B);
+  for (int sw = 0; sw < std::max(1, sweeps); ++sw) {
+    for (int t = 0; t < T; ++t) {
+      const ite_mps k = tg[t];
+      CS(set_one(ctx, RO[t][N]));
+      CS(set_one(ctx, LO[t][0]));
+      for (int i = N - 1; i >= 2; --i)
+        CS(ov_right(ctx, d, y->chi[i], k->chi[i], y->chi[i + 1], k->chi[i + 1], RO[t][i + 1],
+                    y->site[i], k->site[i], RO[t][i]));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool lr = pass == 0;
+      for (int kk = 0; kk < N - 1; ++kk) {
+        const int i = lr ? kk : N - 2 - kk;
+        const int chl = y->chi[i], chr = y->chi[i + 2];
+        const long long n = (long long)chl * d * d * chr;
+        CK(vec_zero(X, n, ctx->stream));
+        for (int t = 0; t < T; ++t) {
+          const ite_mps k = tg[t];
+          CS(project(ctx, d, chl, k->chi[i], k->chi[i + 1], k->chi[i + 2], chr, LO[t][i],
+                     k->site[i], k->site[i + 1], RO[t][i + 2], B));
+          CK(vec_axpby(X, B, coef[t], C(1), n, ctx->stream));
+        }
+        int r = 0;
+        double disc = 0.0;
+        CS(split(ctx, X, chl * d, d * chr, chi_max, cutoff, lr, y->site[i], y->site[i + 1], &r, &disc));
+        y->chi[i + 1] = r;
+        stats.max_disc = std::max(stats.max_disc, disc);
+        for (int t = 0; t < T; ++t) {
+          const ite_mps k = tg[t];
+          if (lr)
+            CS(ov_left(ctx, d, y->chi[i], k->chi[i], y->chi[i + 1], k->chi[i + 1], LO[t][i],
+                       y->site[i], k->site[i], LO[t][i + 1]));
+          else
+            CS(ov_right(ctx, d, y->chi[i + 1], k->chi[i + 1], y->chi[i + 2], k->chi[i + 2],
+                        RO[t][i + 2], y->site[i + 1], k->site[i + 1], RO[t][i + 1]));
+        }
+      }
+    }
+  }
+  return ITE_OK;
+}
+
+// R_q(z) = P_q(-z) / P_q(z), the (q, q) Pade approximant of e^{-z} (the
+// Gauss-Legendre collocation step of the linear ODE), in partial fractions:
+// r_inf + sum_j a_j / (z - z_j).  P_q(z) = sum_k (2q-k)! q! / ((2q)! k! (q-k)!)
+// z^k; its roots by the Durand-Kerner (Weierstrass) iteration polished by
+// Newton steps; a_j = P_q(-z_j) / P_q'(z_j); r_inf = (-1)^q.
+struct Cd {
+  double re, im;
+};
+Cd cd_add(Cd a, Cd b) { return {a.re + b.re, a.im + b.im}; }
+Cd cd_sub(Cd a, Cd b) { return {a.re - b.re, a.im - b.im}; }
+Cd cd_mul(Cd a, Cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+Cd cd_div(Cd a, Cd b) {
+  const double den = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+Cd cd_poly(const std::vector<double>& p, Cd z) {   // p[k] z^k, Horner
+  Cd acc{0.0, 0.0};
+  for (int k = (int)p.size() - 1; k >= 0; --k) acc = cd_add(cd_mul(acc, z), Cd{p[k], 0.0});
+  return acc;
+}
+bool gl_partial_fractions(int q, std::vector<Cd>& z, std::vector<Cd>& a, double* r_inf) {
+  if (q < 1 || q > 8) return false;
+  std::vector<double> p(q + 1), pm(q + 1), dp(q);
+  auto fact = [](int n) {
+    double f = 1.0;
+    for (int k = 2; k <= n; ++k) f *= k;
+    return f;
+  };
+  for (int k = 0; k <= q; ++k) {
+    p[k] = fact(2 * q - k) * fact(q) / (fact(2 * q) * fact(k) * fact(q - k));
+    pm[k] = (k % 2 ? -1.0 : 1.0) * p[k];
+  }
+  for (int k = 1; k <= q; ++k) dp[k - 1] = k * p[k];
+  // monic form for Durand-Kerner
+  std::vector<double> mon(q + 1);
+  for (int k = 0; k <= q; ++k) mon[k] = p[k] / p[q];
+  z.assign(q, Cd{0.0, 0.0});
+  Cd seed{0.4, 0.9};
+  Cd w{1.0, 0.0};
+  for (int j = 0; j < q; ++j) {
+    z[j] = cd_mul(w, Cd{4.0, 0.0});
+    w = cd_mul(w, seed);
+  }
+  for (int it = 0; it < 500; ++it) {
+    double change = 0.0;
+    for (int j = 0; j < q; ++j) {
+      Cd den{1.0, 0.0};
+      for (int k = 0; k < q; ++k)
+        if (k != j) den = cd_mul(den, cd_sub(z[j], z[k]));
+      const Cd step = cd_div(cd_poly(mon, z[j]), den);
+      z[j] = cd_sub(z[j], step);
+      change = std::max(change, std::hypot(step.re, step.im));
+    }
+    if (change < 1e-15) break;
+  }
+  for (int j = 0; j < q; ++j)
+    for (int it = 0; it < 3; ++it) z[j] = cd_sub(z[j], cd_div(cd_poly(p, z[j]), cd_poly(dp, z[j])));
+  a.resize(q);
+  for (int j = 0; j < q; ++j) a[j] = cd_div(cd_poly(pm, z[j]), cd_poly(dp, z[j]));
+  *r_inf = q % 2 ? -1.0 : 1.0;
+  for (int j = 0; j < q; ++j)
+    if (!std::isfinite(z[j].re) || !std::isfinite(z[j].im)) return false;
+  return true;
 }
 
 }  // namespace
@@ -949,7 +1084,7 @@ void ite_ctx_destroy(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu};
+                 &ctx->ws_emu, &ctx->ws_ovm};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
@@ -1102,7 +1237,9 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
   CS(validate_pair(ctx, H, psi));
   if (!(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(shift) || !(cutoff >= 0.0) ||
       chi_max < 1 || chi_max > psi->chi_cap || o.krylov_dim < 1 || o.krylov_dim > kMaxKrylov ||
-      o.sweeps < 1 || o.fit_sweeps < 1 || (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID) ||
+      o.sweeps < 1 || o.fit_sweeps < 1 ||
+      (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID &&
+       scheme != ITE_GAUSS_LEGENDRE_2 && scheme != ITE_GAUSS_LEGENDRE_3) ||
       (o.precision != ITE_FP64 && o.precision != ITE_FP64_TC) || psi->N < 2)
     return fail(ctx, ITE_EINVAL, "invalid step arguments");
   CS(ensure_work(ctx, psi));
@@ -1115,33 +1252,76 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
   ctx->gemm_mode = o.precision == ITE_FP64_TC ? 1 : 0;
   CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
   SweepStats st;
-  ite_mps x = psi->work_x, bm = psi;
-  double c;
-  if (scheme == ITE_BACKWARD_EULER) {
-    c = dtau;
-  } else {
-    c = 0.5 * dtau;
-    bm = psi->work_b;
-    CS(mps_copy_into(ctx, psi, bm));
-    CS(right_canonicalize(ctx, bm));
-    for (int f = 0; f < o.fit_sweeps; ++f)
-      CS(sweep(ctx, H, bm, psi, true, 1.0 + c * shift, -c, chi_max, cutoff, o, st));
-  }
-  CS(mps_copy_into(ctx, bm, x));
-  CS(right_canonicalize(ctx, x));
+  ite_mps x = psi->work_x;
   if (o.sweep_tol > 0.0 && !psi->work_p) CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &psi->work_p));
-  for (int s = 0; s < o.sweeps; ++s) {
-    const bool check = o.sweep_tol > 0.0 && s > 0;
-    if (check) CS(mps_copy_into(ctx, x, psi->work_p));
-    CS(sweep(ctx, H, x, bm, false, 1.0 - c * shift, c, chi_max, cutoff, o, st));
-    if (check) {
-      cplx ab, aa, bb;
-      CS(overlap_impl(ctx, psi->work_p, x, nullptr, &ab));
-      CS(overlap_impl(ctx, psi->work_p, psi->work_p, nullptr, &aa));
-      CS(overlap_impl(ctx, x, x, nullptr, &bb));
-      const double ov = std::hypot(ab.x, ab.y) / std::sqrt(aa.x * bb.x);
-      if (1.0 - ov < o.sweep_tol) break;
+  // sweeps of the linear solve (1 - c s) xx + c H xx = b from the guess in xx
+  auto solve = [&](ite_mps xx, ite_mps b, cplx c) -> ite_status {
+    const cplx alpha = csub(C(1), cscale(c, shift));
+    for (int s = 0; s < o.sweeps; ++s) {
+      const bool check = o.sweep_tol > 0.0 && s > 0;
+      if (check) CS(mps_copy_into(ctx, xx, psi->work_p));
+      CS(sweep(ctx, H, xx, b, false, alpha, c, chi_max, cutoff, o, st));
+      if (check) {
+        cplx ab, aa, bb;
+        CS(overlap_impl(ctx, psi->work_p, xx, nullptr, &ab));
+        CS(overlap_impl(ctx, psi->work_p, psi->work_p, nullptr, &aa));
+        CS(overlap_impl(ctx, xx, xx, nullptr, &bb));
+        const double ov = std::hypot(ab.x, ab.y) / std::sqrt(aa.x * bb.x);
+        if (1.0 - ov < o.sweep_tol) break;
+      }
     }
+    return ITE_OK;
+  };
+  if (scheme == ITE_GAUSS_LEGENDRE_2 || scheme == ITE_GAUSS_LEGENDRE_3) {
+    // psi_k = r_inf psi + sum_j w_j x_j, (I + c_j H') x_j = psi, c_j = -dtau / z_j,
+    // w_j = -a_j / z_j, from R_q(z) = r_inf + sum_j a_j / (z - z_j)
+    const int q = scheme == ITE_GAUSS_LEGENDRE_2 ? 2 : 3;
+    std::vector<Cd> zp, ap;
+    double r_inf = 0.0;
+    if (!gl_partial_fractions(q, zp, ap, &r_inf)) return fail(ctx, ITE_EINVAL, "no Pade poles");
+    while ((int)psi->work_gl.size() < q) {
+      ite_mps w = nullptr;
+      CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &w));
+      psi->work_gl.push_back(w);
+    }
+    std::vector<ite_mps> targets{psi};
+    std::vector<cplx> coefs{C(r_inf)};
+    for (int j = 0; j < q; ++j) {
+      ite_mps xj = psi->work_gl[j];
+      CS(mps_copy_into(ctx, psi, xj));
+      CS(right_canonicalize(ctx, xj));
+      const Cd cj = cd_div(Cd{-dtau, 0.0}, zp[j]);
+      CS(solve(xj, psi, C(cj.re, cj.im)));
+      const Cd wj = cd_div(Cd{-ap[j].re, -ap[j].im}, zp[j]);
+      targets.push_back(xj);
+      coefs.push_back(C(wj.re, wj.im));
+    }
+    CS(mps_copy_into(ctx, psi, x));
+    CS(right_canonicalize(ctx, x));
+    CS(fit_combination(ctx, x, targets, coefs, chi_max, cutoff, o.fit_sweeps, st));
+    // right operator environments of x, for the energy below
+    EnvSet e = carve_envs(ctx, H, x->cap);
+    const int N = x->N;
+    CS(set_one(ctx, e.RE[N]));
+    for (int i = N - 1; i >= 1; --i)
+      CS(env_right(ctx, H, i, x->chi[i], x->chi[i], x->chi[i + 1], x->chi[i + 1], e.RE[i + 1],
+                   x->site[i], x->site[i], e.RE[i]));
+  } else {
+    ite_mps bm = psi;
+    double c;
+    if (scheme == ITE_BACKWARD_EULER) {
+      c = dtau;
+    } else {
+      c = 0.5 * dtau;
+      bm = psi->work_b;
+      CS(mps_copy_into(ctx, psi, bm));
+      CS(right_canonicalize(ctx, bm));
+      for (int f = 0; f < o.fit_sweeps; ++f)
+        CS(sweep(ctx, H, bm, psi, true, C(1.0 + c * shift), C(-c), chi_max, cutoff, o, st));
+    }
+    CS(mps_copy_into(ctx, bm, x));
+    CS(right_canonicalize(ctx, x));
+    CS(solve(x, bm, C(c)));
   }
   // normalise the centre tensor (site 0; the rest is right-orthonormal)
   const long long n0 = (long long)x->chi[0] * x->d * x->chi[1];
@@ -1471,6 +1651,19 @@ ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, i
   return step_impl(ctx, H, psi, dtau, scheme, shift, chi_max, cutoff, o, info);
 }
 
+ite_status ite_gl_partial_fractions(int q, double* poles, double* residues, double* r_inf) {
+  if (!poles || !residues || !r_inf) return ITE_EINVAL;
+  std::vector<Cd> z, a;
+  if (!gl_partial_fractions(q, z, a, r_inf)) return ITE_EINVAL;
+  for (int j = 0; j < q; ++j) {
+    poles[2 * j] = z[j].re;
+    poles[2 * j + 1] = z[j].im;
+    residues[2 * j] = a[j].re;
+    residues[2 * j + 1] = a[j].im;
+  }
+  return ITE_OK;
+}
+
 ite_status ite_grid_geometric(double tau0, double tau_max, int n_steps, double* nodes) {
   if (!nodes || n_steps < 1 || !(tau0 > 0.0) || !(tau_max >= tau0)) return ITE_EINVAL;
   grid_geometric_impl(tau0, tau_max, n_steps, nodes);
@@ -1632,7 +1825,7 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   int s = 0;
   double r = 0.0;
   CS(local_solve(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B, (cplx*)X,
-                 alpha, c, krylov_dim, local_tol, &s, &r));
+                 C(alpha), C(c), krylov_dim, local_tol, &s, &r));
   if (steps) *steps = s;
   if (rel_res) *rel_res = r;
   return kernel_finish(ctx);
@@ -1735,7 +1928,7 @@ void internal_release_workspace(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu};
+                 &ctx->ws_emu, &ctx->ws_ovm};
   for (Buf* b : bufs) buf_free(ctx, *b);
 }
 

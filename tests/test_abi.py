@@ -68,3 +68,19 @@ def test_invalid_arguments_fail_cleanly():
     assert lib.ite_ctx_create(10**6, None, _lib.ite_alloc_fn(), _lib.ite_free_fn(), None,
                               ctypes.byref(out)) != _lib.ITE_OK
     assert lib.ite_last_error(None) == b"null context"
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_gl_partial_fractions_match_the_oracle(q):
+    # the library's Durand-Kerner poles and residues against numpy's roots of
+    # the same Pade denominator (oracle)
+    import numpy as np
+    from oracle import ed
+    from paper_2606_02930_gb300 import api
+    z, a, r = api.gl_partial_fractions(q)
+    zo, ao, ro = ed.pade_partial_fractions(q)
+    assert r == ro
+    for zj, aj in zip(zo, ao):
+        k = int(np.argmin(np.abs(z - zj)))
+        assert abs(z[k] - zj) < 1e-12 * abs(zj)
+        assert abs(a[k] - aj) < 1e-11 * abs(aj)

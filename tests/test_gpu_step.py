@@ -305,3 +305,46 @@ def test_rank_deficient_start_takes_the_svd_gauge(api, ctx, precision):
         assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
         assert infid(ost, gst) <= TOL
         assert ginfo["max_chi"] == oinfo.max_chi
+
+
+@pytest.mark.parametrize("scheme,precision", [("gl2", "fp64"), ("gl3", "fp64"), ("gl2", "fp64_tc")])
+def test_gauss_legendre_fixed_mode(api, ctx, scheme, precision):
+    # the paper's Gauss-Legendre step (q complex-shifted solves and the fit of
+    # their combination), fixed effort, against the oracle step by step
+    N = 10
+    Ws = ompo.heisenberg_mpo(N)
+    H = api.mpo_create_heisenberg(ctx, N)
+    psi0 = omps.product_state(inputs.random_product_state(N, 2, 1000))
+    nodes = ogrid.geometric_grid(1e-2, 1e2, 8)
+    pairs = run_pair(api, ctx, Ws, H, psi0, nodes, scheme, 24, 1e-12, shift_mode="energy",
+                     opts=api.solver_opts(precision=precision))
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
+        assert infid(ost, gst) <= TOL
+        assert abs(ginfo["norm_before"] - oinfo.norm_before) <= 1e-10
+        assert ginfo["max_chi"] == oinfo.max_chi
+        assert ginfo["gmres_steps"] == oinfo.gmres_steps
+
+
+def test_gauss_legendre_converged_equals_dense_propagator(api, ctx):
+    # converged solves and fit at full bond dimension: the step is exactly
+    # R_q(dtau (H - E0)) with R_q the (q, q) Pade approximant of e^{-z}
+    N = 8
+    H = api.mpo_create_heisenberg(ctx, N)
+    Hd = ed.heisenberg_hamiltonian(N)
+    e0 = np.linalg.eigvalsh(Hd)[0]
+    sv = inputs.random_product_state(N, 2, 1000)
+    v0 = sv[0]
+    for k in range(1, N):
+        v0 = np.kron(v0, sv[k])
+    nodes = ogrid.geometric_grid(1e-2, 1e2, 6)
+    for scheme in ("gl2", "gl3"):
+        dense, _, _ = ed.propagate_discrete(Hd, v0, ogrid.steps(nodes), scheme, shifts=e0)
+        psi = api.mps_create(ctx, omps.product_state(sv), 16)
+        opts = api.solver_opts(local_tol=1e-13, sweeps=12, sweep_tol=1e-15, fit_sweeps=6,
+                               krylov_dim=20)
+        _, infos = api.evolve_loggrid(ctx, H, psi, 1e-2, 1e2, 6, scheme, 16, 0.0,
+                                      shift0=e0, opts=opts)
+        for v, info in zip(dense, infos):
+            assert abs(ed.energy(Hd, v) - info["energy"]) <= 1e-10 * abs(ed.energy(Hd, v))
+        assert ed.infidelity(dense[-1], omps.to_dense(psi.tensors())) <= 1e-10
