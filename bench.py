@@ -49,6 +49,10 @@ WORKLOAD = ("heisenberg_bulk: XXX chain N=64 J=1 OBC, D=5, chi_max=256, cutoff 1
             "saturated synthetic start (chi=256 bulk)")
 
 
+SCHEME_NAMES = {"be": "backward_euler", "tr": "trapezoid", "gl2": "gauss_legendre_2",
+                "gl3": "gauss_legendre_3"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -61,6 +65,8 @@ def parse():
                     help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores")
     ap.add_argument("--only", choices=["heff", "split"], default=None,
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
+    ap.add_argument("--scheme", choices=["be", "tr", "gl2", "gl3"], default="be",
+                    help="time stepper of the chain workload (the headline runs backward Euler)")
     ap.add_argument("--workload", choices=["chain", "batch"], default="chain",
                     help="batch: a bounded sample of the batched workload served side by side")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
@@ -218,7 +224,7 @@ def run_ours(args, rank, world, local_rank):
 
     def one_step(p):
         k = state["k"] % K_GRID
-        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], "be", state["s"], CHI, CUTOFF,
+        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], args.scheme, state["s"], CHI, CUTOFF,
                                  opts)
         state["k"] += 1
         state["s"] = info["energy"]
@@ -298,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_SITES, "chi_max": CHI, "cutoff": CUTOFF,
-                       "scheme": "backward_euler", "precision": args.precision,
+                       "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state 134 MB + environments 0.7 GB per chain)"},
             "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,

@@ -1069,6 +1069,11 @@ ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free
     ite_ctx_destroy(ctx);
     return ITE_ENOMEM;
   }
+  // error words and device states start cleared
+  if (cudaMemsetAsync(ctx->dcounter, 0, 64 * sizeof(int), ctx->stream) != cudaSuccess) {
+    ite_ctx_destroy(ctx);
+    return ITE_ECUDA;
+  }
   *out = ctx;
   return ITE_OK;
 }
