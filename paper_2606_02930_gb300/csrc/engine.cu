@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace ite;
@@ -101,6 +102,10 @@ struct ite_ctx_s {
   size_t evused = 0;
   struct Rec { int cat; size_t e0, e1; double flops; };
   std::vector<Rec> recs;
+  // child contexts, each on its own stream, for solves that run concurrently
+  // (the Gauss-Legendre step's shifted solves)
+  std::vector<ite_ctx> children;
+  std::vector<cudaStream_t> child_streams;
 };
 
 struct ite_mpo_s {
@@ -1086,6 +1091,10 @@ ite_status ite_ctx_set_stream(ite_ctx ctx, void* stream) {
 
 void ite_ctx_destroy(ite_ctx ctx) {
   if (!ctx) return;
+  for (size_t k = 0; k < ctx->children.size(); ++k) {
+    ite_ctx_destroy(ctx->children[k]);
+    cudaStreamDestroy(ctx->child_streams[k]);
+  }
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
@@ -1237,6 +1246,33 @@ ite_status normalize_impl(ite_ctx ctx, ite_mps psi) {
   return ITE_OK;
 }
 
+// Stream-ordered allocation on a child context's own stream.
+void* child_alloc(size_t bytes, void* user) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, static_cast<cudaStream_t>(user)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void child_free(void* p, size_t, void* user) { cudaFreeAsync(p, static_cast<cudaStream_t>(user)); }
+
+ite_status ensure_children(ite_ctx ctx, int n) {
+  while ((int)ctx->children.size() < n) {
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ite_ctx c = nullptr;
+    const ite_status r = ite_ctx_create(ctx->device, st, child_alloc, child_free, st, &c);
+    if (r != ITE_OK) {
+      cudaStreamDestroy(st);
+      return fail(ctx, r, "cannot create a child context");
+    }
+    ctx->children.push_back(c);
+    ctx->child_streams.push_back(st);
+  }
+  return ITE_OK;
+}
+
 ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int scheme, double shift,
                      int chi_max, double cutoff, const ite_solver_opts& o, ite_step_info* info) {
   CS(validate_pair(ctx, H, psi));
@@ -1291,15 +1327,63 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
     }
     std::vector<ite_mps> targets{psi};
     std::vector<cplx> coefs{C(r_inf)};
+    std::vector<cplx> cs(q);
     for (int j = 0; j < q; ++j) {
       ite_mps xj = psi->work_gl[j];
       CS(mps_copy_into(ctx, psi, xj));
       CS(right_canonicalize(ctx, xj));
       const Cd cj = cd_div(Cd{-dtau, 0.0}, zp[j]);
-      CS(solve(xj, psi, C(cj.re, cj.im)));
+      cs[j] = C(cj.re, cj.im);
       const Cd wj = cd_div(Cd{-ap[j].re, -ap[j].im}, zp[j]);
       targets.push_back(xj);
       coefs.push_back(C(wj.re, wj.im));
+    }
+    if (o.sweep_tol > 0.0) {
+      // the convergence check shares one scratch MPS: solve one at a time
+      for (int j = 0; j < q; ++j) CS(solve(psi->work_gl[j], psi, cs[j]));
+    } else {
+      // The q solves are independent: each runs in a child context (own
+      // stream, own workspaces) from its own host thread, so that their
+      // kernels overlap on the GPU; they only read psi and the MPO.
+      CS(ensure_children(ctx, q));
+      CS(sync(ctx));
+      std::vector<SweepStats> cst(q);
+      std::vector<ite_status> cres(q, ITE_OK);
+      std::vector<std::thread> th;
+      for (int j = 0; j < q; ++j) {
+        th.emplace_back([&, j] {
+          ite_ctx cc = ctx->children[j];
+          ite_status r = cudaSetDevice(ctx->device) == cudaSuccess ? ITE_OK : ITE_ECUDA;
+          cc->gemm_mode = ctx->gemm_mode;
+          if (r == ITE_OK &&
+              cudaMemsetAsync(reinterpret_cast<int*>(cc->dcounter) + 10, 0, sizeof(int), cc->stream) !=
+                  cudaSuccess)
+            r = ITE_ECUDA;
+          if (r == ITE_OK) r = ensure_workspace(cc, H, psi->cap, psi->d, o.krylov_dim);
+          const cplx alpha = csub(C(1), cscale(cs[j], shift));
+          for (int sw = 0; sw < o.sweeps && r == ITE_OK; ++sw)
+            r = sweep(cc, H, psi->work_gl[j], psi, false, alpha, cs[j], chi_max, cutoff, o, cst[j]);
+          if (r == ITE_OK) r = sync(cc);
+          cc->gemm_mode = 0;
+          cres[j] = r;
+        });
+      }
+      for (auto& t : th) t.join();
+      for (int j = 0; j < q; ++j) {
+        ite_ctx cc = ctx->children[j];
+        if (cres[j] != ITE_OK) return fail(ctx, cres[j], cc->err);
+        st.steps += cst[j].steps;
+        st.max_res = std::max(st.max_res, cst[j].max_res);
+        st.max_disc = std::max(st.max_disc, cst[j].max_disc);
+        ctx->jacobi_sweeps_total += cc->jacobi_sweeps_total;
+        ctx->jacobi_splits += cc->jacobi_splits;
+        ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, cc->jacobi_sweeps_max);
+        ctx->jacobi_flops += cc->jacobi_flops;
+        ctx->lq_flops += cc->lq_flops;
+        cc->jacobi_sweeps_total = cc->jacobi_splits = 0;
+        cc->jacobi_sweeps_max = 0;
+        cc->jacobi_flops = cc->lq_flops = 0.0;
+      }
     }
     CS(mps_copy_into(ctx, psi, x));
     CS(right_canonicalize(ctx, x));
