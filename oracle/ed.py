@@ -135,7 +135,9 @@ def pade_partial_fractions(q):
 def amplification(z, scheme):
     """One-step amplification factor of the linear test problem y' = -lambda y
     at z = lambda * dtau (App. A).  'be': backward Euler; 'tr': implicit
-    trapezoid rule (Eq. 4); 'fe': forward Euler (the explicit counter-example);
+    trapezoid rule (Eq. 4); 'fe': forward Euler and 'heun': Heun's explicit
+    predictor-corrector step (the explicit counter-examples of the stability
+    section);
     'gl<q>': q-stage Gauss-Legendre collocation, the (q, q) Pade approximant
     P_q(-z) / P_q(z) of e^{-z}."""
     if str(scheme).startswith("gl"):
@@ -151,6 +153,9 @@ def amplification(z, scheme):
         return (1.0 - 0.5 * z) / (1.0 + 0.5 * z)
     if scheme == "fe":
         return 1.0 - z
+    if scheme == "heun":
+        # explicit trapezoid (predictor-corrector) step: 1 - z + z^2 / 2
+        return 1.0 - z + 0.5 * z * z
     raise ValueError(scheme)
 
 

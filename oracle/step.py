@@ -7,6 +7,11 @@ Schemes (H' = H - s):
           (I - c H') psi_{k-1} and is also the initial guess (App. B).
 * 'be' -- backward Euler: (I + c H') psi_k = psi_{k-1} with c = dtau; b = psi_{k-1}
           and the initial guess is psi_{k-1}.
+* 'fe', 'heun' -- the explicit forward Euler and Heun (predictor-corrector)
+          steps, psi_k = (I - dtau H') psi_{k-1} and psi_k = psi_{k-1}/2 +
+          (I - dtau H') psi*/2 with psi* the Euler predictor, each product formed
+          by two-site fits: the unstable counter-examples of the stability
+          section (|1 - z + z^2/2| > 1 once z > 2).
 * 'gl<q>' -- q-stage Gauss-Legendre collocation (Method: the spectral panel
           method), which for this linear ODE is psi_k = R_q(dtau H') psi_{k-1}
           with R_q the (q, q) Pade approximant of e^{-z}.  By partial fractions
@@ -50,6 +55,19 @@ def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
         b, finfo = ls.fit_affine(Ws, psi, 1.0 + c * shift, -c, chi_max, cutoff, fit_sweeps)
         info.max_discarded = finfo.max_discarded
         x0 = mpsmod.copy(b)
+    elif scheme in ("fe", "heun"):
+        # explicit steps (the stability counter-examples): forward Euler
+        # psi* = (I - dtau H') psi as a two-site fit; Heun adds the corrector
+        # psi_k = psi/2 + (I - dtau H') psi* / 2
+        a, b = 1.0 + dtau * shift, -dtau
+        y, finfo = ls.fit_affine(Ws, psi, a, b, chi_max, cutoff, fit_sweeps)
+        info.max_discarded = finfo.max_discarded
+        if scheme == "heun":
+            y2, finfo = ls.fit_affine(Ws, y, a, b, chi_max, cutoff, fit_sweeps)
+            info.max_discarded = max(info.max_discarded, finfo.max_discarded)
+            y, finfo = ls.fit_combination([psi, y2], [0.5, 0.5], chi_max, cutoff, fit_sweeps)
+            info.max_discarded = max(info.max_discarded, finfo.max_discarded)
+        return _finish(y, info, Ws)
     elif str(scheme).startswith("gl"):
         from .ed import pade_partial_fractions, gl_stages
         z, a, r_inf = pade_partial_fractions(gl_stages(scheme))

@@ -297,3 +297,18 @@ def test_gauss_legendre_order_and_a_stability(q):
     t = np.array([0.3, 2.0, 17.0, 1e3])
     assert np.allclose(r_inf + sum(aj / (t - zj) for zj, aj in zip(zp, a)),
                        ed.amplification(t, f"gl{q}"), rtol=1e-12, atol=1e-14)
+
+
+def test_heun_amplification_and_its_instability():
+    # Heun's stability function from its two stages: predictor y* = y - z y,
+    # corrector y_1 = y - (z/2)(y + y*)
+    z = np.linspace(0.0, 5.0, 51)
+    pred = 1.0 - z
+    assert np.allclose(ed.amplification(z, "heun"), 1.0 - 0.5 * z * (1.0 + pred), rtol=1e-15)
+    # second order, and unstable once z exceeds 2 (the critical step of the
+    # stability section: dtau * E_max = 2)
+    zz = np.array([0.02, 0.01])
+    err = np.abs(np.exp(-zz) - ed.amplification(zz, "heun"))
+    assert abs(np.log2(err[0] / err[1]) - 3.0) < 0.1
+    r = np.abs(ed.amplification(z, "heun"))
+    assert np.all(r[z <= 2.0] <= 1.0 + 1e-15) and np.all(r[z > 2.0] > 1.0)

@@ -254,3 +254,21 @@ def test_trapezoid_fit_is_exact_at_full_bond_dimension():
     v = mps.to_dense(A)
     want = (1 + c * s) * v - c * (H @ v)
     assert np.linalg.norm(mps.to_dense(f) - want) < 1e-11 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("scheme", ["fe", "heun"])
+def test_explicit_steps_equal_dense_at_full_bond_dimension(scheme):
+    # the fitted explicit steps are exact at full bond dimension
+    N = 6
+    Ws = mpo.heisenberg_mpo(N)
+    H = ed.heisenberg_hamiltonian(N)
+    psi = inputs.random_product_state(N, 2, 5)
+    v0 = dense_of_product(psi)
+    e0 = np.linalg.eigvalsh(H)[0]
+    dts = [0.05, 0.1, 0.2]
+    dense, _, _ = ed.propagate_discrete(H, v0, dts, scheme, shifts=e0)
+    x = mps.product_state(psi)
+    for v, dt in zip(dense, dts):
+        x, info = step.implicit_step(Ws, x, dt, scheme, e0, 8, 0.0, fit_sweeps=4)
+        assert ed.infidelity(v, mps.to_dense(x)) < 1e-12
+        assert abs(ed.energy(H, v) - info.energy) < 1e-12 * abs(ed.energy(H, v))
