@@ -78,7 +78,12 @@ typedef enum {
   ITE_BACKWARD_EULER = 0,
   ITE_TRAPEZOID = 1,
   ITE_GAUSS_LEGENDRE_2 = 2,
-  ITE_GAUSS_LEGENDRE_3 = 3
+  ITE_GAUSS_LEGENDRE_3 = 3,
+  ITE_FORWARD_EULER = 4,   /* explicit, R(z) = 1 - z (stability counter-example) */
+  ITE_HEUN = 5             /* explicit predictor-corrector, R(z) = 1 - z + z^2/2:
+                              unstable once dtau (E - s) > 2 for an eigenvalue E
+                              (the explicit counter-example of the stability
+                              section); both products formed by two-site fits */
 } ite_scheme;
 
 /* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere on the

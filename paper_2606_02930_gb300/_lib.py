@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_HERE, "libite.so")
 (ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA,
  ITE_PENDING) = range(8)
 ITE_MODEL_HEISENBERG, ITE_MODEL_ANDERSON = 0, 1
-ITE_BACKWARD_EULER, ITE_TRAPEZOID, ITE_GAUSS_LEGENDRE_2, ITE_GAUSS_LEGENDRE_3 = 0, 1, 2, 3
+(ITE_BACKWARD_EULER, ITE_TRAPEZOID, ITE_GAUSS_LEGENDRE_2, ITE_GAUSS_LEGENDRE_3, ITE_FORWARD_EULER,
+ ITE_HEUN) = range(6)
 ITE_FP64, ITE_FP64_TC = 0, 1
 ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
 STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",

@@ -17,8 +17,9 @@ from ._lib import lib, check
 BACKWARD_EULER, TRAPEZOID = L.ITE_BACKWARD_EULER, L.ITE_TRAPEZOID
 SHIFT_FIXED, SHIFT_CURRENT_ENERGY = L.ITE_SHIFT_FIXED, L.ITE_SHIFT_CURRENT_ENERGY
 GAUSS_LEGENDRE_2, GAUSS_LEGENDRE_3 = L.ITE_GAUSS_LEGENDRE_2, L.ITE_GAUSS_LEGENDRE_3
+FORWARD_EULER, HEUN = L.ITE_FORWARD_EULER, L.ITE_HEUN
 SCHEMES = {"be": BACKWARD_EULER, "tr": TRAPEZOID, "gl2": GAUSS_LEGENDRE_2,
-           "gl3": GAUSS_LEGENDRE_3}
+           "gl3": GAUSS_LEGENDRE_3, "fe": FORWARD_EULER, "heun": HEUN}
 
 
 def _scheme(s):

@@ -1280,7 +1280,8 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
       chi_max < 1 || chi_max > psi->chi_cap || o.krylov_dim < 1 || o.krylov_dim > kMaxKrylov ||
       o.sweeps < 1 || o.fit_sweeps < 1 ||
       (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID &&
-       scheme != ITE_GAUSS_LEGENDRE_2 && scheme != ITE_GAUSS_LEGENDRE_3) ||
+       scheme != ITE_GAUSS_LEGENDRE_2 && scheme != ITE_GAUSS_LEGENDRE_3 &&
+       scheme != ITE_FORWARD_EULER && scheme != ITE_HEUN) ||
       (o.precision != ITE_FP64 && o.precision != ITE_FP64_TC) || psi->N < 2)
     return fail(ctx, ITE_EINVAL, "invalid step arguments");
   CS(ensure_work(ctx, psi));
@@ -1313,7 +1314,42 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
     }
     return ITE_OK;
   };
-  if (scheme == ITE_GAUSS_LEGENDRE_2 || scheme == ITE_GAUSS_LEGENDRE_3) {
+  // right operator environments of x, for the energy below (the fits keep
+  // only overlap or mixed environments)
+  auto right_envs_of_x = [&]() -> ite_status {
+    EnvSet e = carve_envs(ctx, H, x->cap);
+    const int N = x->N;
+    CS(set_one(ctx, e.RE[N]));
+    for (int i = N - 1; i >= 1; --i)
+      CS(env_right(ctx, H, i, x->chi[i], x->chi[i], x->chi[i + 1], x->chi[i + 1], e.RE[i + 1],
+                   x->site[i], x->site[i], e.RE[i]));
+    return ITE_OK;
+  };
+  if (scheme == ITE_FORWARD_EULER || scheme == ITE_HEUN) {
+    // explicit steps: y = (I - dtau H') psi by a two-site fit (forward
+    // Euler); Heun then fits y2 = (I - dtau H') y and the corrector
+    // psi_k = psi / 2 + y2 / 2
+    const cplx a = C(1.0 + dtau * shift), b = C(-dtau);
+    ite_mps y = scheme == ITE_HEUN ? psi->work_b : x;
+    CS(mps_copy_into(ctx, psi, y));
+    CS(right_canonicalize(ctx, y));
+    for (int f = 0; f < o.fit_sweeps; ++f) CS(sweep(ctx, H, y, psi, true, a, b, chi_max, cutoff, o, st));
+    if (scheme == ITE_HEUN) {
+      if (psi->work_gl.empty()) {
+        ite_mps w = nullptr;
+        CS(mps_alloc(ctx, psi->N, psi->d, psi->chi_cap, &w));
+        psi->work_gl.push_back(w);
+      }
+      ite_mps y2 = psi->work_gl[0];
+      CS(mps_copy_into(ctx, y, y2));
+      CS(right_canonicalize(ctx, y2));
+      for (int f = 0; f < o.fit_sweeps; ++f) CS(sweep(ctx, H, y2, y, true, a, b, chi_max, cutoff, o, st));
+      CS(mps_copy_into(ctx, psi, x));
+      CS(right_canonicalize(ctx, x));
+      CS(fit_combination(ctx, x, {psi, y2}, {C(0.5), C(0.5)}, chi_max, cutoff, o.fit_sweeps, st));
+    }
+    CS(right_envs_of_x());
+  } else if (scheme == ITE_GAUSS_LEGENDRE_2 || scheme == ITE_GAUSS_LEGENDRE_3) {
     // psi_k = r_inf psi + sum_j w_j x_j, (I + c_j H') x_j = psi, c_j = -dtau / z_j,
     // w_j = -a_j / z_j, from R_q(z) = r_inf + sum_j a_j / (z - z_j)
     const int q = scheme == ITE_GAUSS_LEGENDRE_2 ? 2 : 3;
@@ -1388,13 +1424,7 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
     CS(mps_copy_into(ctx, psi, x));
     CS(right_canonicalize(ctx, x));
     CS(fit_combination(ctx, x, targets, coefs, chi_max, cutoff, o.fit_sweeps, st));
-    // right operator environments of x, for the energy below
-    EnvSet e = carve_envs(ctx, H, x->cap);
-    const int N = x->N;
-    CS(set_one(ctx, e.RE[N]));
-    for (int i = N - 1; i >= 1; --i)
-      CS(env_right(ctx, H, i, x->chi[i], x->chi[i], x->chi[i + 1], x->chi[i + 1], e.RE[i + 1],
-                   x->site[i], x->site[i], e.RE[i]));
+    CS(right_envs_of_x());
   } else {
     ite_mps bm = psi;
     double c;

@@ -78,7 +78,9 @@ size_t estimate_bytes(const ite_job* j) {
   long long elems = 4 * mps + 2 * envs + 2 * ovs + (long long)(krylov + 1) * nmax +
                     2LL * D * nmax + 6 * nmax;
   // Gauss-Legendre: q more MPS copies and overlap environments per fit target
-  const int q = j->scheme == ITE_GAUSS_LEGENDRE_2 ? 2 : j->scheme == ITE_GAUSS_LEGENDRE_3 ? 3 : 0;
+  const int q = j->scheme == ITE_GAUSS_LEGENDRE_2 ? 2
+                : j->scheme == ITE_GAUSS_LEGENDRE_3 ? 3
+                : j->scheme == ITE_HEUN ? 1 : 0;
   elems += q * mps + 2LL * (q + 1) * ovs;
   size_t bytes = (size_t)elems * 16;
   if (j->opts.precision == ITE_FP64_TC) bytes += (size_t)128 * D * nmax;   // slice scratch

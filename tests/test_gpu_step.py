@@ -348,3 +348,33 @@ def test_gauss_legendre_converged_equals_dense_propagator(api, ctx):
         for v, info in zip(dense, infos):
             assert abs(ed.energy(Hd, v) - info["energy"]) <= 1e-10 * abs(ed.energy(Hd, v))
         assert ed.infidelity(dense[-1], omps.to_dense(psi.tensors())) <= 1e-10
+
+
+@pytest.mark.parametrize("scheme", ["fe", "heun"])
+def test_explicit_steps_match_oracle_and_blow_up(api, ctx, scheme):
+    # the explicit counter-examples on a growing log grid: parity with the
+    # oracle step by step, and growth of the norm (|R| > 1) once the step
+    # passes the critical size dtau (E_max - s) = 2
+    N = 8
+    Ws = ompo.heisenberg_mpo(N)
+    Hd = ed.heisenberg_hamiltonian(N)
+    ev = np.linalg.eigvalsh(Hd)
+    H = api.mpo_create_heisenberg(ctx, N)
+    psi0 = omps.product_state(inputs.random_product_state(N, 2, 1002))
+    nodes = ogrid.geometric_grid(1e-2, 2.0, 8)
+    pairs = run_pair(api, ctx, Ws, H, psi0, nodes, scheme, 16, 0.0, shift=ev[0],
+                     opts=api.solver_opts(fit_sweeps=2), okw=dict(fit_sweeps=2))
+    grew = False
+    amp = 1.0      # bound on how much an unstable step can amplify rounding differences
+    for k, (ost, oinfo, gst, ginfo) in enumerate(pairs):
+        dt = nodes[k + 1] - nodes[k]
+        z_max = dt * (ev[-1] - ev[0])
+        amp *= max(1.0, abs(float(ed.amplification(z_max, scheme))))
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * amp * max(abs(oinfo.energy), 1.0)
+        assert infid(ost, gst) <= TOL * amp ** 2
+        assert abs(ginfo["norm_before"] - oinfo.norm_before) <= 1e-10 * amp * max(oinfo.norm_before, 1.0)
+        if z_max > 2.5:
+            grew = grew or ginfo["norm_before"] > 1.0
+        elif z_max <= 2.0:
+            assert ginfo["norm_before"] <= 1.0 + 1e-12
+    assert grew
