@@ -1,0 +1,104 @@
+"""Pins of the METTS tier of the oracle: the sequential draw against the dense
+probabilities |<sigma|psi>|^2 (exactly, and in frequency), the MPS chain
+against the same chain on dense vectors, and the chain's energy average
+against the thermal energy Tr(H e^{-beta H}) / Z."""
+import numpy as np
+
+from oracle import ed, grid, metts, mpo, mps
+from paper_2606_02930_gb300 import inputs
+
+
+def _dense_prob(psi, config, d):
+    v = mps.to_dense(psi)
+    idx = 0
+    for s in config:
+        idx = idx * d + s
+    return abs(v[idx]) ** 2 / np.vdot(v, v).real
+
+
+def test_sample_probability_is_the_born_weight():
+    rng = np.random.default_rng(3)
+    for N, d, chi in ((6, 2, 4), (4, 4, 6)):
+        psi = inputs.random_mps(N, d, chi, 11 + N)
+        for _ in range(20):
+            config, p = metts.sample(psi, rng.random(N))
+            assert abs(p - _dense_prob(psi, config, d)) < 1e-13
+
+
+def test_sample_frequencies_follow_the_distribution():
+    N, d = 4, 2
+    psi = inputs.random_mps(N, d, 4, 5)
+    v = mps.to_dense(psi)
+    want = np.abs(v) ** 2 / np.vdot(v, v).real
+    rng = np.random.default_rng(9)
+    n = 20000
+    counts = np.zeros(d ** N)
+    for _ in range(n):
+        config, _ = metts.sample(psi, rng.random(N))
+        counts[int("".join(map(str, config)), 2)] += 1
+    sigma = np.sqrt(want * (1 - want) / n)
+    assert np.all(np.abs(counts / n - want) <= 5 * sigma + 1e-12)
+
+
+def test_mps_chain_equals_dense_chain():
+    # converged steps at full bond dimension: the MPS chain draws the same
+    # configurations and measures the same energies as the dense chain
+    N, d, beta = 6, 2, 2.0
+    Ws = mpo.heisenberg_mpo(N)
+    H = ed.heisenberg_hamiltonian(N)
+    rng = np.random.default_rng(21)
+    us = rng.random((6, N))
+    config0 = [0, 1] * (N // 2)
+    nodes = grid.geometric_grid(1e-2, 0.5 * beta, 5)
+    e_mps, _, _ = metts.metts_chain(Ws, config0, d, beta, 6, us, 1e-2, 5, 8, 0.0,
+                                    local_tol=1e-13, sweeps=12, sweep_tol=1e-15,
+                                    krylov_dim=20)
+    e_dense, _ = metts.dense_metts_chain(H, d, N, config0, beta, us, nodes=nodes, scheme="be")
+    assert np.allclose(e_mps, e_dense, rtol=0, atol=1e-9)
+
+
+def _thermal(evals, beta):
+    w = np.exp(-beta * (evals - evals[0]))
+    return np.sum(evals * w) / np.sum(w)
+
+
+def _chain_mean_and_error(e, burn=100, block=100):
+    e = np.array(e[burn:])
+    blocks = e[: len(e) // block * block].reshape(-1, block).mean(axis=1)
+    return e.mean(), blocks.std(ddof=1) / np.sqrt(len(blocks))
+
+
+def test_chain_average_is_the_thermal_energy():
+    # The chain samples the thermal ensemble: its energy average approaches
+    # Tr(H e^{-beta H}) / Z (exact propagator, dense chain).  Collapsing in
+    # the computational basis only, the chain keeps the total S^z of its
+    # start state (the Heisenberg chain conserves it), so it samples that
+    # sector's ensemble; alternating z and x collapses samples all of it.
+    N, d, beta = 4, 2, 1.5
+    H = ed.heisenberg_hamiltonian(N)
+    rng = np.random.default_rng(33)
+    us = rng.random((6000, N))
+    sector = [i for i in range(d ** N) if bin(i).count("1") == N // 2]
+    e_sector = _thermal(np.linalg.eigvalsh(H[np.ix_(sector, sector)]), beta)
+    e, _ = metts.dense_metts_chain(H, d, N, [0, 1, 0, 1], beta, us)
+    m, err = _chain_mean_and_error(e)
+    assert abs(m - e_sector) < 5 * err
+    e, _ = metts.dense_metts_chain(H, d, N, [0, 1, 0, 1], beta, us, alt_basis=metts.X_BASIS)
+    m, err = _chain_mean_and_error(e)
+    assert abs(m - _thermal(np.linalg.eigvalsh(H), beta)) < 5 * err
+
+
+def test_mps_chain_with_alternating_basis_equals_dense_chain():
+    N, d, beta = 6, 2, 2.0
+    Ws = mpo.heisenberg_mpo(N)
+    H = ed.heisenberg_hamiltonian(N)
+    rng = np.random.default_rng(22)
+    us = rng.random((6, N))
+    config0 = [0, 1] * (N // 2)
+    nodes = grid.geometric_grid(1e-2, 0.5 * beta, 5)
+    e_mps, _, _ = metts.metts_chain(Ws, config0, d, beta, 6, us, 1e-2, 5, 8, 0.0,
+                                    alt_basis=metts.X_BASIS, local_tol=1e-13, sweeps=12,
+                                    sweep_tol=1e-15, krylov_dim=20)
+    e_dense, _ = metts.dense_metts_chain(H, d, N, config0, beta, us, nodes=nodes, scheme="be",
+                                         alt_basis=metts.X_BASIS)
+    assert np.allclose(e_mps, e_dense, rtol=0, atol=1e-9)
