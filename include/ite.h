@@ -198,6 +198,36 @@ ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, i
  * k = 1..n_steps, and evolution over it.  per_step[n_steps], nodes[n_steps+1]
  * may be NULL. */
 ite_status ite_grid_geometric(double tau0, double tau_max, int n_steps, double* nodes);
+/* METTS collapse (Anderson-impurity section: METTS on top of the implicit
+ * steps): draws a product configuration sigma with probability
+ * |<sigma|psi>|^2 / <psi|psi> by sequential conditional draws, site i taking
+ * the smallest state s whose cumulative conditional probability exceeds
+ * u[i] (u: N host numbers in [0, 1)).  basis (host, d x d interleaved
+ * complex unitary, may be NULL) gives the collapse basis: sigma is a product
+ * of its columns; NULL is the computational basis.  Brings psi to
+ * right-canonical form first (the state is unchanged).  config[N] (host)
+ * receives the states, *prob (may be NULL) the probability.  d <= 4. */
+ite_status ite_mps_sample(ite_ctx ctx, ite_mps psi, const double* u, const double* basis,
+                          int* config, double* prob);
+/* METTS chain (Anderson-impurity section): from the product configuration
+ * config0 (computational basis), n_samples times: evolve the product state
+ * to tau = beta/2 on the geometric grid tau0 -> beta/2 (n_steps steps,
+ * shift_mode and shift0 as ite_evolve_loggrid; a fixed shift at or below the
+ * ground energy keeps every solve positive definite, whereas the current
+ * energy of a high-energy product state with steps where dtau (s - E0) > 1
+ * makes the solves indefinite and ill-conditioned), record its energy in
+ * energies[k] and, if obs (d x d interleaved complex) is given, <obs at
+ * obs_site> in obs_values[k], then collapse it with uniforms[k N .. k N + N)
+ * into the next configuration (written to configs[k N ..], may be NULL) in
+ * the computational basis, or on even k in alt_basis when given (alternating
+ * bases let the chain leave a conserved sector of its start state).  Averages
+ * over the chain estimate thermal averages at inverse temperature beta. */
+ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, double beta, double tau0,
+                     int n_steps, int scheme, int shift_mode, double shift0, int chi_max,
+                     double cutoff, const ite_solver_opts* opts, const double* alt_basis,
+                     const double* obs,
+                     int obs_site, int n_samples, const double* uniforms, double* energies,
+                     double* obs_values, int* configs);
 /* Partial fractions of the q-stage Gauss-Legendre step (host only, q = 1..8):
  * R_q(z) = r_inf + sum_j a_j / (z - z_j); poles[2q] and residues[2q] receive
  * z_j and a_j (interleaved complex).  The step with dtau uses the shifts

@@ -65,10 +65,12 @@ X_BASIS = np.array([[1.0, 1.0], [1.0, -1.0]]) / np.sqrt(2.0)
 
 
 def metts_chain(Ws, config0, d, beta, n_samples, uniforms, tau0, n_steps, chi_max, cutoff,
-                obs=None, obs_site=0, scheme="be", alt_basis=None, **kw):
+                obs=None, obs_site=0, scheme="be", alt_basis=None, shift_mode="energy",
+                shift=0.0, **kw):
     """METTS chain from config0 (computational basis): per sample, evolve the
     product state to tau = beta/2 on the geometric grid tau0 -> beta/2
-    (n_steps steps, shift = the current energy), record the energy and
+    (n_steps steps, shift as step.evolve: the current energy by default),
+    record the energy and
     <obs at obs_site>, then draw the next configuration with uniforms[k] (N
     numbers) in the computational basis, or, on odd samples when alt_basis is
     given, in that basis.  Returns (energies, observables, configurations)."""
@@ -78,7 +80,7 @@ def metts_chain(Ws, config0, d, beta, n_samples, uniforms, tau0, n_steps, chi_ma
     energies, values, configs = [], [], []
     for k in range(n_samples):
         states, infos = stepmod.evolve(Ws, product_tensors(config, d, basis), nodes, scheme,
-                                       chi_max, cutoff, shift_mode="energy", **kw)
+                                       chi_max, cutoff, shift_mode=shift_mode, shift=shift, **kw)
         phi = states[-1]
         energies.append(infos[-1].energy)
         if obs is not None:

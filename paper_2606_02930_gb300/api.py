@@ -229,6 +229,39 @@ def evolve_panels(ctx, H, psi, tau_max, P, n, scheme, chi_max, cutoff, shift_mod
                    shift0, chi_max, cutoff, opts)
 
 
+def mps_sample(ctx, psi, u, basis=None):
+    """METTS collapse of psi with the uniforms u (N numbers in [0, 1)) in the
+    given d x d basis (None: computational).  Returns (config, probability)."""
+    u = np.ascontiguousarray(u, np.float64)
+    cfg = np.zeros(psi.N, np.int32)
+    p = C.c_double()
+    b = None if basis is None else _c128(basis)
+    check(lib.ite_mps_sample(ctx.h, psi.h, _dptr(u), None if b is None else _dptr(b.view(np.float64)),
+                             cfg.ctypes.data_as(C.POINTER(C.c_int)), C.byref(p)), ctx.h)
+    return cfg.tolist(), p.value
+
+
+def metts(ctx, H, config0, beta, tau0, n_steps, chi_max, cutoff, uniforms, scheme="be", opts=None,
+          alt_basis=None, obs=None, obs_site=0, shift_mode=SHIFT_FIXED, shift0=0.0):
+    """METTS chain (ite_metts); uniforms (n_samples, N).  Returns (energies,
+    observable values or None, configurations (n_samples, N))."""
+    u = np.ascontiguousarray(uniforms, np.float64)
+    n, N = u.shape
+    c0 = np.ascontiguousarray(config0, np.int32)
+    e = np.zeros(n)
+    vals = np.zeros(n)
+    cfgs = np.zeros((n, N), np.int32)
+    o = opts if opts is not None else solver_opts()
+    ab = None if alt_basis is None else _c128(alt_basis)
+    ob = None if obs is None else _c128(obs)
+    check(lib.ite_metts(ctx.h, H.h, c0.ctypes.data_as(C.POINTER(C.c_int)), beta, tau0, n_steps,
+                        _scheme(scheme), shift_mode, shift0, chi_max, cutoff, C.byref(o),
+                        None if ab is None else _dptr(ab.view(np.float64)),
+                        None if ob is None else _dptr(ob.view(np.float64)), obs_site, n, _dptr(u),
+                        _dptr(e), _dptr(vals), cfgs.ctypes.data_as(C.POINTER(C.c_int))), ctx.h)
+    return e, (vals if obs is not None else None), cfgs
+
+
 def gl_partial_fractions(q):
     """(poles z_j, residues a_j, r_inf) of the q-stage Gauss-Legendre step."""
     z = np.zeros(2 * q)

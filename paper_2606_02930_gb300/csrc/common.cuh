@@ -193,6 +193,13 @@ cudaError_t svd_gather_uh(const cplx* D, int len, const int* perm, const double*
 // *out = scale * sum |x|^2 (device), deterministic
 cudaError_t scaled_norm2(const cplx* x, long long n, double scale, double* out, double* partial,
                          cudaStream_t st);
+// METTS collapse, one site (metts.cu): from the unit row vector v (chl) and
+// the site tensor A (chl x d x chr), draws the site's state with the uniform
+// u in the collapse basis (d x d device matrix, NULL: computational), writes
+// it to *choice, multiplies *prob by its conditional probability and writes
+// the next unit vector to v_out (chr).  d <= 4.
+cudaError_t sample_site(const cplx* A, int chl, int d, int chr, const cplx* v, double u,
+                        const cplx* basis, cplx* v_out, int* choice, double* prob, cudaStream_t st);
 // out = A^H for a row-major m x n matrix A (out is n x m)
 cudaError_t conj_transpose(const cplx* A, int m, int n, cplx* out, cudaStream_t st);
 

@@ -1770,6 +1770,99 @@ ite_status ite_implicit_step(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, i
   return step_impl(ctx, H, psi, dtau, scheme, shift, chi_max, cutoff, o, info);
 }
 
+ite_status ite_mps_sample(ite_ctx ctx, ite_mps psi, const double* u, const double* basis,
+                          int* config, double* prob) {
+  if (!ctx || !psi || !u || !config || psi->ctx != ctx || psi->d < 1 || psi->d > 4)
+    return ITE_EINVAL;
+  for (int i = 0; i < psi->N; ++i)
+    if (!(u[i] >= 0.0 && u[i] < 1.0)) return fail(ctx, ITE_EINVAL, "uniform numbers must lie in [0, 1)");
+  const int N = psi->N, d = psi->d;
+  // the draw reads the state in right-canonical form; the state is unchanged.
+  // The gauge move writes its left factor (chl x min(chl, d chr)) and the
+  // product into the neighbouring site (chl_{i-1} d x chl_i): both fit in
+  // the largest site capacity.
+  long long site_max = 1;
+  for (int i = 0; i < N; ++i)
+    site_max = std::max(site_max, (long long)psi->cap[i] * d * psi->cap[i + 1]);
+  CS(buf_ensure(ctx, ctx->ws_left, (size_t)site_max * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_X2, (size_t)site_max * sizeof(cplx)));
+  CS(right_canonicalize(ctx, psi));
+  CS(buf_ensure(ctx, ctx->ws_X, (size_t)2 * psi->chi_cap * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_small, std::max<size_t>(small_bytes(1), (size_t)N * sizeof(int) + 256)));
+  cplx* va = P<cplx>(ctx->ws_X);
+  cplx* vb = va + psi->chi_cap;
+  int* cfg = P<int>(ctx->ws_small);
+  double* pr = ctx->dscal + 11;
+  cplx* bdev = nullptr;
+  if (basis) {
+    bdev = ctx->dcplx + 256;
+    CK(cudaMemcpyAsync(bdev, basis, sizeof(cplx) * d * d, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(pr, &one, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CS(set_one(ctx, va));
+  for (int i = 0; i < N; ++i) {
+    CK(sample_site(psi->site[i], psi->chi[i], d, psi->chi[i + 1], va, u[i], bdev, vb, cfg + i, pr,
+                   ctx->stream));
+    std::swap(va, vb);
+  }
+  CK(cudaMemcpyAsync(config, cfg, sizeof(int) * N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->d[0], pr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (prob) *prob = ctx->hr->d[0];
+  if (!(ctx->hr->d[0] > 0.0)) return fail(ctx, ITE_ESINGULAR, "zero or non-finite state in the draw");
+  return ITE_OK;
+}
+
+ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, double beta, double tau0,
+                     int n_steps, int scheme, int shift_mode, double shift0, int chi_max,
+                     double cutoff, const ite_solver_opts* opts, const double* alt_basis,
+                     const double* obs,
+                     int obs_site, int n_samples, const double* uniforms, double* energies,
+                     double* obs_values, int* configs) {
+  if (!ctx || !H || !config0 || !uniforms || !energies || n_samples < 1 || n_steps < 1 ||
+      !(tau0 > 0.0) || !(0.5 * beta > tau0) || chi_max < 1 || H->ctx != ctx || H->d > 4 ||
+      (obs && (obs_site < 0 || obs_site >= H->N || !obs_values)))
+    return ITE_EINVAL;
+  const int N = H->N, d = H->d;
+  for (int i = 0; i < N; ++i)
+    if (config0[i] < 0 || config0[i] >= d) return fail(ctx, ITE_EINVAL, "start configuration out of range");
+  ite_mps psi = nullptr;
+  CS(mps_alloc(ctx, N, d, chi_max, &psi));
+  struct Free {
+    ite_mps m;
+    ~Free() { mps_free(m); }
+  } free_psi{psi};
+  std::vector<double> A((size_t)2 * N * d), ident((size_t)2 * d * d, 0.0), out(2);
+  for (int k = 0; k < d; ++k) ident[2 * (k * d + k)] = 1.0;
+  std::vector<int> ones(N + 1, 1), config(config0, config0 + N);
+  std::vector<ite_step_info> info(n_steps);
+  const double* cur_basis = nullptr;      // the product state's basis (NULL: computational)
+  for (int k = 0; k < n_samples; ++k) {
+    // product state: site i is column config[i] of the current basis
+    for (int i = 0; i < N; ++i)
+      for (int t = 0; t < d; ++t) {
+        const int e = 2 * (t * d + config[i]);
+        A[2 * (i * d + t)] = cur_basis ? cur_basis[e] : (t == config[i] ? 1.0 : 0.0);
+        A[2 * (i * d + t) + 1] = cur_basis ? cur_basis[e + 1] : 0.0;
+      }
+    CS(ite_mps_set(ctx, psi, ones.data(), A.data()));
+    CS(ite_evolve_loggrid(ctx, H, psi, tau0, 0.5 * beta, n_steps, scheme, shift_mode, shift0,
+                          chi_max, cutoff, opts, info.data(), nullptr));
+    energies[k] = info[n_steps - 1].energy;
+    if (obs) {
+      CS(ite_correlator(ctx, psi, obs, obs_site, ident.data(), obs_site, nullptr, out.data()));
+      obs_values[k] = out[0];
+    }
+    const double* basis_k = (alt_basis && k % 2 == 0) ? alt_basis : nullptr;
+    double p = 0.0;
+    CS(ite_mps_sample(ctx, psi, uniforms + (size_t)k * N, basis_k, config.data(), &p));
+    if (configs) std::copy(config.begin(), config.end(), configs + (size_t)k * N);
+    cur_basis = basis_k;
+  }
+  return ITE_OK;
+}
+
 ite_status ite_gl_partial_fractions(int q, double* poles, double* residues, double* r_inf) {
   if (!poles || !residues || !r_inf) return ITE_EINVAL;
   std::vector<Cd> z, a;
