@@ -211,21 +211,23 @@ ite_status ite_mps_sample(ite_ctx ctx, ite_mps psi, const double* u, const doubl
                           int* config, double* prob);
 /* METTS chain (Anderson-impurity section): from the product configuration
  * config0 (computational basis), n_samples times: evolve the product state
- * to tau = beta/2 on the geometric grid tau0 -> beta/2 (n_steps steps,
- * shift_mode and shift0 as ite_evolve_loggrid; a fixed shift at or below the
- * ground energy keeps every solve positive definite, whereas the current
- * energy of a high-energy product state with steps where dtau (s - E0) > 1
- * makes the solves indefinite and ill-conditioned), record its energy in
- * energies[k] and, if obs (d x d interleaved complex) is given, <obs at
- * obs_site> in obs_values[k], then collapse it with uniforms[k N .. k N + N)
- * into the next configuration (written to configs[k N ..], may be NULL) in
- * the computational basis, or on even k in alt_basis when given (alternating
- * bases let the chain leave a conserved sector of its start state).  Averages
- * over the chain estimate thermal averages at inverse temperature beta. */
-ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, double beta, double tau0,
-                     int n_steps, int scheme, int shift_mode, double shift0, int chi_max,
-                     double cutoff, const ite_solver_opts* opts, const double* alt_basis,
-                     const double* obs,
+ * over the tau grid nodes[0..n_steps] (host; nodes[0] = 0, strictly
+ * increasing; nodes[n_steps] = beta/2), with scheme, shift_mode and shift0
+ * as ite_evolve_loggrid, record its energy in energies[k] and, if obs (d x d
+ * interleaved complex) is given, <obs at obs_site> in obs_values[k], then
+ * collapse it with uniforms[k N .. k N + N) into the next configuration
+ * (written to configs[k N ..], may be NULL) in the computational basis, or on
+ * even k in alt_basis when given (alternating bases let the chain leave a
+ * conserved sector of its start state).  Averages over the chain estimate
+ * thermal averages at inverse temperature beta.  The paper's grid is the
+ * panel grid (ite_grid_panels: first panel about [0, 0.01], 4 steps per
+ * panel) with the trapezoid rule and the current-energy shift; its steps stay
+ * small against tau, so dtau (s - E0) stays below 1 and every solve is well
+ * conditioned.  A few long steps from a high-energy product state with the
+ * current-energy shift make (I + c (H - s)) indefinite instead. */
+ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, const double* nodes, int n_steps,
+                     int scheme, int shift_mode, double shift0, int chi_max, double cutoff,
+                     const ite_solver_opts* opts, const double* alt_basis, const double* obs,
                      int obs_site, int n_samples, const double* uniforms, double* energies,
                      double* obs_values, int* configs);
 /* Partial fractions of the q-stage Gauss-Legendre step (host only, q = 1..8):

@@ -64,18 +64,15 @@ def product_tensors(config, d, basis=None):
 X_BASIS = np.array([[1.0, 1.0], [1.0, -1.0]]) / np.sqrt(2.0)
 
 
-def metts_chain(Ws, config0, d, beta, n_samples, uniforms, tau0, n_steps, chi_max, cutoff,
-                obs=None, obs_site=0, scheme="be", alt_basis=None, shift_mode="energy",
-                shift=0.0, **kw):
+def metts_chain(Ws, config0, d, nodes, n_samples, uniforms, chi_max, cutoff, obs=None,
+                obs_site=0, scheme="be", alt_basis=None, shift_mode="energy", shift=0.0, **kw):
     """METTS chain from config0 (computational basis): per sample, evolve the
-    product state to tau = beta/2 on the geometric grid tau0 -> beta/2
-    (n_steps steps, shift as step.evolve: the current energy by default),
-    record the energy and
+    product state over the tau grid `nodes` (0 -> beta/2; shift as
+    step.evolve, the current energy by default), record the energy and
     <obs at obs_site>, then draw the next configuration with uniforms[k] (N
-    numbers) in the computational basis, or, on odd samples when alt_basis is
-    given, in that basis.  Returns (energies, observables, configurations)."""
-    from . import grid
-    nodes = grid.geometric_grid(tau0, 0.5 * beta, n_steps)
+    numbers) in the computational basis, or, after even samples when
+    alt_basis is given, in that basis.  Returns (energies, observables,
+    configurations)."""
     config, basis = list(config0), None
     energies, values, configs = [], [], []
     for k in range(n_samples):

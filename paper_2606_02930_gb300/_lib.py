@@ -105,7 +105,7 @@ SIGNATURES = {
     "ite_grid_geometric": (_i, [_d, _d, _i, _pd]),
     "ite_gl_partial_fractions": (_i, [_i, _pd, _pd, _pd]),
     "ite_mps_sample": (_i, [_vp, _vp, _pd, _pd, _pi, _pd]),
-    "ite_metts": (_i, [_vp, _vp, _pi, _d, _d, _i, _i, _i, _d, _i, _d, C.POINTER(ite_solver_opts),
+    "ite_metts": (_i, [_vp, _vp, _pi, _pd, _i, _i, _i, _d, _i, _d, C.POINTER(ite_solver_opts),
                        _pd, _pd, _i, _i, _pd, _pd, _pd, _pi]),
     "ite_evolve_loggrid": (_i, [_vp, _vp, _vp, _d, _d, _i, _i, _i, _d, _i, _d,
                                 C.POINTER(ite_solver_opts), C.POINTER(ite_step_info), _pd]),

@@ -241,10 +241,13 @@ def mps_sample(ctx, psi, u, basis=None):
     return cfg.tolist(), p.value
 
 
-def metts(ctx, H, config0, beta, tau0, n_steps, chi_max, cutoff, uniforms, scheme="be", opts=None,
-          alt_basis=None, obs=None, obs_site=0, shift_mode=SHIFT_FIXED, shift0=0.0):
-    """METTS chain (ite_metts); uniforms (n_samples, N).  Returns (energies,
-    observable values or None, configurations (n_samples, N))."""
+def metts(ctx, H, config0, nodes, chi_max, cutoff, uniforms, scheme="tr", opts=None,
+          alt_basis=None, obs=None, obs_site=0, shift_mode=SHIFT_CURRENT_ENERGY, shift0=0.0):
+    """METTS chain (ite_metts) over the tau grid `nodes` (0 -> beta/2);
+    uniforms (n_samples, N).  The defaults are the paper's: trapezoid rule,
+    shift = the current energy.  Returns (energies, observable values or None,
+    configurations (n_samples, N))."""
+    g = np.ascontiguousarray(nodes, np.float64)
     u = np.ascontiguousarray(uniforms, np.float64)
     n, N = u.shape
     c0 = np.ascontiguousarray(config0, np.int32)
@@ -254,7 +257,7 @@ def metts(ctx, H, config0, beta, tau0, n_steps, chi_max, cutoff, uniforms, schem
     o = opts if opts is not None else solver_opts()
     ab = None if alt_basis is None else _c128(alt_basis)
     ob = None if obs is None else _c128(obs)
-    check(lib.ite_metts(ctx.h, H.h, c0.ctypes.data_as(C.POINTER(C.c_int)), beta, tau0, n_steps,
+    check(lib.ite_metts(ctx.h, H.h, c0.ctypes.data_as(C.POINTER(C.c_int)), _dptr(g), len(g) - 1,
                         _scheme(scheme), shift_mode, shift0, chi_max, cutoff, C.byref(o),
                         None if ab is None else _dptr(ab.view(np.float64)),
                         None if ob is None else _dptr(ob.view(np.float64)), obs_site, n, _dptr(u),

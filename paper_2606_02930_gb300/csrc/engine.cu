@@ -1814,16 +1814,23 @@ ite_status ite_mps_sample(ite_ctx ctx, ite_mps psi, const double* u, const doubl
   return ITE_OK;
 }
 
-ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, double beta, double tau0,
-                     int n_steps, int scheme, int shift_mode, double shift0, int chi_max,
-                     double cutoff, const ite_solver_opts* opts, const double* alt_basis,
-                     const double* obs,
+ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, const double* nodes, int n_steps,
+                     int scheme, int shift_mode, double shift0, int chi_max, double cutoff,
+                     const ite_solver_opts* opts, const double* alt_basis, const double* obs,
                      int obs_site, int n_samples, const double* uniforms, double* energies,
                      double* obs_values, int* configs) {
-  if (!ctx || !H || !config0 || !uniforms || !energies || n_samples < 1 || n_steps < 1 ||
-      !(tau0 > 0.0) || !(0.5 * beta > tau0) || chi_max < 1 || H->ctx != ctx || H->d > 4 ||
+  if (!ctx || !H || !config0 || !nodes || !uniforms || !energies || n_samples < 1 || n_steps < 1 ||
+      chi_max < 1 || H->ctx != ctx || H->d > 4 ||
       (obs && (obs_site < 0 || obs_site >= H->N || !obs_values)))
     return ITE_EINVAL;
+  std::vector<double> grid(nodes, nodes + n_steps + 1);
+  if (grid[0] != 0.0) return fail(ctx, ITE_EINVAL, "the tau grid must start at 0");
+  for (int k = 1; k <= n_steps; ++k)
+    if (!(grid[k] > grid[k - 1]) || !std::isfinite(grid[k]))
+      return fail(ctx, ITE_EINVAL, "the tau grid must increase strictly");
+  ite_solver_opts o;
+  ite_solver_opts_default(&o);
+  if (opts) o = *opts;
   const int N = H->N, d = H->d;
   for (int i = 0; i < N; ++i)
     if (config0[i] < 0 || config0[i] >= d) return fail(ctx, ITE_EINVAL, "start configuration out of range");
@@ -1847,8 +1854,7 @@ ite_status ite_metts(ite_ctx ctx, ite_mpo H, const int* config0, double beta, do
         A[2 * (i * d + t) + 1] = cur_basis ? cur_basis[e + 1] : 0.0;
       }
     CS(ite_mps_set(ctx, psi, ones.data(), A.data()));
-    CS(ite_evolve_loggrid(ctx, H, psi, tau0, 0.5 * beta, n_steps, scheme, shift_mode, shift0,
-                          chi_max, cutoff, opts, info.data(), nullptr));
+    CS(evolve_impl(ctx, H, psi, grid, scheme, shift_mode, shift0, chi_max, cutoff, o, info.data()));
     energies[k] = info[n_steps - 1].energy;
     if (obs) {
       CS(ite_correlator(ctx, psi, obs, obs_site, ident.data(), obs_site, nullptr, out.data()));
