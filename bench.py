@@ -67,10 +67,14 @@ def parse():
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
     ap.add_argument("--scheme", choices=["be", "tr", "gl2", "gl3"], default="be",
                     help="time stepper of the chain workload (the headline runs backward Euler)")
-    ap.add_argument("--workload", choices=["chain", "batch"], default="chain",
-                    help="batch: a bounded sample of the batched workload served side by side")
+    ap.add_argument("--workload", choices=["chain", "batch", "chi_study"], default="chain",
+                    help="batch: a bounded sample of the batched workload served side by side; "
+                         "chi_study: bond-dimension growth and step cost of an evolution")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
     ap.add_argument("--slots", type=int, default=4, help="concurrent jobs in the batch sample")
+    ap.add_argument("--study-n", type=int, default=100, help="chain length of the chi study")
+    ap.add_argument("--study-m", type=int, default=8, help="chi study runs to tau_max = 2^m")
+    ap.add_argument("--study-chi", type=int, default=128, help="bond-dimension cap of the chi study")
     return ap.parse_args()
 
 
@@ -380,6 +384,77 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_chi_study(args):
+    """Bond-dimension growth and step cost of the paper's Heisenberg run (App.
+    C): XXX chain of --study-n spins (J = 1, open ends) from the Neel state,
+    trapezoid rule on the panel grid (first panel [0, 2^-5], 4 steps per
+    panel) up to tau_max = 2^--study-m, discarded weight 1e-10 per bond, chi
+    capped at --study-chi, shift = the current energy, tensor-core mode.  Every
+    step is one synchronous library call, timed by the host clock around it.
+    Fits the step cost t(chi) = a chi^p and the growth chi(tau) (logarithmic
+    and power laws), and sets the measured cost of the logarithmic grid
+    against uniform steps of 0.1 (the paper's TDVP step) predicted from the
+    fit on the same evolution.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    from paper_2606_02930_gb300 import api, costmodel
+    torch.cuda.init()
+    N, m, cap = args.study_n, args.study_m, args.study_chi
+    opts = api.solver_opts(precision=args.precision)
+    ctx = api.ctx_create(0)
+    neel = np.zeros((N, 2))
+    neel[np.arange(N), np.arange(N) % 2] = 1.0
+    # warm-up on a short chain: kernel images, caches
+    Hw = api.mpo_create_heisenberg(ctx, 8)
+    pw = api.mps_create_product(ctx, neel[:8], 8)
+    for dt in (0.01, 0.02, 0.04):
+        api.implicit_step(ctx, Hw, pw, dt, "tr", 0.0, 8, CUTOFF, opts)
+    H = api.mpo_create_heisenberg(ctx, N)
+    psi = api.mps_create_product(ctx, neel, cap)
+    P = m + 5 + 1
+    nodes = api.grid_panels(2.0 ** m, P, 4)
+    s = api.energy(ctx, H, psi)
+    taus, chis, secs, energies = [], [], [], []
+    for k in range(1, len(nodes)):
+        t0 = time.perf_counter()
+        info = api.implicit_step(ctx, H, psi, nodes[k] - nodes[k - 1], "tr", s, cap, CUTOFF, opts)
+        secs.append(time.perf_counter() - t0)
+        s = info["energy"]
+        taus.append(float(nodes[k]))
+        chis.append(int(info["max_chi"]))
+        energies.append(float(s))
+    taus, chis_a, secs_a = np.array(taus), np.array(chis), np.array(secs)
+    big = chis_a >= 16
+    a, p = costmodel.fit_power_law(chis_a[big], secs_a[big])
+    grow = chis_a < cap
+    growth = costmodel.fit_growth(taus[grow & (taus >= 0.1)], chis_a[grow & (taus >= 0.1)])
+    t_fit = lambda c: a * np.maximum(c, 16.0) ** p
+    ratios = {}
+    for j in range(0, m + 1):
+        tmax = 2.0 ** j
+        c_log = float(np.sum(secs_a[taus <= tmax + 1e-12]))
+        c_uni = costmodel.uniform_cost(tmax, 0.1, nodes, chis, t_fit)
+        ratios[str(int(tmax))] = {"log_grid_s": c_log, "uniform_0.1_s": c_uni,
+                                  "ratio": c_uni / c_log}
+    at_cap = secs_a[chis_a == cap]
+    out = {"workload": "chi_study", "metric": "chi(tau), step cost t(chi), App. C cost sums",
+           "config": {"model": f"Heisenberg XXX N={N} J=1 OBC, Neel start", "scheme": "trapezoid",
+                      "grid": f"panels, first [0, 2^-5], 4 steps/panel, tau_max 2^{m}",
+                      "cutoff": CUTOFF, "chi_cap": cap, "shift": "current energy",
+                      "precision": args.precision},
+           "steps": len(taus), "total_s": float(np.sum(secs_a)),
+           "step_cost_fit": {"a": a, "p": p, "over": "steps with chi >= 16"},
+           "growth_fit": growth,
+           "cost_vs_tau_max": ratios,
+           "at_cap": ({"steps": int(at_cap.size), "mean_s": float(at_cap.mean()),
+                       "min_s": float(at_cap.min()), "max_s": float(at_cap.max()),
+                       "dtau_range": [float(np.min(np.diff(nodes)[chis_a == cap])),
+                                      float(np.max(np.diff(nodes)[chis_a == cap]))]}
+                      if at_cap.size else None),
+           "trace": {"tau": taus.tolist(), "chi": chis, "s": [round(x, 4) for x in secs],
+                     "energy": energies}}
+    print(json.dumps(out), flush=True)
+
+
 def run_only(args):
     """Time one kernel-level entry point at the workload's bulk shape: the
     two-site H_eff (chi = 256, d = 2, D = 5) or the truncated SVD split of a
@@ -429,6 +504,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "chi_study":
+        run_chi_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
