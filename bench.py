@@ -67,9 +67,11 @@ def parse():
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
     ap.add_argument("--scheme", choices=["be", "tr", "gl2", "gl3"], default="be",
                     help="time stepper of the chain workload (the headline runs backward Euler)")
-    ap.add_argument("--workload", choices=["chain", "batch", "chi_study"], default="chain",
+    ap.add_argument("--workload", choices=["chain", "batch", "chi_study", "metts"],
+                    default="chain",
                     help="batch: a bounded sample of the batched workload served side by side; "
-                         "chi_study: bond-dimension growth and step cost of an evolution")
+                         "chi_study: bond-dimension growth and step cost of an evolution; "
+                         "metts: independent METTS chains served side by side")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
     ap.add_argument("--slots", type=int, default=4, help="concurrent jobs in the batch sample")
     ap.add_argument("--study-n", type=int, default=100, help="chain length of the chi study")
@@ -384,6 +386,53 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_metts(args):
+    """Independent METTS chains of the impurity model served side by side: the
+    paper's METTS setting (trapezoid rule, panel grid from [0, 0.01] with 4
+    steps per panel, shift = the current energy, all non-zero singular values
+    kept below the cap, double occupancy of the impurity measured) on a
+    flat-band bath of 9 sites (Gamma = 0.05, U = 0.3), chi cap 64, beta = 16,
+    --jobs chains of 2 samples each from seeded configurations (seed 5000),
+    tensor-core mode.  Runs the chains one at a time (1 slot) and side by side
+    (--slots) and prints one JSON line (not the benchmark line): METTS
+    samples/s, tau-steps/s and p50/p99 chain latency."""
+    import torch
+    from paper_2606_02930_gb300 import api, inputs
+    torch.cuda.init()
+    n_bath, beta, samples = 9, 16.0, 2
+    eps, V = inputs.flat_band_bath(n_bath)
+    P = int(np.ceil(np.log2(0.5 * beta / 0.01))) + 1
+    docc = np.diag([0.0, 0.0, 0.0, 1.0]).astype(complex)
+    rng = np.random.default_rng(5000)
+    cfgs = rng.integers(0, 4, size=(args.jobs, n_bath + 1))
+    us = rng.random((args.jobs, samples, n_bath + 1))
+    opts = api.solver_opts(precision=args.precision)
+
+    def make():
+        return [api.MettsJob("anderson", n_bath, cfgs[i], 64, 0.0, 0.5 * beta, P, 4, us[i],
+                             obs=docc, obs_site=0, U=0.3, eps_d=-0.15, eps=eps, V=V, opts=opts)
+                for i in range(args.jobs)]
+
+    api.evolve_batch(make()[:2], n_slots=2)          # warm-up: caches, kernel images
+    out = {"workload": "metts", "metric": "METTS samples/s and p50/p99 chain latency, served",
+           "chains": int(args.jobs), "samples_per_chain": samples, "steps_per_sample": 4 * P,
+           "precision": args.precision,
+           "config": {"model": "Anderson impurity, flat-band bath of 9 sites, U=0.3, eps_d=-U/2",
+                      "beta": beta, "chi_cap": 64, "cutoff": 0.0, "scheme": "trapezoid",
+                      "grid": f"panels from [0, {0.5 * beta / 2 ** (P - 1):.4g}], 4 steps/panel",
+                      "start": "seeded configurations (seed 5000)"}}
+    for slots in (1, args.slots):
+        res, st = api.evolve_batch(make(), n_slots=slots)
+        assert all(r["status"] == 0 for r in res)
+        out[f"slots{slots}"] = {"samples_per_s": args.jobs * samples / (st["wall_ms"] * 1e-3),
+                                **{k: st[k] for k in ("tau_steps_per_s", "p50_latency_ms",
+                                                      "p99_latency_ms", "wall_ms",
+                                                      "peak_running")}}
+    out["speedup"] = (out[f"slots{args.slots}"]["samples_per_s"]
+                      / out["slots1"]["samples_per_s"])
+    print(json.dumps(out), flush=True)
+
+
 def run_chi_study(args):
     """Bond-dimension growth and step cost of the paper's Heisenberg run (App.
     C): XXX chain of --study-n spins (J = 1, open ends) from the Neel state,
@@ -507,6 +556,9 @@ def main():
         return
     if args.workload == "chi_study":
         run_chi_study(args)
+        return
+    if args.workload == "metts":
+        run_metts(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -20,8 +20,9 @@
  *   - Memory: workers allocate stream-ordered (cudaMallocAsync on their own
  *     stream), so no job's allocation waits for the whole device, and release
  *     a job's workspaces when it ends.
- *   - Each job is the same computation as ite_evolve_loggrid on a product
- *     start state: its results do not depend on what else runs (the kernels
+ *   - Each job is the same computation as ite_evolve_loggrid (or
+ *     ite_evolve_panels) on a product start state, or as ite_metts for a
+ *     METTS job: its results do not depend on what else runs (the kernels
  *     are deterministic and jobs share no data).
  *   - Host arrays in ite_job are copied by ite_server_submit; the output
  *     buffers (energies, state) must stay valid until the job has finished.
@@ -38,9 +39,22 @@ extern "C" {
 #endif
 
 typedef enum { ITE_MODEL_HEISENBERG = 0, ITE_MODEL_ANDERSON = 1 } ite_model;
+typedef enum { ITE_JOB_GRID_GEOMETRIC = 0, ITE_JOB_GRID_PANELS = 1 } ite_job_grid;
 
-/* One evolution: model, product start state, truncation and the geometric
- * tau grid (tau0 -> tau_max in n_steps steps, as ite_evolve_loggrid). */
+/* One job: model, truncation, tau grid, and either one evolution of a product
+ * start state or a METTS chain.
+ *   grid ITE_JOB_GRID_GEOMETRIC: tau0 -> tau_max in n_steps steps (as
+ *     ite_evolve_loggrid); ITE_JOB_GRID_PANELS: `panels` panels of n_steps
+ *     uniform steps each up to tau_max (as ite_grid_panels; tau0 unused).
+ *   metts_samples == 0: one evolution of site_vecs over the grid.
+ *   metts_samples > 0: a METTS chain (as ite_metts) from metts_config0 over
+ *     the grid (tau_max = beta/2) with metts_uniforms[samples][N], the optional
+ *     collapse basis and observable (d x d interleaved complex), all copied at
+ *     submit; writes metts_energies[samples], metts_obs_values[samples] (when
+ *     metts_obs is given) and metts_configs[samples][N] (may be NULL).
+ *     site_vecs, energies and state are not used.
+ * A zero-initialised tail (grid, panels, metts_*) gives one evolution on the
+ * geometric grid. */
 typedef struct {
   int model;                  /* ite_model                                          */
   int n;                      /* Heisenberg: sites N; Anderson: bath sites (N = n+1) */
@@ -61,8 +75,21 @@ typedef struct {
   double* state;              /* optional out: final tensors as ite_mps_get writes  */
   size_t state_cap;           /* capacity of state in doubles                       */
   int* state_chi;             /* optional out [N+1]: final bond dimensions          */
+  int grid;                   /* ite_job_grid                                       */
+  int panels;                 /* panel count for ITE_JOB_GRID_PANELS                */
+  int metts_samples;          /* 0: one evolution; > 0: METTS chain of this length  */
+  const int* metts_config0;   /* [N] start configuration (copied)                   */
+  const double* metts_uniforms;  /* [samples][N] in [0, 1) (copied)                 */
+  const double* metts_alt_basis; /* optional d x d collapse basis (copied)          */
+  const double* metts_obs;    /* optional d x d observable (copied)                 */
+  int metts_obs_site;
+  double* metts_energies;     /* out [samples]                                      */
+  double* metts_obs_values;   /* out [samples], needed with metts_obs               */
+  int* metts_configs;         /* optional out [samples][N]                          */
 } ite_job;
 
+/* For a METTS job, steps_done counts the steps of all samples, energy is the
+ * last sample's, and max_discarded_weight and max_chi are 0. */
 typedef struct {
   int status;                 /* ite_status of the evolution                         */
   int steps_done;

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libite.so")
 (ITE_OK, ITE_EINVAL, ITE_ENOMEM, ITE_ESINGULAR, ITE_ENOTCONV, ITE_ETIMEOUT, ITE_ECUDA,
  ITE_PENDING) = range(8)
 ITE_MODEL_HEISENBERG, ITE_MODEL_ANDERSON = 0, 1
+ITE_JOB_GRID_GEOMETRIC, ITE_JOB_GRID_PANELS = 0, 1
 (ITE_BACKWARD_EULER, ITE_TRAPEZOID, ITE_GAUSS_LEGENDRE_2, ITE_GAUSS_LEGENDRE_3, ITE_FORWARD_EULER,
  ITE_HEUN) = range(6)
 ITE_FP64, ITE_FP64_TC = 0, 1
@@ -45,7 +46,12 @@ class ite_job(C.Structure):
                 ("shift_mode", C.c_int), ("shift0", C.c_double), ("tau0", C.c_double),
                 ("tau_max", C.c_double), ("n_steps", C.c_int), ("opts", ite_solver_opts),
                 ("energies", C.POINTER(C.c_double)), ("state", C.POINTER(C.c_double)),
-                ("state_cap", C.c_size_t), ("state_chi", C.POINTER(C.c_int))]
+                ("state_cap", C.c_size_t), ("state_chi", C.POINTER(C.c_int)),
+                ("grid", C.c_int), ("panels", C.c_int), ("metts_samples", C.c_int),
+                ("metts_config0", C.POINTER(C.c_int)), ("metts_uniforms", C.POINTER(C.c_double)),
+                ("metts_alt_basis", C.POINTER(C.c_double)), ("metts_obs", C.POINTER(C.c_double)),
+                ("metts_obs_site", C.c_int), ("metts_energies", C.POINTER(C.c_double)),
+                ("metts_obs_values", C.POINTER(C.c_double)), ("metts_configs", C.POINTER(C.c_int))]
 
 
 class ite_job_result(C.Structure):

@@ -432,31 +432,42 @@ def _bond_caps(N, d, chi_max):
     return caps
 
 
+def _job_base(holder, model, n, chi_max, cutoff, tau0, tau_max, n_steps, scheme, shift_mode,
+              shift0, J, Jz, U, eps_d, eps, V, opts, panels):
+    j = L.ite_job()
+    j.model = MODELS[model] if isinstance(model, str) else int(model)
+    j.n = n
+    j.J, j.Jz = J, (J if Jz is None else Jz)
+    j.U, j.eps_d = U, eps_d
+    if eps is not None:
+        holder.eps = np.ascontiguousarray(eps, dtype=np.float64)
+        holder.V = np.ascontiguousarray(V, dtype=np.float64)
+        j.eps, j.V = _dptr(holder.eps), _dptr(holder.V)
+    j.chi_max, j.cutoff = chi_max, cutoff
+    j.scheme, j.shift_mode, j.shift0 = _scheme(scheme), shift_mode, shift0
+    j.tau0, j.tau_max, j.n_steps = tau0, tau_max, n_steps
+    j.grid = L.ITE_JOB_GRID_PANELS if panels else L.ITE_JOB_GRID_GEOMETRIC
+    j.panels = panels
+    j.opts = opts if opts is not None else solver_opts()
+    return j
+
+
 class Job:
     """One evolution for the server (ite_job): model, product start state
-    site_vecs (N, d), truncation, geometric grid.  The arrays referenced by the
-    C struct live as long as this object."""
+    site_vecs (N, d), truncation, and the geometric grid tau0 -> tau_max in
+    n_steps steps, or with panels > 0 the panel grid (panels panels of n_steps
+    steps up to tau_max; tau0 unused).  The arrays referenced by the C struct
+    live as long as this object."""
 
     def __init__(self, model, n, site_vecs, chi_max, cutoff, tau0, tau_max, n_steps, scheme="be",
                  shift_mode=SHIFT_CURRENT_ENERGY, shift0=0.0, J=1.0, Jz=None, U=0.0, eps_d=0.0,
-                 eps=None, V=None, opts=None, want_state=False):
-        j = L.ite_job()
-        j.model = MODELS[model] if isinstance(model, str) else int(model)
-        j.n = n
-        j.J, j.Jz = J, (J if Jz is None else Jz)
-        j.U, j.eps_d = U, eps_d
+                 eps=None, V=None, opts=None, want_state=False, panels=0):
+        j = _job_base(self, model, n, chi_max, cutoff, tau0, tau_max, n_steps, scheme, shift_mode,
+                      shift0, J, Jz, U, eps_d, eps, V, opts, panels)
         self.sv = _c128(site_vecs)
         self.N, self.d = self.sv.shape
         j.site_vecs = _dptr(self.sv.view(np.float64))
-        if eps is not None:
-            self.eps = np.ascontiguousarray(eps, dtype=np.float64)
-            self.V = np.ascontiguousarray(V, dtype=np.float64)
-            j.eps, j.V = _dptr(self.eps), _dptr(self.V)
-        j.chi_max, j.cutoff = chi_max, cutoff
-        j.scheme, j.shift_mode, j.shift0 = _scheme(scheme), shift_mode, shift0
-        j.tau0, j.tau_max, j.n_steps = tau0, tau_max, n_steps
-        j.opts = opts if opts is not None else solver_opts()
-        self.energies = np.zeros(n_steps)
+        self.energies = np.zeros(n_steps * (panels if panels else 1))
         j.energies = _dptr(self.energies)
         if want_state:
             caps = _bond_caps(self.N, self.d, chi_max)
@@ -482,6 +493,44 @@ class Job:
                                                 self.state_chi[i + 1]).copy())
             pos += cnt
         return out
+
+
+class MettsJob:
+    """A METTS chain for the server (ite_job with metts_samples > 0): from
+    config0 over the panel grid (panels panels of steps_per_panel steps up to
+    tau_max = beta/2), one draw per row of uniforms (samples, N).  Defaults are
+    the paper's: trapezoid rule, shift = the current energy.  After the job:
+    energies, obs_values (with obs) and configs (samples, N)."""
+
+    def __init__(self, model, n, config0, chi_max, cutoff, tau_max, panels, steps_per_panel,
+                 uniforms, scheme="tr", shift_mode=SHIFT_CURRENT_ENERGY, shift0=0.0,
+                 alt_basis=None, obs=None, obs_site=0, J=1.0, Jz=None, U=0.0, eps_d=0.0, eps=None,
+                 V=None, opts=None):
+        j = _job_base(self, model, n, chi_max, cutoff, 0.0, tau_max, steps_per_panel, scheme,
+                      shift_mode, shift0, J, Jz, U, eps_d, eps, V, opts, panels)
+        self.u = np.ascontiguousarray(uniforms, np.float64)
+        samples, self.N = self.u.shape
+        self.config0 = np.ascontiguousarray(config0, np.int32)
+        self.energies = np.zeros(samples)
+        self.obs_values = np.zeros(samples)
+        self.configs = np.zeros((samples, self.N), np.int32)
+        j.metts_samples = samples
+        j.metts_config0 = self.config0.ctypes.data_as(C.POINTER(C.c_int))
+        j.metts_uniforms = _dptr(self.u)
+        if alt_basis is not None:
+            self.ab = _c128(alt_basis)
+            j.metts_alt_basis = _dptr(self.ab.view(np.float64))
+        if obs is not None:
+            self.ob = _c128(obs)
+            j.metts_obs = _dptr(self.ob.view(np.float64))
+            j.metts_obs_values = _dptr(self.obs_values)
+        j.metts_obs_site = obs_site
+        j.metts_energies = _dptr(self.energies)
+        j.metts_configs = self.configs.ctypes.data_as(C.POINTER(C.c_int))
+        self.c = j
+
+    def device_bytes(self):
+        return int(lib.ite_job_device_bytes(C.byref(self.c)))
 
 
 class Server:

@@ -44,17 +44,40 @@ std::vector<long long> bond_caps(int N, int d, int chi_max) {
   return cap;
 }
 
-bool job_valid(const ite_job* j) {
-  if (!j || j->n < 1 || j->chi_max < 1 || !(j->cutoff >= 0.0) || j->n_steps < 1 ||
-      !(j->tau0 > 0.0) || !(j->tau_max > j->tau0) || !j->site_vecs)
-    return false;
-  if (j->model == ITE_MODEL_HEISENBERG) return j->n >= 2;
-  if (j->model == ITE_MODEL_ANDERSON) return j->eps && j->V;
-  return false;
-}
-
 int job_sites(const ite_job* j) { return j->model == ITE_MODEL_HEISENBERG ? j->n : j->n + 1; }
 int job_d(const ite_job* j) { return j->model == ITE_MODEL_HEISENBERG ? 2 : 4; }
+
+bool job_valid(const ite_job* j) {
+  if (!j || j->n < 1 || j->chi_max < 1 || !(j->cutoff >= 0.0) || j->n_steps < 1) return false;
+  if (j->grid == ITE_JOB_GRID_GEOMETRIC) {
+    if (!(j->tau0 > 0.0) || !(j->tau_max > j->tau0)) return false;
+  } else if (j->grid == ITE_JOB_GRID_PANELS) {
+    if (j->panels < 1 || j->panels > 1000 || !(j->tau_max > 0.0)) return false;
+  } else {
+    return false;
+  }
+  if (j->model == ITE_MODEL_HEISENBERG) {
+    if (j->n < 2) return false;
+  } else if (j->model == ITE_MODEL_ANDERSON) {
+    if (!j->eps || !j->V) return false;
+  } else {
+    return false;
+  }
+  if (j->metts_samples < 0) return false;
+  if (j->metts_samples == 0) return j->site_vecs != nullptr;
+  const int N = job_sites(j), d = job_d(j);
+  if (!j->metts_config0 || !j->metts_uniforms || !j->metts_energies) return false;
+  if (j->metts_obs && (!j->metts_obs_values || j->metts_obs_site < 0 || j->metts_obs_site >= N))
+    return false;
+  for (int i = 0; i < N; ++i)
+    if (j->metts_config0[i] < 0 || j->metts_config0[i] >= d) return false;
+  return true;
+}
+
+// steps of one evolution on the job's grid
+int job_steps(const ite_job* j) {
+  return j->grid == ITE_JOB_GRID_PANELS ? j->panels * j->n_steps : j->n_steps;
+}
 int job_D(const ite_job* j) { return j->model == ITE_MODEL_HEISENBERG ? 5 : 6; }
 
 size_t estimate_bytes(const ite_job* j) {
@@ -90,7 +113,8 @@ size_t estimate_bytes(const ite_job* j) {
 struct Job {
   long long id = 0;
   ite_job spec{};
-  std::vector<double> eps, V, site_vecs;
+  std::vector<double> eps, V, site_vecs, uniforms, alt_basis, obs;
+  std::vector<int> config0;
   size_t bytes = 0;
   Clock::time_point t_submit, t_start, t_end;
   bool done = false;
@@ -133,40 +157,60 @@ struct ite_server_s {
 
 void ite_server_s::run_job(ite_ctx ctx, cudaStream_t st, Job& job) {
   ite_job& j = job.spec;
-  const int N = job_sites(&j), d = job_d(&j);
+  const int N = job_sites(&j), d = job_d(&j), K = job_steps(&j);
   ite_mpo H = nullptr;
   ite_mps psi = nullptr;
   ite_status s = ITE_OK;
+  ite_job_result& r = job.result;
+  r.steps_done = 0;
+  r.max_discarded_weight = 0.0;
+  r.max_chi = 0;
   if (j.model == ITE_MODEL_HEISENBERG)
     s = ite_mpo_create_heisenberg(ctx, N, j.J, j.Jz, &H);
   else
     s = ite_mpo_create_anderson(ctx, j.n, job.eps.data(), job.V.data(), j.U, j.eps_d, &H);
-  if (s == ITE_OK) s = ite_mps_create_product(ctx, N, d, job.site_vecs.data(), j.chi_max, &psi);
-  std::vector<ite_step_info> info(j.n_steps);
-  if (s == ITE_OK)
-    s = ite_evolve_loggrid(ctx, H, psi, j.tau0, j.tau_max, j.n_steps, j.scheme, j.shift_mode,
-                           j.shift0, j.chi_max, j.cutoff, &j.opts, info.data(), nullptr);
-  ite_job_result& r = job.result;
-  r.status = s;
-  r.steps_done = 0;
-  r.max_discarded_weight = 0.0;
-  r.max_chi = 0;
-  // steps that ran have filled their record (max_chi >= 1)
-  for (int k = 0; k < j.n_steps && info[k].max_chi > 0; ++k) {
-    ++r.steps_done;
-    r.energy = info[k].energy;
-    r.max_discarded_weight = std::max(r.max_discarded_weight, info[k].max_discarded_weight);
-    r.max_chi = std::max(r.max_chi, info[k].max_chi);
-    if (j.energies) j.energies[k] = info[k].energy;
-  }
-  if (s == ITE_OK && (j.state || j.state_chi)) {
-    std::vector<int> chi(N + 1);
-    size_t nd = 0;
-    s = ite_mps_bond_dims(psi, chi.data(), &nd);
-    if (s == ITE_OK && j.state_chi) std::copy(chi.begin(), chi.end(), j.state_chi);
-    if (s == ITE_OK && j.state) s = nd <= j.state_cap ? ite_mps_get(ctx, psi, j.state, j.state_cap)
-                                                      : ITE_EINVAL;
+  if (j.metts_samples > 0) {
+    std::vector<double> nodes((size_t)K + 1);
+    if (s == ITE_OK)
+      s = j.grid == ITE_JOB_GRID_PANELS ? ite_grid_panels(j.tau_max, j.panels, j.n_steps, nodes.data())
+                                        : ite_grid_geometric(j.tau0, j.tau_max, j.n_steps, nodes.data());
+    if (s == ITE_OK)
+      s = ite_metts(ctx, H, job.config0.data(), nodes.data(), K, j.scheme, j.shift_mode, j.shift0,
+                    j.chi_max, j.cutoff, &j.opts, job.alt_basis.empty() ? nullptr : job.alt_basis.data(),
+                    job.obs.empty() ? nullptr : job.obs.data(), j.metts_obs_site, j.metts_samples,
+                    job.uniforms.data(), j.metts_energies, j.metts_obs_values, j.metts_configs);
     r.status = s;
+    if (s == ITE_OK) {
+      r.steps_done = j.metts_samples * K;
+      r.energy = j.metts_energies[j.metts_samples - 1];
+    }
+  } else {
+    if (s == ITE_OK) s = ite_mps_create_product(ctx, N, d, job.site_vecs.data(), j.chi_max, &psi);
+    std::vector<ite_step_info> info(K);
+    if (s == ITE_OK)
+      s = j.grid == ITE_JOB_GRID_PANELS
+              ? ite_evolve_panels(ctx, H, psi, j.tau_max, j.panels, j.n_steps, j.scheme, j.shift_mode,
+                                  j.shift0, j.chi_max, j.cutoff, &j.opts, info.data(), nullptr)
+              : ite_evolve_loggrid(ctx, H, psi, j.tau0, j.tau_max, j.n_steps, j.scheme, j.shift_mode,
+                                   j.shift0, j.chi_max, j.cutoff, &j.opts, info.data(), nullptr);
+    r.status = s;
+    // steps that ran have filled their record (max_chi >= 1)
+    for (int k = 0; k < K && info[k].max_chi > 0; ++k) {
+      ++r.steps_done;
+      r.energy = info[k].energy;
+      r.max_discarded_weight = std::max(r.max_discarded_weight, info[k].max_discarded_weight);
+      r.max_chi = std::max(r.max_chi, info[k].max_chi);
+      if (j.energies) j.energies[k] = info[k].energy;
+    }
+    if (s == ITE_OK && (j.state || j.state_chi)) {
+      std::vector<int> chi(N + 1);
+      size_t nd = 0;
+      s = ite_mps_bond_dims(psi, chi.data(), &nd);
+      if (s == ITE_OK && j.state_chi) std::copy(chi.begin(), chi.end(), j.state_chi);
+      if (s == ITE_OK && j.state) s = nd <= j.state_cap ? ite_mps_get(ctx, psi, j.state, j.state_cap)
+                                                        : ITE_EINVAL;
+      r.status = s;
+    }
   }
   if (psi) ite_mps_destroy(psi);
   if (H) ite_mpo_destroy(H);
@@ -270,13 +314,22 @@ ite_status ite_server_submit(ite_server s, const ite_job* job, long long* ticket
   auto j = std::make_shared<Job>();
   j->spec = *job;
   const int N = job_sites(job), d = job_d(job);
-  j->site_vecs.assign(job->site_vecs, job->site_vecs + (size_t)2 * N * d);
+  if (job->metts_samples == 0) {
+    j->site_vecs.assign(job->site_vecs, job->site_vecs + (size_t)2 * N * d);
+  } else {
+    j->config0.assign(job->metts_config0, job->metts_config0 + N);
+    j->uniforms.assign(job->metts_uniforms, job->metts_uniforms + (size_t)job->metts_samples * N);
+    if (job->metts_alt_basis) j->alt_basis.assign(job->metts_alt_basis, job->metts_alt_basis + 2 * d * d);
+    if (job->metts_obs) j->obs.assign(job->metts_obs, job->metts_obs + 2 * d * d);
+  }
   if (job->model == ITE_MODEL_ANDERSON) {
     j->eps.assign(job->eps, job->eps + job->n);
     j->V.assign(job->V, job->V + job->n);
   }
   j->spec.site_vecs = nullptr;
   j->spec.eps = j->spec.V = nullptr;
+  j->spec.metts_config0 = nullptr;
+  j->spec.metts_uniforms = j->spec.metts_alt_basis = j->spec.metts_obs = nullptr;
   j->bytes = estimate_bytes(job);
   {
     std::lock_guard<std::mutex> lock(s->mu);

@@ -84,3 +84,36 @@ def test_gl_partial_fractions_match_the_oracle(q):
         k = int(np.argmin(np.abs(z - zj)))
         assert abs(z[k] - zj) < 1e-12 * abs(zj)
         assert abs(a[k] - aj) < 1e-11 * abs(aj)
+
+
+def test_struct_layouts_match_the_headers(tmp_path):
+    # offsets and sizes of the structs the binding passes by pointer, from a C
+    # program compiled against the headers, against the ctypes declarations
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_2606_02930_gb300 import _lib as L
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"ite_job": L.ite_job, "ite_job_result": L.ite_job_result,
+               "ite_server_stats": L.ite_server_stats, "ite_step_info": L.ite_step_info,
+               "ite_solver_opts": L.ite_solver_opts}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ite_server.h"',
+             'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        name, field, value = line.split()
+        cls = structs[name]
+        want = C.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert int(value) == want, (name, field)

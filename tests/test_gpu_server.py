@@ -91,3 +91,63 @@ def test_admission_by_device_bytes(api):
     with pytest.raises(Exception):
         server.submit(jobs[-1])
     server.close()
+
+
+def _metts_specs(api):
+    X = np.array([[1.0, 1.0], [1.0, -1.0]]) / np.sqrt(2.0)
+    sz = np.diag([0.5, -0.5]).astype(complex)
+    docc = np.diag([0.0, 0.0, 0.0, 1.0]).astype(complex)
+    specs = []
+    for k, N in enumerate((6, 8, 8)):
+        specs.append(dict(model="heisenberg", n=N, config0=[0, 1] * (N // 2), chi_max=16,
+                          cutoff=1e-12, tau_max=1.0, panels=8, steps_per_panel=4,
+                          uniforms=np.random.default_rng(60 + k).random((4, N)), alt_basis=X,
+                          obs=sz, obs_site=2))
+    eps, V = inputs.flat_band_bath(2)
+    specs.append(dict(model="anderson", n=2, config0=[3, 0, 1], chi_max=16, cutoff=0.0,
+                      tau_max=2.0, panels=9, steps_per_panel=4,
+                      uniforms=np.random.default_rng(13).random((4, 3)), obs=docc, obs_site=0,
+                      U=0.3, eps_d=-0.15, eps=eps, V=V))
+    return specs
+
+
+def _metts_alone(api, spec):
+    ctx = api.ctx_create(0)
+    if spec["model"] == "heisenberg":
+        H = api.mpo_create_heisenberg(ctx, spec["n"])
+    else:
+        H = api.mpo_create_anderson(ctx, spec["eps"], spec["V"], spec["U"], spec["eps_d"])
+    nodes = api.grid_panels(spec["tau_max"], spec["panels"], spec["steps_per_panel"])
+    return api.metts(ctx, H, spec["config0"], nodes, spec["chi_max"], spec["cutoff"],
+                     spec["uniforms"], alt_basis=spec.get("alt_basis"), obs=spec["obs"],
+                     obs_site=spec["obs_site"])
+
+
+def test_metts_and_panel_jobs_in_the_mix_equal_calls_alone(api):
+    # METTS chains (ite_metts) and a panel-grid evolution (ite_evolve_panels)
+    # served side by side give what the same calls give alone
+    specs = _metts_specs(api)
+    jobs = [api.MettsJob(**s) for s in specs]
+    sv = inputs.random_product_state(10, 2, 77)
+    evo = api.Job("heisenberg", 10, sv, 24, 1e-10, 0.0, 4.0, 3, scheme="tr", panels=6,
+                  want_state=True)
+    results, st = api.evolve_batch(jobs + [evo], n_slots=3)
+    assert st["completed"] == len(jobs) + 1 and st["failed"] == 0
+    for job, res, spec in zip(jobs, results, specs):
+        assert res["status"] == 0
+        assert res["steps_done"] == len(spec["uniforms"]) * spec["panels"] * spec["steps_per_panel"]
+        e, vals, cfgs = _metts_alone(api, spec)
+        assert np.array_equal(job.configs, cfgs)
+        assert np.max(np.abs(job.energies - e)) <= 1e-12 * np.max(np.abs(e))
+        assert np.max(np.abs(job.obs_values - vals)) <= 1e-12
+    ctx = api.ctx_create(0)
+    H = api.mpo_create_heisenberg(ctx, 10)
+    psi = api.mps_create_product(ctx, sv, 24)
+    _, infos = api.evolve_panels(ctx, H, psi, 4.0, 6, 3, "tr", 24, 1e-10,
+                                 shift_mode=api.SHIFT_CURRENT_ENERGY)
+    e_alone = np.array([i["energy"] for i in infos])
+    assert results[-1]["steps_done"] == 18
+    assert np.max(np.abs(evo.energies - e_alone)) <= 1e-12 * np.max(np.abs(e_alone))
+    t_mix, t_alone = evo.tensors(), psi.tensors()
+    ov = omps.overlap(t_alone, t_mix)
+    assert 1.0 - abs(ov) / (omps.norm(t_alone) * omps.norm(t_mix)) <= 1e-12

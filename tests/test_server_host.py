@@ -52,3 +52,22 @@ def test_server_calls_reject_invalid_arguments():
     assert lib.ite_evolve_batch(0, 2, 0, 1, arr, res, None) == L.ITE_EINVAL
     assert lib.ite_server_drain(None) == L.ITE_EINVAL
     assert np.isfinite(_heis(8, 16).device_bytes())
+
+
+def test_metts_and_panel_job_validation():
+    from paper_2606_02930_gb300.api import MettsJob
+    us = np.full((3, 6), 0.5)
+    ok = MettsJob("heisenberg", 6, [0, 1] * 3, 16, 1e-12, 1.0, 8, 4, us)
+    assert ok.device_bytes() > 0
+    bad = MettsJob("heisenberg", 6, [0, 1, 0, 1, 0, 2], 16, 1e-12, 1.0, 8, 4, us)
+    assert bad.device_bytes() == 0                     # state 2 of a spin
+    bad = MettsJob("heisenberg", 6, [0, 1] * 3, 16, 1e-12, 1.0, 0, 4, us)
+    assert bad.device_bytes() == 0                     # no panels
+    bad = MettsJob("heisenberg", 6, [0, 1] * 3, 16, 1e-12, 1.0, 8, 4, us,
+                   obs=np.eye(2), obs_site=6)
+    assert bad.device_bytes() == 0                     # observable site out of range
+    pj = Job("heisenberg", 8, inputs.random_product_state(8, 2, 1), 16, 1e-10, 0.0, 4.0, 3,
+             panels=5)
+    assert pj.device_bytes() > 0 and len(pj.energies) == 15
+    pj.c.grid = 5
+    assert pj.device_bytes() == 0
