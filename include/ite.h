@@ -2,8 +2,7 @@
  * ite.h -- C ABI of the GB300 (sm_103a) library for imaginary-time evolution
  * of matrix product states by A-stable implicit steps on logarithmic tau grids.
  *
- * The method (paper: "Fast Tensor Network Imaginary Time Evolution by Implicit
- * Stepping on Logarithmic Grids"): evolve |psi(tau)> = e^{-H tau}|psi(0)>
+ * The method (arXiv 2606.02930): evolve |psi(tau)> = e^{-H tau}|psi(0)>
  * (Method, Eq. 1) on a grid whose steps grow geometrically (Method, log-grid
  * and panel paragraphs), each step being the implicit linear solve
  *
@@ -93,8 +92,8 @@ typedef enum {
 typedef enum { ITE_FP64 = 0, ITE_FP64_TC = 1 } ite_precision;
 
 /* Spectrum shift s of each step.  FIXED: the caller's value.  CURRENT_ENERGY:
- * s_k = <psi_{k-1}|H|psi_{k-1}> (App. D: shift by the energy of the new
- * time-evolved state to limit norm drift). */
+ * s_k = <psi_{k-1}|H|psi_{k-1}> (App. D shifts H by the energy of the state
+ * each step produced, which keeps the norm of the next step near one). */
 typedef enum { ITE_SHIFT_FIXED = 0, ITE_SHIFT_CURRENT_ENERGY = 1 } ite_shift_mode;
 
 /* Device allocator hooks: alloc returns a device pointer (NULL on failure). */

@@ -4,7 +4,7 @@ Test infrastructure only.
 The paper solves each implicit step (Eq. 4) as an MPO-MPS linear system with
 a two-site DMRG-like scheme: the right-hand side MPS b is projected into the
 basis of the solution MPS x, each two-site block is found by GMRES, and the
-block is split again by a truncated SVD (Method, "two operations"; App. B).
+block is split again by a truncated SVD (Method; App. B).
 Everything below follows those steps in that order, with the readings that
 the paper leaves open fixed as follows:
 
@@ -14,14 +14,16 @@ the paper leaves open fixed as follows:
   sweep").
 * The local system is ((1 - c s) I + c H_eff) X = B, i.e. A = I + c (H - s)
   projected, with H_eff the two-site effective Hamiltonian.
-* GMRES: one cycle of at most m Arnoldi steps (m = 10: "a single GMRES restart
-  with a Krylov subspace of size 10", App. D), modified Gram-Schmidt with one
-  re-orthogonalisation pass, initial guess the current two-site block, early
-  exit on breakdown (h_{j+1,j} <= 1e-14 |r0|) or when the relative residual
+* GMRES: one cycle of at most m Arnoldi steps (m = 10: App. D fixes one
+  GMRES cycle on a ten-dimensional Krylov space per local solve), modified
+  Gram-Schmidt with one re-orthogonalisation pass, initial guess the current
+  two-site block, early exit on a happy breakdown (h_{j+1,j} <= 1e-14 |A v_j|,
+  |A v_j| being the norm of Hessenberg column j) or when the relative residual
   |r|/|B| <= local_tol.  The small least-squares problem is solved with LAPACK.
 * Truncation: keep r = min(chi_max, smallest r >= 1 whose discarded squared
-  weight sum_{k>r} s_k^2 <= max(cutoff, 1e-24) * sum_k s_k^2) (Heisenberg
-  section: "total discarded squared Schmidt weight at a bond"); then, if
+  weight sum_{k>r} s_k^2 <= max(cutoff, 1e-24) * sum_k s_k^2) (the Heisenberg
+  section bounds the sum of the squared Schmidt values dropped at each bond);
+  then, if
   s_{r+1} >= s_r (1 - 1e-10), lower r to just before that near-degenerate
   group, unless that would leave r = 0 (then r is left as it was).
 """
@@ -120,7 +122,9 @@ def gmres(matvec, B, X0, m, local_tol=0.0):
         e1[0] = beta
         y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
         res = np.linalg.norm(e1 - H[:k + 1, :k] @ y)
-        if H[j + 1, j].real <= BREAKDOWN_REL * beta:
+        # happy breakdown: the new direction is negligible against A v_j,
+        # whose norm is that of Hessenberg column j (Arnoldi relation)
+        if H[j + 1, j].real <= BREAKDOWN_REL * np.linalg.norm(H[:j + 2, j]):
             break
         if local_tol > 0.0 and res <= local_tol * bnorm:
             break

@@ -21,7 +21,7 @@ Schemes (H' = H - s):
           from the initial guess psi_{k-1}), then a two-site fit of the sum.
 After the solve the state is normalised (Heisenberg section, App. D).  The
 shift s is either fixed or, in 'energy' mode, the energy of the current state
-(App. D: shift the spectrum by the energy of the new time-evolved state).
+(App. D moves the spectrum by the energy of the state the last step produced).
 """
 import numpy as np
 

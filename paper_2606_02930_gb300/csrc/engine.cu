@@ -37,7 +37,7 @@ namespace {
 
 constexpr double kWeightFloor = 1e-24;   // relative squared weight treated as zero
 constexpr double kTieRel = 1e-10;        // near-degenerate singular values
-constexpr double kBreakdownRel = 1e-14;  // GMRES breakdown threshold (relative to |r0|)
+constexpr double kBreakdownRel = 1e-14;  // GMRES happy breakdown: h_{j+1,j} <= this * |A v_j|
 // one-sided Jacobi: rows count as orthogonal once |a_u^H a_v| <= q eps |a_u||a_v|
 // (the rounding floor of a length-q inner product); sweeps are capped
 constexpr double kEps = 2.220446049250313e-16;

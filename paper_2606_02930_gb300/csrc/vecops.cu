@@ -224,6 +224,14 @@ __global__ void k_gmres_collect(GmresState* s, int j, const cplx* h1, const cplx
 __global__ void k_gmres_step(GmresState* s, int j, int m, double brel, double ltol) {
   if (!s->active) return;
   const double hj1 = sqrt(s->wnorm2);
+  // |A v_j|^2 = sum_i |h_ij|^2 + h_{j+1,j}^2 (Arnoldi relation), read before
+  // the rotations touch column j; a happy breakdown is a new direction that
+  // is negligible against it
+  double col2 = s->wnorm2;
+  for (int i = 0; i <= j; ++i) {
+    const cplx h = Hc(s, i, j);
+    col2 = fma(h.x, h.x, fma(h.y, h.y, col2));
+  }
   // earlier rotations on column j
   for (int i = 0; i < j; ++i) {
     const cplx a = Hc(s, i, j), b = Hc(s, i + 1, j);
@@ -253,7 +261,7 @@ __global__ void k_gmres_step(GmresState* s, int j, int m, double brel, double lt
   s->g[j + 1] = cscale(cmul(cconj(sn), gj), -1.0);
   s->res = hypot(s->g[j + 1].x, s->g[j + 1].y);
   s->steps = j + 1;
-  if (!(hj1 > brel * s->beta) || !isfinite(hj1)) {
+  if (!(hj1 > brel * sqrt(col2)) || !isfinite(hj1)) {
     s->breakdown = 1;
     s->active = 0;
   } else if (ltol > 0.0 && s->res <= ltol * s->bnorm) {

@@ -233,6 +233,30 @@ def test_local_solve_matches_oracle_gmres(api, ctx, model, N, chi, i):
         assert abs(res - res_ref) < 1e-8 * max(res_ref, 1e-6)
 
 
+def test_local_solve_is_invariant_under_scaling(api, ctx):
+    # (A, s B, s X0) gives s X in the same number of Krylov steps, also when
+    # the scale makes |r0| tiny or huge next to |A v_j|
+    N, chi, i = 8, 12, 3
+    Ws = ompo.heisenberg_mpo(N)
+    A = inputs.random_mps(N, 2, chi, 100 + N)
+    H = api.mpo_create(ctx, Ws)
+    L, R, X0 = _canonical_envs(Ws, A, i)
+    B = X0 + 0.3 * crandn(np.random.default_rng(9), *X0.shape)
+    Ld, Rd = to_dev(L_to_lib(L)), to_dev(R_to_lib(R))
+    runs = {}
+    for scale in (1.0, 1e-20, 1e20):
+        X = to_dev(scale * X0)
+        k, res = api.k_local_solve(ctx, H, i, Ld, Rd, to_dev(scale * B), X, 1.05, 0.05, 10)
+        runs[scale] = (k, res, to_host(X) / scale)
+    k1, r1, x1 = runs[1.0]
+    assert k1 == 10
+    for scale in (1e-20, 1e20):
+        k, res, x = runs[scale]
+        assert k == k1, scale
+        assert rel_err(x, x1) < 1e-12
+        assert abs(res - r1) < 1e-10
+
+
 @pytest.mark.parametrize("m,n,kind", [(128, 128, "decay"), (512, 512, "decay"), (200, 160, "ties"),
                                       (160, 200, "decay"), (256, 512, "decay")])
 def test_split_tensor_core_mode(api, ctx, m, n, kind):

@@ -177,6 +177,25 @@ def test_gmres_equals_krylov_least_squares():
     assert k == 3 and np.linalg.norm(D @ x - bb) < 1e-13
 
 
+def test_gmres_is_invariant_under_scaling():
+    # GMRES on (A, s b, s x0) returns s x in the same number of steps for any
+    # scale s: the breakdown test compares h_{j+1,j} with |A v_j| (both of
+    # the unit Krylov vectors), not with the scale of the residual
+    rng = np.random.default_rng(73)
+    n = 40
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = np.eye(n) + 0.1 * (G + G.conj().T)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x0 = rng.standard_normal(n) + 0j
+    x1, (k1, r1) = ls.gmres(lambda v: A @ v, b, x0, 10)
+    assert k1 == 10
+    for scale in (1e-20, 1e-8, 1e8, 1e20):
+        xs, (ks, rs) = ls.gmres(lambda v: A @ v, scale * b, scale * x0, 10)
+        assert ks == k1, scale
+        assert np.linalg.norm(xs / scale - x1) < 1e-12 * np.linalg.norm(x1)
+        assert abs(rs - r1) < 1e-12
+
+
 def test_choose_rank_rules():
     S = np.array([1.0, 0.5, 0.25, 1e-3, 1e-6, 0.0])
     assert ls.choose_rank(S, 10, 0.0)[0] == 5          # exact zero dropped (weight floor)
