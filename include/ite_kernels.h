@@ -79,6 +79,17 @@ ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, 
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded, int flags);
 
+/* Self-test of the bounded grid-wide wait that the cooperative kernels of the
+ * SVD (LQ and Jacobi sweeps) meet at after each step or round; the paper has
+ * no counterpart.  Launches `blocks` co-resident blocks (2 <= blocks <= the
+ * SM count) at one grid barrier, of which the first `absent` (0 <= absent <
+ * blocks) never arrive.  absent == 0: the barrier completes, ITE_OK.
+ * absent > 0: the waiting blocks give up at the barrier's iteration limit
+ * (about a second), record the failure and return, and the call returns
+ * ITE_ETIMEOUT with the context still usable.  ITE_EINVAL for other
+ * arguments. */
+ite_status ite_k_barrier_selftest(ite_ctx ctx, int blocks, int absent);
+
 /* Tensor-core GEMM (the contraction engine of the library on sm_103a):
  * C[M][N] = A[M][K] B[N][K]^T, A and B bf16 row-major with K contiguous
  * (leading dimensions lda, ldb in elements, multiples of 8, pointers 16-byte

@@ -131,6 +131,7 @@ SIGNATURES = {
     "ite_k_zgemm": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _i, _vp,
                          C.c_longlong, C.c_longlong, _i, _vp, C.c_longlong, _pd, _pd]),
     "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd, _i]),
+    "ite_k_barrier_selftest": (_i, [_vp, _i, _i]),
     "ite_job_device_bytes": (_sz, [C.POINTER(ite_job)]),
     "ite_server_create": (_i, [_i, _i, _sz, C.POINTER(_vp)]),
     "ite_server_submit": (_i, [_vp, C.POINTER(ite_job), C.POINTER(C.c_longlong)]),

@@ -359,6 +359,12 @@ def k_split(ctx, X, m, n, chi_max, cutoff, centre_right, left, right, sigma=None
     return r.value, disc.value
 
 
+def k_barrier_selftest(ctx, blocks, absent):
+    """ite_k_barrier_selftest; returns the status (ITE_OK, or ITE_ETIMEOUT
+    when `absent` blocks never reach the barrier)."""
+    return int(lib.ite_k_barrier_selftest(ctx.h, blocks, absent))
+
+
 # ------------------------------------------------------------------ profiling
 PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step", "lq", "jacobi")
 PROFILE_SLOTS = 16

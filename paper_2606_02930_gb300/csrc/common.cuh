@@ -177,6 +177,10 @@ cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cud
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
                         unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st);
+// one cooperative launch of `blocks` blocks meeting at the grid barrier, the
+// first `absent` of them never arriving; word 4 of dev_state ends nonzero
+// when the wait ran out (blocks must be co-resident: at most the SM count)
+cudaError_t barrier_selftest(unsigned int* dev_state, int blocks, int absent, cudaStream_t st);
 // row norms sigma[i] = |A row i|, the permutation sorting them descending (ties
 // by index), and the kept rank by the truncation rule (see engine).
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

@@ -2092,6 +2092,19 @@ ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double*
   return ITE_OK;
 }
 
+ite_status ite_k_barrier_selftest(ite_ctx ctx, int blocks, int absent) {
+  if (!ctx || blocks < 2 || absent < 0 || absent >= blocks) return ITE_EINVAL;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  if (blocks > sms) return ITE_EINVAL;
+  unsigned int* st = reinterpret_cast<unsigned int*>(ctx->dcounter) + 16;
+  CK(barrier_selftest(st, blocks, absent, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, st + 4, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "grid barrier wait ran out");
+  return ITE_OK;
+}
+
 ite_status ite_k_split(ite_ctx ctx, const double* X, int m, int n, int chi_max, double cutoff,
                        int centre_right, double* left, double* right, double* sigma, int* rank,
                        double* discarded, int flags) {

@@ -734,7 +734,23 @@ struct Coresident {
 };
 Coresident g_lq_blocks, g_jacobi_blocks, g_formq_blocks;
 
+// The grid barrier of the cooperative kernels with `absent` blocks that never
+// arrive: the others wait until the barrier's iteration limit, set the error
+// word and return.
+__global__ void k_barrier_selftest(unsigned int* st, int absent) {
+  if ((int)blockIdx.x < absent) return;
+  grid_barrier(st, gridDim.x);
+}
+
 }  // namespace
+
+cudaError_t barrier_selftest(unsigned int* dev_state, int blocks, int absent, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, S_WORDS * sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
+  void* args[] = {&dev_state, &absent};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(blocks), dim3(32), args, 0, st);
+}
 
 cudaError_t svd_lq(cplx* W, int p, int q, cplx* beta, double* refl, unsigned int* dev_state,
                    cudaStream_t st) {

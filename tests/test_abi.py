@@ -68,6 +68,7 @@ def test_invalid_arguments_fail_cleanly():
     assert lib.ite_ctx_create(10**6, None, _lib.ite_alloc_fn(), _lib.ite_free_fn(), None,
                               ctypes.byref(out)) != _lib.ITE_OK
     assert lib.ite_last_error(None) == b"null context"
+    assert lib.ite_k_barrier_selftest(None, 4, 1) == _lib.ITE_EINVAL
 
 
 @pytest.mark.parametrize("q", [1, 2, 3, 4])

@@ -233,6 +233,27 @@ def test_local_solve_matches_oracle_gmres(api, ctx, model, N, chi, i):
         assert abs(res - res_ref) < 1e-8 * max(res_ref, 1e-6)
 
 
+def test_bounded_grid_wait_ends_with_a_status(api, ctx):
+    # A grid barrier that some blocks never reach: the waiting blocks give up
+    # at the barrier's iteration limit, the call reports ITE_ETIMEOUT instead
+    # of hanging, and the context keeps working (a split afterwards is exact).
+    import torch
+    from paper_2606_02930_gb300 import _lib as L
+    assert api.k_barrier_selftest(ctx, 16, 0) == L.ITE_OK
+    assert api.k_barrier_selftest(ctx, 16, 3) == L.ITE_ETIMEOUT
+    assert b"wait ran out" in L.lib.ite_last_error(ctx.h)
+    assert api.k_barrier_selftest(ctx, 16, 0) == L.ITE_OK
+    rng = np.random.default_rng(5)
+    X = _spectrum_matrix(rng, 64, 48, np.exp(-np.arange(48) / 6.0))
+    left = to_dev(np.zeros(64 * 64))
+    right = to_dev(np.zeros(64 * 48))
+    sig = torch.zeros(48, dtype=torch.float64, device="cuda")
+    r, _ = api.k_split(ctx, to_dev(X), 64, 48, 48, 0.0, True, left, right, sig)
+    S = np.linalg.svd(X, compute_uv=False)
+    assert r == 48
+    assert np.max(np.abs(sig.cpu().numpy() - S) / S) < 1e-12
+
+
 def test_local_solve_is_invariant_under_scaling(api, ctx):
     # (A, s B, s X0) gives s X in the same number of Krylov steps, also when
     # the scale makes |r0| tiny or huge next to |A v_j|
