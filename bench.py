@@ -147,7 +147,9 @@ class ClockSampler:
 
     def start(self):
         try:
-            fd, self.path = tempfile.mkstemp(prefix=f"ite_clocks_rank{self.index}_", suffix=".csv")
+            work = os.path.join(ROOT, "_build", "clocks")           # git-ignored scratch
+            os.makedirs(work, exist_ok=True)
+            fd, self.path = tempfile.mkstemp(prefix=f"rank{self.index}_", suffix=".csv", dir=work)
             self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
                                           f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",

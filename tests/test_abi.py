@@ -87,7 +87,7 @@ def test_gl_partial_fractions_match_the_oracle(q):
         assert abs(a[k] - aj) < 1e-11 * abs(aj)
 
 
-def test_struct_layouts_match_the_headers(tmp_path):
+def test_struct_layouts_match_the_headers():
     # offsets and sizes of the structs the binding passes by pointer, from a C
     # program compiled against the headers, against the ctypes declarations
     import ctypes as C
@@ -107,10 +107,14 @@ def test_struct_layouts_match_the_headers(tmp_path):
         for field, _ in cls._fields_:
             lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
     lines += ['  return 0;', '}']
-    src = tmp_path / "layout.c"
-    src.write_text("\n".join(lines) + "\n")
-    exe = tmp_path / "layout"
-    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    work = os.path.join(root, "_build", "abi_layout")           # git-ignored scratch
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, "layout.c")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    exe = os.path.join(work, "layout")
+    inc = os.path.join(root, "include")
     subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
     for line in out.splitlines():
