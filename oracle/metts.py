@@ -13,8 +13,9 @@ right-canonical form (orthogonality centre on the first site), the
 conditional probability of s at site i given the earlier choices is
 |v A_i[:, s, :]|^2 / sum_s' |v A_i[:, s', :]|^2, v the normalised row
 vector of the earlier choices; s is the smallest value whose cumulative
-conditional probability exceeds the uniform number u_i.  The uniform numbers
-are inputs, so that a chain is a deterministic function of them.
+conditional probability exceeds the uniform number u_i (when rounding leaves
+the total below u_i, the last value of nonzero probability).  The uniform
+numbers are inputs, so that a chain is a deterministic function of them.
 """
 import numpy as np
 
@@ -36,16 +37,23 @@ def sample(psi, u, basis=None):
             M = np.asarray(basis).conj().T @ M               # <b_s| components
         w = np.sum(np.abs(M) ** 2, axis=1)
         p = w / np.sum(w)
-        cum, s = 0.0, len(p) - 1
-        for k in range(len(p)):
-            cum += p[k]
-            if cum > u[i]:
-                s = k
-                break
+        s = _draw(p, u[i])
         config.append(s)
         prob *= p[s]
         v = M[s] / np.sqrt(w[s])
     return config, prob
+
+
+def _draw(p, u):
+    """Smallest s whose cumulative probability exceeds u; if rounding leaves
+    the total at or below u, the last s of nonzero probability."""
+    cum = 0.0
+    for k in range(len(p)):
+        cum += p[k]
+        if cum > u:
+            return k
+    nz = np.nonzero(p > 0)[0]
+    return int(nz[-1]) if nz.size else len(p) - 1
 
 
 def product_tensors(config, d, basis=None):
@@ -122,13 +130,7 @@ def dense_metts_chain(H, d, N, config0, beta, uniforms, obs_dense=None, nodes=No
             w = np.abs(amp) ** 2
             if w.ndim > 1:
                 w = np.sum(w, axis=tuple(range(1, w.ndim)))
-            p = w / np.sum(w)
-            cum, s = 0.0, d - 1
-            for k in range(d):
-                cum += p[k]
-                if cum > u[i]:
-                    s = k
-                    break
+            s = _draw(w / np.sum(w), u[i])
             config.append(s)
             amp = amp[s]
     return energies, values

@@ -4,7 +4,8 @@
 // are M_s = <b_s| v A_i (s < d, b_s the columns of the collapse basis, or
 // the computational basis), their weights w_s = |M_s|^2 give the conditional
 // probabilities p_s = w_s / sum w, the choice is the smallest s whose
-// cumulative probability exceeds the uniform u, and the next vector is
+// cumulative probability exceeds the uniform u (the last s of nonzero weight
+// when rounding leaves the total at or below u), and the next vector is
 // M_s / |M_s|.
 #include "common.cuh"
 
@@ -66,15 +67,14 @@ k_sample_site(const cplx* A, int chl, int d, int chr, const cplx* v, double u, c
       for (int k = 0; k < ST / 32; ++k) ws[s] += red[k][s];
       tot += ws[s];
     }
-    int pick = d - 1;
+    int pick = -1, last = d - 1;
     double cum = 0.0;
     for (int s = 0; s < d; ++s) {
+      if (ws[s] > 0.0) last = s;
       cum += ws[s] / tot;
-      if (cum > u) {
-        pick = s;
-        break;
-      }
+      if (pick < 0 && cum > u) pick = s;
     }
+    if (pick < 0) pick = last;
     *choice = pick;
     *prob *= ws[pick] / tot;
     sel[0] = (double)pick;

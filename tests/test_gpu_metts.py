@@ -48,6 +48,20 @@ def _paper_grid(api, tau_max, first=0.01, n=4):
     return api.grid_panels(tau_max, P, n)
 
 
+def test_collapse_never_takes_a_state_of_zero_probability(api, ctx):
+    # amplitudes (a, b, c, 0) on the first site and u the largest double
+    # below 1: whether or not rounding leaves the cumulative total below u,
+    # the draw takes c (the last state of nonzero probability), never 3
+    amp = np.array([1.0486494471372438, 0.41183145201048543, 0.5233264489725756, 0.0])
+    A = [amp.astype(complex).reshape(1, 4, 1), np.eye(4)[0].astype(complex).reshape(1, 4, 1)]
+    u = [1.0 - 2.0 ** -53, 0.5]
+    psi = api.mps_create(ctx, A, 4)
+    cfg, p = api.mps_sample(ctx, psi, u)
+    cfg_o, p_o = ometts.sample(A, u)
+    assert cfg == cfg_o == [2, 0]
+    assert abs(p - p_o) <= 1e-12 * p_o
+
+
 def test_heisenberg_chain_matches_oracle(api, ctx):
     # trapezoid rule on the paper's panel grid with the current-energy shift;
     # the steps keep dtau (s - E0) / 2 <= 0.33 for every product start state,

@@ -154,3 +154,15 @@ def test_anderson_chain_conditioning():
                                  obs_site=0, scheme="tr")
     e1, _, _ = _in_sector_noise_chain(Ws, [1, 2, 1, 2], 4, nodes, us, 1e-14, 1e-14, 1, docc)
     assert np.max(np.abs(np.array(e1) - e0) / np.abs(e0)) > 1e-6
+
+
+def test_draw_never_takes_a_state_of_zero_probability():
+    # Amplitudes (a, b, c, 0) whose normalised cumulative probabilities round
+    # to 1 - 2^-53 in total: with u the largest double below 1 no cumulative
+    # probability exceeds u, and the draw must still take a state of nonzero
+    # probability (the last one, c), never the empty state 3.
+    amp = np.array([1.0486494471372438, 0.41183145201048543, 0.5233264489725756, 0.0])
+    psi = [amp.astype(complex).reshape(1, 4, 1)]
+    config, p = metts.sample(psi, [1.0 - 2.0 ** -53])
+    assert config == [2]
+    assert abs(p - amp[2] ** 2 / np.sum(amp ** 2)) < 1e-15
