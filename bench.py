@@ -187,6 +187,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ replicas
+def replica_seed(rank):
+    """Seed of rank's chain: replicas evolve different synthetic states."""
+    return SEED + rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks of the process group (x without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, t_max_s):
+    """tau-steps/s of the whole job: every rank's steps over the slowest rank's time."""
+    return world * steps / t_max_s
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -226,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = api.ctx_create(local_rank)
     stream = torch.cuda.current_stream()
     H = api.mpo_create_heisenberg(ctx, N_SITES)
-    A0 = inputs.random_isometric_mps(N_SITES, D_SITE, CHI, SEED + rank)
+    A0 = inputs.random_isometric_mps(N_SITES, D_SITE, CHI, replica_seed(rank))
     psi = api.mps_create(ctx, A0, CHI)
     nodes = api.grid_geometric(TAU0, TAU_MAX, K_GRID)
     state = {"k": 0, "s": api.energy(ctx, H, psi)}
@@ -266,12 +287,8 @@ def run_ours(args, rank, world, local_rank):
     launches = api.kernel_launches() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(world, args.steps, t_max * 1e-3)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     cap = [1] + inputs.bond_profile(N_SITES, D_SITE, CHI) + [1]
@@ -298,11 +315,7 @@ def run_ours(args, rank, world, local_rank):
         L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
         d2h += 8 * n.value
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
 
     heff = prof["heff"]
     heff_tf = heff["flops"] / (heff["ms"] * 1e-3) / 1e12 if heff["ms"] > 0 else 0.0
@@ -317,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
                        "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state 134 MB + environments 0.7 GB per chain)"},
-            "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_rate(world, args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
             "gpu_launches": int(launches),
             "roofline": {"kernel": "k_jacobi_persistent (one-sided Jacobi of the SVD splits)",
