@@ -278,6 +278,34 @@ def test_local_solve_is_invariant_under_scaling(api, ctx):
         assert abs(res - r1) < 1e-10
 
 
+@pytest.mark.parametrize("m,n,chi_max,cutoff", [(1024, 1024, 256, 1e-10), (2048, 2048, 512, 1e-14)])
+def test_split_workload_row_lengths(api, ctx, m, n, chi_max, cutoff):
+    # The two-site blocks of the larger workloads: rows of 1024 (chi = 512
+    # with d = 2, or chi = 256 with d = 4) and of 2048 (the chi = 512 impurity
+    # chain, d = 4).  They take the Jacobi's 16-element register path and its
+    # streamed path.  Same rank, singular values and truncated product as the
+    # oracle's SVD, and an isometric left factor.
+    import torch
+    rng = np.random.default_rng(m + 1)
+    p = min(m, n)
+    X = _spectrum_matrix(rng, m, n, np.exp(-np.arange(p) / (p / 16)))
+    S_ref = np.linalg.svd(X, compute_uv=False)
+    r_ref, disc_ref = ls.choose_rank(S_ref, chi_max, cutoff)
+    left = to_dev(np.zeros(m * p))
+    right = to_dev(np.zeros(p * n))
+    sig = torch.zeros(p, dtype=torch.float64, device="cuda")
+    r, disc = api.k_split(ctx, to_dev(X), m, n, chi_max, cutoff, True, left, right, sig, tc=True)
+    assert r == r_ref
+    assert abs(disc - disc_ref) <= 1e-10 * max(disc_ref, 1e-12) + 1e-15
+    sg = sig.cpu().numpy()[:r]
+    assert np.max(np.abs(sg - S_ref[:r]) / S_ref[:r]) < 1e-10
+    Lh = to_host(left)[: m * r].reshape(m, r)
+    Rh = to_host(right)[: r * n].reshape(r, n)
+    A1, A2, _, _ = ls.split_two_site(X.reshape(m, 1, 1, n), chi_max, cutoff, True)
+    assert rel_err(Lh @ Rh, A1.reshape(m, -1) @ A2.reshape(-1, n)) < 1e-10
+    assert np.abs(Lh.conj().T @ Lh - np.eye(r)).max() < 1e-12
+
+
 @pytest.mark.parametrize("m,n,kind", [(128, 128, "decay"), (512, 512, "decay"), (200, 160, "ties"),
                                       (160, 200, "decay"), (256, 512, "decay")])
 def test_split_tensor_core_mode(api, ctx, m, n, kind):
