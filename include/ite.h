@@ -108,6 +108,10 @@ typedef struct {
   double sweep_tol;   /* stop sweeping at 1-|<x_s|x_{s-1}>| < tol (0: fixed)   */
   int fit_sweeps;     /* sweeps of the trapezoid right-hand-side fit (1)       */
   int precision;      /* ite_precision (ITE_FP64 or ITE_FP64_TC)               */
+  int max_cycles;     /* GMRES(krylov_dim) cycles per local solve, each
+                         restarted from the last iterate (default 1, as App. D;
+                         <= 0 counts as 1); a cycle that ends early (breakdown
+                         or local_tol reached) ends the solve                  */
 } ite_solver_opts;
 
 /* Per-step report. */
@@ -186,6 +190,23 @@ ite_status ite_mps_copy(ite_ctx ctx, ite_mps src, ite_mps dst);
 ite_status ite_mps_bond_dims(ite_mps mps, int* chi, size_t* n_doubles);
 ite_status ite_mps_get(ite_ctx ctx, ite_mps mps, double* A, size_t cap_doubles);
 void ite_mps_destroy(ite_mps mps);
+
+/* Checkpoint of an MPS, to resume an evolution later or in another process
+ * (library addition; the paper has no counterpart).  The byte image is
+ * the magic "ITEMPS01", then the 8-byte integers N, d, chi_cap and
+ * chi[0..N], then the site tensors as ite_mps_get writes them (interleaved
+ * complex doubles), all in the host's byte order (little-endian on the
+ * supported hosts).  ite_mps_bytes gives its size; ite_mps_save writes it to
+ * host memory buf of cap bytes (ITE_EINVAL if too small); ite_mps_load
+ * creates a new MPS in ctx from len bytes at buf, and returns ITE_EINVAL for
+ * a wrong magic, truncated or inconsistent image without creating one. */
+ite_status ite_mps_bytes(ite_mps mps, size_t* bytes);
+ite_status ite_mps_save(ite_mps mps, void* buf, size_t cap);
+ite_status ite_mps_load(ite_ctx ctx, const void* buf, size_t len, ite_mps* out);
+/* The state as a dense vector psi[s_0 ... s_{N-1}] (s_0 most significant;
+ * interleaved complex; cap_doubles >= 2 d^N), contracted on the host from
+ * the tensors: a check for small systems (d^N <= 2^24), ITE_EINVAL above. */
+ite_status ite_mps_to_dense(ite_ctx ctx, ite_mps mps, double* out, size_t cap_doubles);
 
 /* One implicit step of size dtau with shift s (Eq. 4 / backward Euler), in
  * place.  The state is normalised afterwards (Heisenberg section, App. D). */

@@ -15,7 +15,8 @@ the paper leaves open fixed as follows:
 * The local system is ((1 - c s) I + c H_eff) X = B, i.e. A = I + c (H - s)
   projected, with H_eff the two-site effective Hamiltonian.
 * GMRES: one cycle of at most m Arnoldi steps (m = 10: App. D fixes one
-  GMRES cycle on a ten-dimensional Krylov space per local solve), modified
+  GMRES cycle on a ten-dimensional Krylov space per local solve; more cycles,
+  each restarted from the last iterate, are an option), modified
   Gram-Schmidt with one re-orthogonalisation pass, initial guess the current
   two-site block, early exit on a happy breakdown (h_{j+1,j} <= 1e-14 |A v_j|,
   |A v_j| being the norm of Hessenberg column j) or when the relative residual
@@ -135,6 +136,19 @@ def gmres(matvec, B, X0, m, local_tol=0.0):
     return X, (k, res / bnorm if bnorm > 0 else 0.0)
 
 
+def gmres_restarted(matvec, B, X0, m, cycles=1, local_tol=0.0):
+    """Up to `cycles` GMRES(m) cycles, each restarted from the last iterate;
+    a cycle that ends before m steps (breakdown, or the relative residual at
+    local_tol) ends the solve.  Returns (X, (total steps, last residual))."""
+    X, steps, res = X0, 0, 0.0
+    for _ in range(max(1, cycles)):
+        X, (k, res) = gmres(matvec, B, X, m, local_tol)
+        steps += k
+        if k < m or (local_tol > 0.0 and res <= local_tol):
+            break
+    return X, (steps, res)
+
+
 def choose_rank(S, chi_max, cutoff):
     """Kept rank for descending singular values S (see module docstring)."""
     n = len(S)
@@ -245,7 +259,7 @@ def _sweep(Ws, x, local_block, others, chi_max, cutoff, info):
 
 
 def linsolve(Ws, x0, b, c, s, chi_max, cutoff, krylov_dim=10, local_tol=0.0,
-             sweeps=1, sweep_tol=0.0):
+             sweeps=1, sweep_tol=0.0, max_cycles=1):
     """Solve (I + c (H - s)) x = b for MPS x, starting from x0 (App. B).
     Returns (x, info); x has its orthogonality centre on site 1."""
     x = right_canonicalize_svd(x0)
@@ -260,7 +274,7 @@ def linsolve(Ws, x0, b, c, s, chi_max, cutoff, krylov_dim=10, local_tol=0.0,
         def matvec(V):
             return alpha * V + c * heff_apply(Lop, Ws[i], Ws[i + 1], Rop, V)
 
-        X, (steps, res) = gmres(matvec, B, X0, krylov_dim, local_tol)
+        X, (steps, res) = gmres_restarted(matvec, B, X0, krylov_dim, max_cycles, local_tol)
         info.gmres_steps += steps
         info.max_local_residual = max(info.max_local_residual, res)
         return X

@@ -41,7 +41,7 @@ class StepInfo:
 
 
 def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
-                  local_tol=0.0, sweeps=1, sweep_tol=0.0, fit_sweeps=1):
+                  local_tol=0.0, sweeps=1, sweep_tol=0.0, fit_sweeps=1, max_cycles=1):
     """Advance the MPS psi (assumed normalised) by one step of size dtau.
     Returns (new normalised MPS, StepInfo)."""
     info = StepInfo()
@@ -75,7 +75,7 @@ def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
         for zj, aj in zip(z, a):
             cj = -dtau / zj
             xj, sinfo = ls.linsolve(Ws, mpsmod.copy(psi), psi, cj, shift, chi_max, cutoff,
-                                    krylov_dim, local_tol, sweeps, sweep_tol)
+                                    krylov_dim, local_tol, sweeps, sweep_tol, max_cycles)
             info.max_discarded = max(info.max_discarded, sinfo.max_discarded)
             info.max_local_residual = max(info.max_local_residual, sinfo.max_local_residual)
             info.gmres_steps += sinfo.gmres_steps
@@ -87,7 +87,7 @@ def implicit_step(Ws, psi, dtau, scheme, shift, chi_max, cutoff, krylov_dim=10,
     else:
         raise ValueError(scheme)
     x, sinfo = ls.linsolve(Ws, x0, b, c, shift, chi_max, cutoff, krylov_dim,
-                           local_tol, sweeps, sweep_tol)
+                           local_tol, sweeps, sweep_tol, max_cycles)
     info.max_discarded = max(info.max_discarded, sinfo.max_discarded)
     info.max_local_residual = sinfo.max_local_residual
     info.gmres_steps = sinfo.gmres_steps

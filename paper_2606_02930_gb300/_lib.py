@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR
 
 class ite_solver_opts(C.Structure):
     _fields_ = [("krylov_dim", C.c_int), ("sweeps", C.c_int), ("local_tol", C.c_double),
-                ("sweep_tol", C.c_double), ("fit_sweeps", C.c_int), ("precision", C.c_int)]
+                ("sweep_tol", C.c_double), ("fit_sweeps", C.c_int), ("precision", C.c_int),
+                ("max_cycles", C.c_int)]
 
 
 class ite_step_info(C.Structure):
@@ -132,6 +133,10 @@ SIGNATURES = {
                          C.c_longlong, C.c_longlong, _i, _vp, C.c_longlong, _pd, _pd]),
     "ite_k_split": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _vp, _vp, _vp, _pi, _pd, _i]),
     "ite_k_barrier_selftest": (_i, [_vp, _i, _i]),
+    "ite_mps_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),
+    "ite_mps_save": (_i, [_vp, _vp, C.c_size_t]),
+    "ite_mps_load": (_i, [_vp, _vp, C.c_size_t, C.POINTER(_vp)]),
+    "ite_mps_to_dense": (_i, [_vp, _vp, _pd, C.c_size_t]),
     "ite_job_device_bytes": (_sz, [C.POINTER(ite_job)]),
     "ite_server_create": (_i, [_i, _i, _sz, C.POINTER(_vp)]),
     "ite_server_submit": (_i, [_vp, C.POINTER(ite_job), C.POINTER(C.c_longlong)]),

@@ -38,10 +38,11 @@ PRECISIONS = {"fp64": L.ITE_FP64, "fp64_tc": L.ITE_FP64_TC}
 
 
 def solver_opts(krylov_dim=10, sweeps=1, local_tol=0.0, sweep_tol=0.0, fit_sweeps=1,
-                precision="fp64"):
+                precision="fp64", max_cycles=1):
     o = L.ite_solver_opts()
     lib.ite_solver_opts_default(C.byref(o))
     o.krylov_dim, o.sweeps, o.local_tol = krylov_dim, sweeps, local_tol
+    o.max_cycles = max_cycles
     o.sweep_tol, o.fit_sweeps = sweep_tol, fit_sweeps
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return o
@@ -142,6 +143,20 @@ class MPS:
     def __init__(self, ctx, h, N, d):
         self.ctx, self.h, self.N, self.d = ctx, h, N, d
 
+    def save(self):
+        """Checkpoint (ite_mps_save) as bytes."""
+        n = C.c_size_t()
+        check(lib.ite_mps_bytes(self.h, C.byref(n)), self.ctx.h)
+        buf = C.create_string_buffer(n.value)
+        check(lib.ite_mps_save(self.h, buf, n.value), self.ctx.h)
+        return buf.raw
+
+    def to_dense(self):
+        """The state as a dense vector (ite_mps_to_dense; d^N <= 2^24)."""
+        out = np.zeros(2 * self.d ** self.N)
+        check(lib.ite_mps_to_dense(self.ctx.h, self.h, _dptr(out), out.size), self.ctx.h)
+        return out.view(np.complex128)
+
     def bond_dims(self):
         chi = np.zeros(self.N + 1, np.int32)
         n = C.c_size_t()
@@ -183,6 +198,14 @@ def mps_create(ctx, tensors, chi_cap):
     check(lib.ite_mps_create(ctx.h, N, d, chi.ctypes.data_as(C.POINTER(C.c_int)), _dptr(flat),
                              chi_cap, C.byref(h)), ctx.h)
     return MPS(ctx, h, N, d)
+
+
+def mps_load(ctx, data):
+    """A new MPS from a checkpoint made by MPS.save (ite_mps_load)."""
+    h = C.c_void_p()
+    check(lib.ite_mps_load(ctx.h, data, len(data), C.byref(h)), ctx.h)
+    head = np.frombuffer(data[8:24], dtype=np.int64)                # N, d
+    return MPS(ctx, h, int(head[0]), int(head[1]))
 
 
 def mps_create_product(ctx, site_vecs, chi_cap):

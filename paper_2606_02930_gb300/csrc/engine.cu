@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -479,7 +480,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
 }
 
 // One GMRES cycle on (alpha I + c H_eff) X = B; X updated in place.
-ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
+ite_status gmres_cycle(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
                        const cplx* R, const cplx* B, cplx* X, cplx alpha, cplx c, int m,
                        double local_tol, int* steps, double* res) {
   Scope sc(ctx, P_SOLVE);
@@ -838,6 +839,26 @@ struct SweepStats {
   int steps = 0;
 };
 
+// Up to `cycles` GMRES(m) cycles, each restarted from the last iterate; a
+// cycle that ends before m steps (breakdown, or the relative residual at
+// local_tol) ends the solve.  steps: all cycles' Arnoldi steps; res: the
+// last relative residual.
+ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
+                       const cplx* R, const cplx* B, cplx* X, cplx alpha, cplx c, int m,
+                       int cycles, double local_tol, int* steps, double* res) {
+  int total = 0;
+  double r = 0.0;
+  for (int cy = 0; cy < std::max(1, cycles); ++cy) {
+    int k = 0;
+    CS(gmres_cycle(ctx, H, i, chl, chr, L, R, B, X, alpha, c, m, local_tol, &k, &r));
+    total += k;
+    if (k < m || (local_tol > 0.0 && r <= local_tol)) break;
+  }
+  if (steps) *steps = total;
+  if (res) *res = r;
+  return ITE_OK;
+}
+
 // Two-site sweep solving (alpha I + c H) x = b, or (fit mode) x ~ alpha b + beta H b.
 ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, cplx alpha, cplx cbeta,
                  int chi_max, double cutoff, const ite_solver_opts& o, SweepStats& stats) {
@@ -869,7 +890,7 @@ ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, cplx al
         int steps = 0;
         double res = 0.0;
         CS(local_solve(ctx, H, i, chl, chr, e.LE[i], e.RE[i + 2], B, X, alpha, cbeta, o.krylov_dim,
-                       o.local_tol, &steps, &res));
+                       o.max_cycles, o.local_tol, &steps, &res));
         stats.steps += steps;
         stats.max_res = std::max(stats.max_res, res);
       } else {
@@ -1040,6 +1061,7 @@ extern "C" {
 void ite_solver_opts_default(ite_solver_opts* o) {
   if (!o) return;
   o->krylov_dim = 10;
+  o->max_cycles = 1;
   o->sweeps = 1;
   o->local_tol = 0.0;
   o->sweep_tol = 0.0;
@@ -1728,6 +1750,96 @@ ite_status ite_mps_set(ite_ctx ctx, ite_mps m, const int* chi, const double* A) 
   return sync(ctx);
 }
 
+namespace {
+constexpr char kMpsMagic[8] = {'I', 'T', 'E', 'M', 'P', 'S', '0', '1'};
+}
+
+ite_status ite_mps_bytes(ite_mps m, size_t* bytes) {
+  if (!m || !bytes) return ITE_EINVAL;
+  size_t nd = 0;
+  ite_mps_bond_dims(m, nullptr, &nd);
+  *bytes = 8 + 8 * (3 + (size_t)m->N + 1) + nd * sizeof(double);
+  return ITE_OK;
+}
+
+ite_status ite_mps_save(ite_mps m, void* buf, size_t cap) {
+  size_t need = 0;
+  if (!m || !buf || ite_mps_bytes(m, &need) != ITE_OK) return ITE_EINVAL;
+  if (cap < need) return fail(m->ctx, ITE_EINVAL, "checkpoint buffer too small");
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, kMpsMagic, 8);
+  std::vector<long long> head = {m->N, m->d, m->chi_cap};
+  for (int b = 0; b <= m->N; ++b) head.push_back(m->chi[b]);
+  std::memcpy(p + 8, head.data(), head.size() * 8);
+  const size_t off = 8 + head.size() * 8;
+  return ite_mps_get(m->ctx, m, reinterpret_cast<double*>(p + off), (cap - off) / sizeof(double));
+}
+
+ite_status ite_mps_load(ite_ctx ctx, const void* buf, size_t len, ite_mps* out) {
+  if (!ctx || !buf || !out) return ITE_EINVAL;
+  *out = nullptr;
+  const char* p = static_cast<const char*>(buf);
+  if (len < 8 + 3 * 8 || std::memcmp(p, kMpsMagic, 8) != 0)
+    return fail(ctx, ITE_EINVAL, "not an MPS checkpoint");
+  long long N = 0, d = 0, cap = 0;
+  std::memcpy(&N, p + 8, 8);
+  std::memcpy(&d, p + 16, 8);
+  std::memcpy(&cap, p + 24, 8);
+  if (N < 1 || N > (1 << 20) || d < 1 || d > 16 || cap < 1 || cap > (1 << 20))
+    return fail(ctx, ITE_EINVAL, "inconsistent MPS checkpoint header");
+  const size_t off = 8 + 8 * (3 + (size_t)N + 1);
+  if (len < off) return fail(ctx, ITE_EINVAL, "truncated MPS checkpoint");
+  std::vector<int> chi(N + 1);
+  size_t nd = 0;
+  for (long long b = 0; b <= N; ++b) {
+    long long c = 0;
+    std::memcpy(&c, p + 32 + 8 * b, 8);
+    if (c < 1 || c > cap) return fail(ctx, ITE_EINVAL, "inconsistent MPS checkpoint bond dimension");
+    chi[b] = (int)c;
+  }
+  for (long long i = 0; i < N; ++i) nd += 2 * (size_t)chi[i] * d * chi[i + 1];
+  if (len < off + nd * sizeof(double)) return fail(ctx, ITE_EINVAL, "truncated MPS checkpoint");
+  // the tensors may sit at any alignment in the caller's buffer
+  std::vector<double> A(nd);
+  std::memcpy(A.data(), p + off, nd * sizeof(double));
+  return ite_mps_create(ctx, (int)N, (int)d, chi.data(), A.data(), (int)cap, out);
+}
+
+ite_status ite_mps_to_dense(ite_ctx ctx, ite_mps m, double* out, size_t cap_doubles) {
+  if (!ctx || !m || !out) return ITE_EINVAL;
+  double logsz = m->N * std::log2((double)m->d);
+  if (logsz > 24.0) return fail(ctx, ITE_EINVAL, "state too large for a dense vector");
+  size_t dim = 1;
+  for (int i = 0; i < m->N; ++i) dim *= (size_t)m->d;
+  if (cap_doubles < 2 * dim) return fail(ctx, ITE_EINVAL, "output buffer too small");
+  size_t nd = 0;
+  ite_mps_bond_dims(m, nullptr, &nd);
+  std::vector<double> A(nd);
+  CS(ite_mps_get(ctx, m, A.data(), nd));
+  // v[prefix][bond] grows one site at a time: v' = v . A_i (prefix x d)
+  typedef std::complex<double> z;
+  std::vector<z> v(1, z(1.0, 0.0)), w;
+  size_t rows = 1, pos = 0;
+  for (int i = 0; i < m->N; ++i) {
+    const int cl = m->chi[i], cr = m->chi[i + 1], d = m->d;
+    const z* Ai = reinterpret_cast<const z*>(A.data()) + pos;
+    if ((double)rows * d * cr > (double)(1u << 28)) return fail(ctx, ITE_EINVAL, "intermediate too large");
+    w.assign(rows * d * cr, z(0.0, 0.0));
+    for (size_t r = 0; r < rows; ++r)
+      for (int a = 0; a < cl; ++a) {
+        const z va = v[r * cl + a];
+        if (va == z(0.0, 0.0)) continue;
+        for (int s = 0; s < d; ++s)
+          for (int b = 0; b < cr; ++b) w[(r * d + s) * cr + b] += va * Ai[((size_t)a * d + s) * cr + b];
+      }
+    v.swap(w);
+    rows *= d;
+    pos += (size_t)cl * d * cr;
+  }
+  std::memcpy(out, v.data(), 2 * dim * sizeof(double));
+  return ITE_OK;
+}
+
 ite_status ite_mps_copy(ite_ctx ctx, ite_mps src, ite_mps dst) {
   if (!ctx || !src || !dst || src->N != dst->N || src->d != dst->d) return ITE_EINVAL;
   for (int b = 0; b <= src->N; ++b)
@@ -2043,7 +2155,7 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   int s = 0;
   double r = 0.0;
   CS(local_solve(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B, (cplx*)X,
-                 C(alpha), C(c), krylov_dim, local_tol, &s, &r));
+                 C(alpha), C(c), krylov_dim, 1, local_tol, &s, &r));
   if (steps) *steps = s;
   if (rel_res) *rel_res = r;
   return kernel_finish(ctx);

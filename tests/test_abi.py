@@ -69,6 +69,11 @@ def test_invalid_arguments_fail_cleanly():
                               ctypes.byref(out)) != _lib.ITE_OK
     assert lib.ite_last_error(None) == b"null context"
     assert lib.ite_k_barrier_selftest(None, 4, 1) == _lib.ITE_EINVAL
+    n = ctypes.c_size_t()
+    assert lib.ite_mps_bytes(None, ctypes.byref(n)) == _lib.ITE_EINVAL
+    assert lib.ite_mps_save(None, b"x" * 64, 64) == _lib.ITE_EINVAL
+    assert lib.ite_mps_load(None, b"ITEMPS01", 8, ctypes.byref(out)) == _lib.ITE_EINVAL
+    assert lib.ite_mps_to_dense(None, None, None, 0) == _lib.ITE_EINVAL
 
 
 @pytest.mark.parametrize("q", [1, 2, 3, 4])

@@ -74,6 +74,26 @@ def test_heisenberg_n10_backward_euler_fixed_mode(api, ctx):
     assert all(b <= a + 1e-10 for a, b in zip(es, es[1:]))
 
 
+def test_restarted_gmres_steps_match_oracle(api, ctx):
+    # three GMRES(4) cycles per local solve, each restarted from the last
+    # iterate, on N = 10 with the trapezoid rule: the same states, energies
+    # and Arnoldi step counts as the oracle's restarted solve
+    N = 10
+    Ws = ompo.heisenberg_mpo(N)
+    e0 = np.linalg.eigvalsh(ed.heisenberg_hamiltonian(N))[0]
+    H = api.mpo_create_heisenberg(ctx, N)
+    psi0 = omps.product_state(inputs.random_product_state(N, 2, 1001))
+    nodes = ogrid.geometric_grid(1e-2, 1e1, 6)
+    opts = api.solver_opts(krylov_dim=4, max_cycles=3)
+    pairs = run_pair(api, ctx, Ws, H, psi0, nodes, "tr", 32, 0.0, shift=e0, opts=opts,
+                     okw=dict(krylov_dim=4, max_cycles=3))
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= TOL * abs(oinfo.energy)
+        assert infid(ost, gst) <= TOL
+        assert ginfo["gmres_steps"] == oinfo.gmres_steps
+    assert max(o.gmres_steps for _, o, _, _ in pairs) > 2 * (N - 1) * 4   # restarts ran
+
+
 def test_heisenberg_n10_evolve_loggrid_equals_steps(api, ctx):
     N = 10
     e0 = np.linalg.eigvalsh(ed.heisenberg_hamiltonian(N))[0]

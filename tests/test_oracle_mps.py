@@ -196,6 +196,31 @@ def test_gmres_is_invariant_under_scaling():
         assert abs(rs - r1) < 1e-12
 
 
+def test_restarted_gmres():
+    # one cycle is plain GMRES; on a well-conditioned system restarted
+    # GMRES(4) reaches the solution that a dense solve gives, with a
+    # residual that never grows from cycle to cycle
+    rng = np.random.default_rng(74)
+    n = 40
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = 3.0 * np.eye(n) + 0.05 * (G + G.conj().T)             # spectrum in about [2, 4]
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x0 = np.zeros(n, complex)
+    mv = lambda v: A @ v
+    x1, (k1, r1) = ls.gmres_restarted(mv, b, x0, 4, 1)
+    xg, (kg, rg) = ls.gmres(mv, b, x0, 4)
+    assert k1 == kg == 4 and np.array_equal(x1, xg) and r1 == rg
+    res = []
+    for cycles in (1, 2, 4, 8, 60):
+        _, (_, r) = ls.gmres_restarted(mv, b, x0, 4, cycles)
+        res.append(r)
+    assert all(b_ <= a_ * (1 + 1e-12) + 1e-14 for a_, b_ in zip(res, res[1:]))
+    x, (k, r) = ls.gmres_restarted(mv, b, x0, 4, 60, local_tol=1e-13)
+    want = np.linalg.solve(A, b)
+    assert r <= 1e-13 and k < 4 * 60
+    assert np.linalg.norm(x - want) < 1e-11 * np.linalg.norm(want)
+
+
 def test_choose_rank_rules():
     S = np.array([1.0, 0.5, 0.25, 1e-3, 1e-6, 0.0])
     assert ls.choose_rank(S, 10, 0.0)[0] == 5          # exact zero dropped (weight floor)
