@@ -166,3 +166,32 @@ def test_draw_never_takes_a_state_of_zero_probability():
     config, p = metts.sample(psi, [1.0 - 2.0 ** -53])
     assert config == [2]
     assert abs(p - amp[2] ** 2 / np.sum(amp ** 2)) < 1e-15
+
+
+def test_impurity_chain_samples_its_sector_thermal_state():
+    # The dense METTS chain of the impurity model (2 bath sites) with
+    # collapses in the occupation basis keeps N_up and N_down of its start
+    # state; its energy and impurity double occupancy (the paper's METTS
+    # observable) average to that sector's thermal values at beta = 8.
+    eps, V = inputs.flat_band_bath(2)
+    H = ed.anderson_hamiltonian(-0.15, 0.3, eps, V)
+    d, N = 4, 3
+
+    def n_up_down(i):
+        digits = [(i // d ** (N - 1 - k)) % d for k in range(N)]
+        return sum(s in (1, 3) for s in digits), sum(s in (2, 3) for s in digits)
+
+    sector = [i for i in range(d ** N) if n_up_down(i) == (2, 1)]         # start state up, down, up
+    docc = np.diag([1.0 if (i // d ** (N - 1)) % d == 3 else 0.0 for i in range(d ** N)])
+    beta = 8.0
+    ev, U = np.linalg.eigh(H[np.ix_(sector, sector)])
+    w = np.exp(-beta * (ev - ev[0]))
+    e_th = np.sum(w * ev) / np.sum(w)
+    Dsec = docc[np.ix_(sector, sector)]
+    d_th = np.sum(w * np.real(np.einsum("ij,ik,kj->j", U.conj(), Dsec, U))) / np.sum(w)
+    us = np.random.default_rng(41).random((30000, N))
+    e, dd = metts.dense_metts_chain(H, d, N, [1, 2, 1], beta, us, obs_dense=docc)
+    m, err = _chain_mean_and_error(e, burn=200, block=500)
+    assert abs(m - e_th) < 5 * err and err < 1e-3
+    m, err = _chain_mean_and_error(dd, burn=200, block=500)
+    assert abs(m - d_th) < 5 * err and err < 1e-3
