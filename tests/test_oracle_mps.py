@@ -316,3 +316,61 @@ def test_explicit_steps_equal_dense_at_full_bond_dimension(scheme):
         x, info = step.implicit_step(Ws, x, dt, scheme, e0, 8, 0.0, fit_sweeps=4)
         assert ed.infidelity(v, mps.to_dense(x)) < 1e-12
         assert abs(ed.energy(H, v) - info.energy) < 1e-12 * abs(ed.energy(H, v))
+
+
+def _evolve_long(Ws, psi, chi, steps):
+    psi = mps.copy(psi)
+    psi[0] = psi[0] / mps.norm(psi)
+    s = mps.expect_mpo(psi, Ws)
+    nodes = grid.geometric_grid(1e-1, 2e2, steps)
+    for k in range(1, len(nodes)):
+        psi, info = step.implicit_step(Ws, psi, nodes[k] - nodes[k - 1], "be", s, chi, 1e-12,
+                                       local_tol=1e-12, sweeps=3, sweep_tol=1e-12, krylov_dim=16)
+        s = info.energy
+    return s
+
+
+def test_long_time_limit_of_the_open_xx_chain_is_free_fermions():
+    # J_z = 0 maps by Jordan-Wigner to free fermions hopping with amplitude
+    # J/2: from the Neel state (S^z = 0, half filling) the evolution reaches
+    # the sum of the negative single-particle energies
+    N = 16
+    hop = np.diag(np.full(N - 1, 0.5), 1)
+    lev = np.linalg.eigvalsh(hop + hop.T)
+    neel = np.zeros((N, 2))
+    neel[np.arange(N), np.arange(N) % 2] = 1.0
+    e = _evolve_long(mpo.heisenberg_mpo(N, 1.0, 0.0), mps.product_state(neel), 24, 14)
+    assert abs(e - np.sum(lev[lev < 0])) < 1e-6 * abs(np.sum(lev[lev < 0]))
+
+
+def _u0_levels(nb):
+    eps, V = inputs.flat_band_bath(nb)
+    h1 = np.diag(np.concatenate([[0.0], eps]))
+    h1[0, 1:] = h1[1:, 0] = V
+    return eps, V, np.linalg.eigvalsh(h1)
+
+
+def test_long_time_limit_of_the_u0_impurity_is_free_fermions():
+    # U = 0, eps_d = 0: the ground energy is twice the sum of the negative
+    # levels of the one-body impurity + bath matrix (both spins); a generic
+    # product state reaches it
+    nb = 7
+    eps, V, lev = _u0_levels(nb)
+    Ws = mpo.anderson_mpo(0.0, 0.0, eps, V)
+    psi = mps.product_state(inputs.random_product_state(nb + 1, 4, 7))
+    e = _evolve_long(Ws, psi, 32, 14)
+    assert abs(e - 2 * np.sum(lev[lev < 0])) < 1e-6 * abs(2 * np.sum(lev[lev < 0]))
+
+
+def test_two_site_updates_keep_the_bond_sectors_of_an_occupation_product_state():
+    # From a product of occupation states the one-sweep two-site evolution of
+    # the star-geometry impurity cannot open the bond sectors that the ground
+    # state of its particle sector needs: it settles far above that energy
+    # (in exact arithmetic; rounding or a later seed may open them).
+    nb = 7
+    eps, V, lev = _u0_levels(nb)
+    Ws = mpo.anderson_mpo(0.0, 0.0, eps, V)
+    occ = np.zeros((nb + 1, 4))
+    occ[np.arange(nb + 1), [1, 2] * ((nb + 1) // 2)] = 1.0            # 4 up, 4 down
+    e = _evolve_long(Ws, mps.product_state(occ), 32, 8)
+    assert e > 2 * np.sum(lev[: (nb + 1) // 2]) + 1.0
