@@ -59,7 +59,9 @@ typedef enum {
   ITE_EINVAL = 1,
   ITE_ENOMEM = 2,
   ITE_ESINGULAR = 3,
-  ITE_ENOTCONV = 4,
+  ITE_ENOTCONV = 4,   /* reserved: fixed-effort solves (the paper's one sweep, one
+                         GMRES cycle) are not failures and return ITE_OK, with
+                         their residuals in ite_step_info                       */
   ITE_ETIMEOUT = 5,
   ITE_ECUDA = 6,
   ITE_PENDING = 7     /* a served job has not finished yet (ite_server.h) */
