@@ -1823,7 +1823,8 @@ ite_status ite_mps_to_dense(ite_ctx ctx, ite_mps m, double* out, size_t cap_doub
   for (int i = 0; i < m->N; ++i) {
     const int cl = m->chi[i], cr = m->chi[i + 1], d = m->d;
     const z* Ai = reinterpret_cast<const z*>(A.data()) + pos;
-    if ((double)rows * d * cr > (double)(1u << 28)) return fail(ctx, ITE_EINVAL, "intermediate too large");
+    // a minimal MPS keeps every intermediate within d^N <= 2^24 entries
+    if ((double)rows * d * cr > (double)(1u << 26)) return fail(ctx, ITE_EINVAL, "intermediate too large");
     w.assign(rows * d * cr, z(0.0, 0.0));
     for (size_t r = 0; r < rows; ++r)
       for (int a = 0; a < cl; ++a) {
