@@ -205,6 +205,13 @@ void ite_mps_destroy(ite_mps mps);
 ite_status ite_mps_bytes(ite_mps mps, size_t* bytes);
 ite_status ite_mps_save(ite_mps mps, void* buf, size_t cap);
 ite_status ite_mps_load(ite_ctx ctx, const void* buf, size_t len, ite_mps* out);
+/* Reads a checkpoint's header without a device: N, d, chi_cap, the bond
+ * dimensions (chi_out[chi_len >= N+1]) and the number of doubles of its
+ * tensors; each output may be NULL.  ITE_EINVAL for a wrong magic, a header
+ * out of range (1 <= N, chi_cap <= 2^20, 1 <= d <= 16, 1 <= chi[b] <=
+ * chi_cap, chi[0] = chi[N] = 1) or a buffer shorter than the image. */
+ite_status ite_mps_checkpoint_info(const void* buf, size_t len, int* N, int* d, int* chi_cap,
+                                   int* chi_out, size_t chi_len, size_t* n_doubles);
 /* The state as a dense vector psi[s_0 ... s_{N-1}] (s_0 most significant;
  * interleaved complex; cap_doubles >= 2 d^N), contracted on the host from
  * the tensors: a check for small systems (d^N <= 2^24), ITE_EINVAL above. */

@@ -136,6 +136,8 @@ SIGNATURES = {
     "ite_mps_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),
     "ite_mps_save": (_i, [_vp, _vp, C.c_size_t]),
     "ite_mps_load": (_i, [_vp, _vp, C.c_size_t, C.POINTER(_vp)]),
+    "ite_mps_checkpoint_info": (_i, [_vp, C.c_size_t, _pi, _pi, _pi, _pi, C.c_size_t,
+                                     C.POINTER(C.c_size_t)]),
     "ite_mps_to_dense": (_i, [_vp, _vp, _pd, C.c_size_t]),
     "ite_job_device_bytes": (_sz, [C.POINTER(ite_job)]),
     "ite_server_create": (_i, [_i, _i, _sz, C.POINTER(_vp)]),

@@ -200,12 +200,24 @@ def mps_create(ctx, tensors, chi_cap):
     return MPS(ctx, h, N, d)
 
 
+def checkpoint_info(data):
+    """(N, d, chi_cap, bond dimensions, doubles of the tensors) of a
+    checkpoint, read on the host (ite_mps_checkpoint_info)."""
+    N, d, cap, nd = C.c_int(), C.c_int(), C.c_int(), C.c_size_t()
+    check(lib.ite_mps_checkpoint_info(data, len(data), C.byref(N), C.byref(d), C.byref(cap), None,
+                                      0, C.byref(nd)))
+    chi = np.zeros(N.value + 1, np.int32)
+    check(lib.ite_mps_checkpoint_info(data, len(data), None, None, None,
+                                      chi.ctypes.data_as(C.POINTER(C.c_int)), chi.size, None))
+    return N.value, d.value, cap.value, chi, nd.value
+
+
 def mps_load(ctx, data):
     """A new MPS from a checkpoint made by MPS.save (ite_mps_load)."""
+    N, d = checkpoint_info(data)[:2]
     h = C.c_void_p()
     check(lib.ite_mps_load(ctx.h, data, len(data), C.byref(h)), ctx.h)
-    head = np.frombuffer(data[8:24], dtype=np.int64)                # N, d
-    return MPS(ctx, h, int(head[0]), int(head[1]))
+    return MPS(ctx, h, N, d)
 
 
 def mps_create_product(ctx, site_vecs, chi_cap):

@@ -1775,34 +1775,53 @@ ite_status ite_mps_save(ite_mps m, void* buf, size_t cap) {
   return ite_mps_get(m->ctx, m, reinterpret_cast<double*>(p + off), (cap - off) / sizeof(double));
 }
 
-ite_status ite_mps_load(ite_ctx ctx, const void* buf, size_t len, ite_mps* out) {
-  if (!ctx || !buf || !out) return ITE_EINVAL;
-  *out = nullptr;
+ite_status ite_mps_checkpoint_info(const void* buf, size_t len, int* N_out, int* d_out,
+                                   int* chi_cap_out, int* chi_out, size_t chi_len,
+                                   size_t* n_doubles) {
+  if (!buf) return ITE_EINVAL;
   const char* p = static_cast<const char*>(buf);
-  if (len < 8 + 3 * 8 || std::memcmp(p, kMpsMagic, 8) != 0)
-    return fail(ctx, ITE_EINVAL, "not an MPS checkpoint");
+  if (len < 8 + 3 * 8 || std::memcmp(p, kMpsMagic, 8) != 0) return ITE_EINVAL;
   long long N = 0, d = 0, cap = 0;
   std::memcpy(&N, p + 8, 8);
   std::memcpy(&d, p + 16, 8);
   std::memcpy(&cap, p + 24, 8);
-  if (N < 1 || N > (1 << 20) || d < 1 || d > 16 || cap < 1 || cap > (1 << 20))
-    return fail(ctx, ITE_EINVAL, "inconsistent MPS checkpoint header");
+  if (N < 1 || N > (1 << 20) || d < 1 || d > 16 || cap < 1 || cap > (1 << 20)) return ITE_EINVAL;
   const size_t off = 8 + 8 * (3 + (size_t)N + 1);
-  if (len < off) return fail(ctx, ITE_EINVAL, "truncated MPS checkpoint");
+  if (len < off) return ITE_EINVAL;
   std::vector<int> chi(N + 1);
   size_t nd = 0;
   for (long long b = 0; b <= N; ++b) {
     long long c = 0;
     std::memcpy(&c, p + 32 + 8 * b, 8);
-    if (c < 1 || c > cap) return fail(ctx, ITE_EINVAL, "inconsistent MPS checkpoint bond dimension");
+    if (c < 1 || c > cap) return ITE_EINVAL;
     chi[b] = (int)c;
   }
+  if (chi[0] != 1 || chi[N] != 1) return ITE_EINVAL;
   for (long long i = 0; i < N; ++i) nd += 2 * (size_t)chi[i] * d * chi[i + 1];
-  if (len < off + nd * sizeof(double)) return fail(ctx, ITE_EINVAL, "truncated MPS checkpoint");
+  if ((len - off) / sizeof(double) < nd) return ITE_EINVAL;
+  if (chi_out && chi_len < (size_t)N + 1) return ITE_EINVAL;
+  if (N_out) *N_out = (int)N;
+  if (d_out) *d_out = (int)d;
+  if (chi_cap_out) *chi_cap_out = (int)cap;
+  if (chi_out) std::copy(chi.begin(), chi.end(), chi_out);
+  if (n_doubles) *n_doubles = nd;
+  return ITE_OK;
+}
+
+ite_status ite_mps_load(ite_ctx ctx, const void* buf, size_t len, ite_mps* out) {
+  if (!ctx || !buf || !out) return ITE_EINVAL;
+  *out = nullptr;
+  int N = 0, d = 0, cap = 0;
+  size_t nd = 0;
+  if (ite_mps_checkpoint_info(buf, len, &N, &d, &cap, nullptr, 0, &nd) != ITE_OK)
+    return fail(ctx, ITE_EINVAL, "not a valid MPS checkpoint (magic, header or length)");
+  std::vector<int> chi(N + 1);
+  ite_mps_checkpoint_info(buf, len, nullptr, nullptr, nullptr, chi.data(), chi.size(), nullptr);
+  const size_t off = 8 + 8 * (3 + (size_t)N + 1);
   // the tensors may sit at any alignment in the caller's buffer
   std::vector<double> A(nd);
-  std::memcpy(A.data(), p + off, nd * sizeof(double));
-  return ite_mps_create(ctx, (int)N, (int)d, chi.data(), A.data(), (int)cap, out);
+  std::memcpy(A.data(), static_cast<const char*>(buf) + off, nd * sizeof(double));
+  return ite_mps_create(ctx, N, d, chi.data(), A.data(), cap, out);
 }
 
 ite_status ite_mps_to_dense(ite_ctx ctx, ite_mps m, double* out, size_t cap_doubles) {

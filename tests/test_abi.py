@@ -127,3 +127,35 @@ def test_struct_layouts_match_the_headers():
         cls = structs[name]
         want = C.sizeof(cls) if field == "size" else getattr(cls, field).offset
         assert int(value) == want, (name, field)
+
+
+def _checkpoint(N, d, cap, chi, tensors_doubles, magic=b"ITEMPS01"):
+    import numpy as np
+    head = np.array([N, d, cap] + list(chi), dtype=np.int64).tobytes()
+    return magic + head + np.arange(tensors_doubles, dtype=np.float64).tobytes()
+
+
+def test_checkpoint_header_is_read_without_a_device():
+    # the byte image ite_mps_save writes (magic, N, d, chi_cap, chi[0..N],
+    # tensors), built here by hand and read back on the host
+    from paper_2606_02930_gb300 import api, _lib
+    chi = [1, 2, 4, 2, 1]
+    nd = 2 * sum(chi[i] * 2 * chi[i + 1] for i in range(4))
+    img = _checkpoint(4, 2, 8, chi, nd)
+    N, d, cap, got_chi, n = api.checkpoint_info(img)
+    assert (N, d, cap, got_chi.tolist(), n) == (4, 2, 8, chi, nd)
+    info = _lib.lib.ite_mps_checkpoint_info
+    bad = [
+        _checkpoint(4, 2, 8, chi, nd, magic=b"ITEMPS02"),     # wrong magic
+        img[:30],                                            # truncated header
+        img[:-8],                                            # truncated tensors
+        _checkpoint(4, 2, 8, [1, 2, 9, 2, 1], 10 ** 4),      # bond above the capacity
+        _checkpoint(4, 2, 8, [2, 2, 4, 2, 1], 10 ** 4),      # open boundary bond
+        _checkpoint(0, 2, 8, [1], 0),                        # no sites
+        _checkpoint(4, 17, 8, chi, 10 ** 4),                 # d out of range
+    ]
+    for b in bad:
+        assert info(b, len(b), None, None, None, None, 0, None) == _lib.ITE_EINVAL
+    # too little room for the bond dimensions
+    out = (ctypes.c_int * 4)()
+    assert info(img, len(img), None, None, None, out, 4, None) == _lib.ITE_EINVAL
