@@ -159,3 +159,33 @@ def test_checkpoint_header_is_read_without_a_device():
     # too little room for the bond dimensions
     out = (ctypes.c_int * 4)()
     assert info(img, len(img), None, None, None, out, 4, None) == _lib.ITE_EINVAL
+
+
+def test_checkpoint_parser_survives_arbitrary_bytes():
+    # random byte strings and randomly mutated valid images: the parser
+    # returns ITE_OK or ITE_EINVAL and never reads past the buffer's end
+    # (an accepted image's tensors fit in it)
+    import numpy as np
+    from paper_2606_02930_gb300 import _lib
+    info = _lib.lib.ite_mps_checkpoint_info
+    rng = np.random.default_rng(77)
+    chi = [1, 2, 4, 4, 2, 1]
+    nd = 2 * sum(chi[i] * 2 * chi[i + 1] for i in range(5))
+    valid = _checkpoint(5, 2, 4, chi, nd)
+    accepted = 0
+    for trial in range(3000):
+        if trial % 2:
+            img = bytearray(valid)
+            for _ in range(rng.integers(1, 6)):
+                img[rng.integers(len(img))] = rng.integers(256)
+            img = bytes(img[: rng.integers(1, len(img) + 1)])
+        else:
+            img = b"ITEMPS01" + rng.bytes(int(rng.integers(0, 200)))
+        N, d, cap, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        st = info(img, len(img), ctypes.byref(N), ctypes.byref(d), ctypes.byref(cap), None, 0,
+                  ctypes.byref(n))
+        assert st in (_lib.ITE_OK, _lib.ITE_EINVAL)
+        if st == _lib.ITE_OK:
+            accepted += 1
+            assert 8 + 8 * (3 + N.value + 1) + 8 * n.value <= len(img)
+    assert accepted > 0
