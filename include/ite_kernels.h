@@ -113,7 +113,7 @@ ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double*
                        int conjB, double* C, long long ldc, const double alpha[2],
                        const double beta[2]);
 
-/* Same result as ite_k_heff, for callers that cannot allocate device memory
+/* Same result as ite_k_heff in FP64 mode, for callers that cannot allocate device memory
  * at call time (cudaMalloc can synchronise the whole device, the process may
  * have given all device memory to another pool, or allocation calls may be
  * forbidden where the caller runs).  This call allocates nothing: its two
@@ -126,7 +126,10 @@ ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double*
  * host threads) race and must be ordered by the caller.  Nothing in the array
  * needs to start at zero.  The first call on a device looks up the array's
  * device address, so make it before any stream capture.  Synchronises the
- * context stream before returning. */
+ * context stream before returning.  Always computes on the FP64 pipe, whatever
+ * ite_ctx_set_kernel_precision selected (the tensor-core path needs slice
+ * buffers sized per call).  Makes the context's device current for the call
+ * and gives the calling thread its previous current device back. */
 ite_status ite_k_heff_noalloc(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
                               int chr_ket, int chr_bra, const double* L, const double* R,
                               const double* X, double* Y, const double alpha[2],

@@ -6,9 +6,11 @@
 // matvec: cudaMalloc may synchronise the whole device (stalling other streams
 // of a latency-critical serving loop), the process may have handed all device
 // memory to another pool, or the caller runs where the CUDA runtime forbids
-// allocation calls.  For them this entry point computes exactly what
-// ite_k_heff computes, with the same kernels, using a scratch array that is
-// part of the loaded library image.
+// allocation calls.  For them this entry point computes the matvec that
+// ite_k_heff computes in FP64 mode, with the same FP64 kernels, using a scratch
+// array that is part of the loaded library image.  It always runs on the FP64
+// pipe: the context's kernel precision (ite_ctx_set_kernel_precision) does not
+// apply, because the tensor-core path needs slice buffers sized per call.
 //
 // The array is 2 x kScratchComplex complex doubles (2 x 8 MiB = 16 MiB) and is
 // held by every GPU that loads this library until the process exits.  Every
@@ -58,6 +60,24 @@ cudaError_t scratch_address(int device, cplx** out) {
   return cudaSuccess;
 }
 
+// Makes `dev` current for the lifetime of the guard and gives the calling
+// thread its previous current device back on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 extern "C" ite_status ite_k_heff_noalloc(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
@@ -80,10 +100,8 @@ extern "C" ite_status ite_k_heff_noalloc(ite_ctx ctx, ite_mpo H, int i, int chl_
     return internal_fail(ctx, ITE_EINVAL,
                          "ite_k_heff_noalloc: D*chl_bra*d^2*chr_ket exceeds the static scratch of "
                          "524288 complex numbers per intermediate");
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) {
-    if (cudaSetDevice(dev) != cudaSuccess) return internal_fail(ctx, ITE_ECUDA, "cudaSetDevice failed");
-  }
+  DeviceGuard guard(dev);
+  if (!guard.ok) return internal_fail(ctx, ITE_ECUDA, "cannot make the context's device current");
   cplx* base = nullptr;
   if (scratch_address(dev, &base) != cudaSuccess)
     return internal_fail(ctx, ITE_ECUDA, "cudaGetSymbolAddress of the static scratch failed");

@@ -1,23 +1,27 @@
 """The allocation-free H_eff entry point (ite_k_heff_noalloc) against the
-regular one (ite_k_heff).
+oracle's two-site matvec.
 
 Callers that cannot allocate device memory when they need a matvec (a
 latency-critical loop that must not let cudaMalloc synchronise the device, or
 a process whose device memory is all owned by another pool) use the variant
-whose scratch is a fixed array inside the library.  This file is collected
-last so that a run stopping at its first failure has run every other test."""
+whose scratch is a fixed array inside the library.  It always computes on the
+FP64 pipe, whatever kernel precision the context carries, so its output is
+held to the FP64 bar against the oracle in both precision settings.  This file
+is collected last so that a run stopping at its first failure has run every
+other test."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
-from oracle import mpo as ompo
+from oracle import linsolve as ls, mpo as ompo
 from paper_2606_02930_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_heff_matches_regular_entry_point():
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_noalloc_heff_matches_oracle(precision):
     import __graft_entry__
     __graft_entry__.build()
     import torch
@@ -26,6 +30,7 @@ def test_noalloc_heff_matches_regular_entry_point():
 
     lib = _lib.lib
     ctx = api.ctx_create(0)
+    api.set_kernel_precision(ctx, precision)
     eps, V = inputs.flat_band_bath(5)
     cases = [("heisenberg", ompo.heisenberg_mpo(12), (64, 64, 64, 64)),
              ("anderson", ompo.anderson_mpo(-0.15, 0.3, eps, V), (20, 24, 28, 16))]
@@ -36,27 +41,27 @@ def test_noalloc_heff_matches_regular_entry_point():
         D0, D2, d = Ws[i].shape[0], Ws[i + 1].shape[3], Ws[i].shape[1]
         rng = np.random.default_rng(len(name))
         for call in range(2):      # two calls in a row share the static scratch
-            L = to_dev(L_to_lib(crandn(rng, chlB, D0, chlK)))
-            R = to_dev(R_to_lib(crandn(rng, chrB, D2, chrK)))
-            X = to_dev(crandn(rng, chlK, d, d, chrK))
-            Z = to_dev(crandn(rng, chlB, d, d, chrB))
-            alpha = np.array([0.3, -0.2])
-            gamma = np.array([1.5, 0.0])
-            Y_ref = torch.zeros((chlB, d, d, chrB), dtype=torch.complex128, device="cuda")
+            Lo, Ro = crandn(rng, chlB, D0, chlK), crandn(rng, chrB, D2, chrK)
+            Xo, Zo = crandn(rng, chlK, d, d, chrK), crandn(rng, chlB, d, d, chrB)
+            alpha, gamma = 0.3 - 0.2j, 1.5
+            want = alpha * ls.heff_apply(Lo, Ws[i], Ws[i + 1], Ro, Xo) + gamma * Zo
+            L, R, X, Z = to_dev(L_to_lib(Lo)), to_dev(R_to_lib(Ro)), to_dev(Xo), to_dev(Zo)
             Y = torch.full((chlB, d, d, chrB), float("nan"), dtype=torch.complex128, device="cuda")
-            args = lambda out: (ctx.h, H.h, i, chlB, chlK, chrK, chrB, C.c_void_p(L.data_ptr()),
-                                C.c_void_p(R.data_ptr()), C.c_void_p(X.data_ptr()),
-                                C.c_void_p(out.data_ptr()), alpha.ctypes.data_as(C.POINTER(C.c_double)),
-                                C.c_void_p(Z.data_ptr()), gamma.ctypes.data_as(C.POINTER(C.c_double)))
-            _lib.check(lib.ite_k_heff(*args(Y_ref)), ctx.h)
+            a = np.array([alpha.real, alpha.imag])
+            g = np.array([gamma, 0.0])
             held = lib.ite_ctx_device_bytes(ctx.h)
             torch.cuda.synchronize()
             before = torch.cuda.memory_allocated()
-            _lib.check(lib.ite_k_heff_noalloc(*args(Y)), ctx.h)
+            _lib.check(lib.ite_k_heff_noalloc(
+                ctx.h, H.h, i, chlB, chlK, chrK, chrB, C.c_void_p(L.data_ptr()),
+                C.c_void_p(R.data_ptr()), C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+                a.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(Z.data_ptr()),
+                g.ctypes.data_as(C.POINTER(C.c_double))), ctx.h)
             torch.cuda.synchronize()
             assert lib.ite_ctx_device_bytes(ctx.h) == held
             assert torch.cuda.memory_allocated() == before
-            assert rel_err(to_host(Y), to_host(Y_ref)) < 1e-12
+            assert rel_err(to_host(Y), want) < 1e-12, (name, call)
+            assert torch.cuda.current_device() == 0
     # sizes beyond the static scratch are rejected with a message, nothing runs
     H = api.mpo_create(ctx, ompo.heisenberg_mpo(20))
     big = torch.zeros(1, dtype=torch.complex128, device="cuda")
