@@ -155,11 +155,13 @@ ite_status ite_profile_start(ite_ctx ctx);
 ite_status ite_profile_stop(ite_ctx ctx, double ms[ITE_PROFILE_SLOTS],
                             double flops[ITE_PROFILE_SLOTS], long long counts[ITE_PROFILE_SLOTS]);
 /* SVD statistics since the last call (then reset): splits performed, total
- * and largest number of Jacobi sweeps, and (fp64_flops, may be NULL) the
- * algorithmic FP64 flops of the Householder LQ ([0]) and of the Jacobi
- * rotations and inner products actually executed ([1]). */
+ * and largest number of Jacobi sweeps, and (fp64_flops, may be NULL; three
+ * entries) the algorithmic FP64 flops of the Householder LQ ([0]), of the
+ * Jacobi rotations and inner products actually executed ([1]), and the
+ * reference algorithmic work of the truncated SVDs ([2]: 8.7 GFLOP for a
+ * 512 x 512 complex block, the 22 n^3-class count, scaled by p q min(p, q)). */
 ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total, int* sweeps_max,
-                         double fp64_flops[2]);
+                         double fp64_flops[3]);
 
 /* MPO from explicit site tensors: d[N] site dimensions (all equal), D[N+1]
  * bond dimensions with D[0] = D[N] = 1, W the concatenated W_i (interleaved

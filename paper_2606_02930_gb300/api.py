@@ -425,11 +425,11 @@ def profile_stop(ctx):
 
 def svd_stats(ctx):
     splits, total, mx = C.c_longlong(), C.c_longlong(), C.c_int()
-    fl = np.zeros(2)
+    fl = np.zeros(3)
     check(lib.ite_svd_stats(ctx.h, C.byref(splits), C.byref(total), C.byref(mx), _dptr(fl)), ctx.h)
     return {"splits": splits.value, "sweeps_mean": total.value / max(1, splits.value),
             "sweeps_max": mx.value, "lq_fp64_flops": float(fl[0]),
-            "jacobi_fp64_flops": float(fl[1])}
+            "jacobi_fp64_flops": float(fl[1]), "svd_alg_flops": float(fl[2])}
 
 
 def k_gemm_bf16(ctx, A, B, Cout, k_tile=64):

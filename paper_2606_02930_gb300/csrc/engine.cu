@@ -45,6 +45,10 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr int kJacobiSweeps = 30;
 constexpr int kMaxKrylov = 32;
 constexpr double kEmuMinWork = 2.0e6;    // complex MACs below which GEMMs stay native
+// Algorithmic FP64 work of a truncated SVD of a p x q complex block, as the
+// reference count that roofline figures divide by: the 22 n^3-class estimate
+// of 8.7 GFLOP for a 512 x 512 block, scaled by p q min(p, q).
+constexpr double kSvdAlgFlopsPerPQK = 8.7e9 / (512.0 * 512.0 * 512.0);
 // Rows whose squared norm is below skip_weight(cutoff) |A|^2 can never be
 // kept by the truncation rule, so the Jacobi sweeps do not orthogonalise two
 // such rows against each other (their total weight is exact regardless).
@@ -95,7 +99,7 @@ struct ite_ctx_s {
   int gemm_mode = 0;           // 0 native FP64, 1 tensor-core FP64 emulation
   int kernel_precision = 0;    // precision of the kernel-level entry points (ite_precision)
   long long jacobi_sweeps_total = 0, jacobi_splits = 0;
-  double jacobi_flops = 0.0, lq_flops = 0.0;
+  double jacobi_flops = 0.0, lq_flops = 0.0, svd_alg_flops = 0.0;
   int jacobi_sweeps_max = 0;
   // event profiling of the sweep's stages (off unless started)
   bool prof = false;
@@ -453,6 +457,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   // algorithmic FP64 flops of the Jacobi: 16 per element and examined pair
   // (three inner products), 20 per element and rotated pair (the rotation)
   ctx->jacobi_flops += (16.0 * ctx->hr->pairs[0] + 20.0 * ctx->hr->pairs[1]) * p;
+  ctx->svd_alg_flops += kSvdAlgFlopsPerPQK * (double)p * q * k;
   const int r = ctx->hr->rank;
   if (r < 1 || r > k) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");
   if (!std::isfinite(ctx->hr->disc)) return fail(ctx, ITE_ESINGULAR, "non-finite singular values");
@@ -667,9 +672,17 @@ ite_status mps_alloc(ite_ctx ctx, int N, int d, int chi_cap, ite_mps* out) {
   m->chi.assign(N + 1, 1);
   size_t total = 0;
   std::vector<size_t> off(N);
-  for (int i = 0; i < N; ++i) {
+  bool overflow = false;
+  for (int i = 0; i < N && !overflow; ++i) {
     off[i] = total;
-    total += (size_t)m->cap[i] * d * m->cap[i + 1];
+    size_t t = 0;
+    overflow = __builtin_mul_overflow((size_t)m->cap[i], (size_t)d, &t) ||
+               __builtin_mul_overflow(t, (size_t)m->cap[i + 1], &t) ||
+               __builtin_add_overflow(total, t, &total);
+  }
+  if (overflow || total > SIZE_MAX / sizeof(cplx)) {
+    delete m;
+    return fail(ctx, ITE_ENOMEM, "MPS of this length and capacity exceeds the address space");
   }
   ite_status st = buf_ensure(ctx, m->mem, total * sizeof(cplx));
   if (st != ITE_OK) {
@@ -1147,10 +1160,11 @@ ite_status ite_svd_stats(ite_ctx ctx, long long* splits, long long* sweeps_total
   if (fp64_flops) {
     fp64_flops[0] = ctx->lq_flops;
     fp64_flops[1] = ctx->jacobi_flops;
+    fp64_flops[2] = ctx->svd_alg_flops;
   }
   ctx->jacobi_splits = ctx->jacobi_sweeps_total = 0;
   ctx->jacobi_sweeps_max = 0;
-  ctx->jacobi_flops = ctx->lq_flops = 0.0;
+  ctx->jacobi_flops = ctx->lq_flops = ctx->svd_alg_flops = 0.0;
   return ITE_OK;
 }
 
@@ -1438,9 +1452,10 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
         ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, cc->jacobi_sweeps_max);
         ctx->jacobi_flops += cc->jacobi_flops;
         ctx->lq_flops += cc->lq_flops;
+        ctx->svd_alg_flops += cc->svd_alg_flops;
         cc->jacobi_sweeps_total = cc->jacobi_splits = 0;
         cc->jacobi_sweeps_max = 0;
-        cc->jacobi_flops = cc->lq_flops = 0.0;
+        cc->jacobi_flops = cc->lq_flops = cc->svd_alg_flops = 0.0;
       }
     }
     CS(mps_copy_into(ctx, psi, x));
@@ -1797,8 +1812,17 @@ ite_status ite_mps_checkpoint_info(const void* buf, size_t len, int* N_out, int*
     chi[b] = (int)c;
   }
   if (chi[0] != 1 || chi[N] != 1) return ITE_EINVAL;
-  for (long long i = 0; i < N; ++i) nd += 2 * (size_t)chi[i] * d * chi[i + 1];
-  if ((len - off) / sizeof(double) < nd) return ITE_EINVAL;
+  // Each site's share is compared with the doubles that remain in the buffer
+  // before it is added, so the running sum never exceeds len / 8 and cannot
+  // wrap (a term is at most 2 * 2^20 * 16 * 2^20 = 2^45, but 2^19 of them
+  // would overflow a 64-bit sum).
+  size_t remaining = (len - off) / sizeof(double);
+  for (long long i = 0; i < N; ++i) {
+    const size_t term = 2 * (size_t)chi[i] * (size_t)d * (size_t)chi[i + 1];
+    if (term > remaining) return ITE_EINVAL;
+    remaining -= term;
+    nd += term;
+  }
   if (chi_out && chi_len < (size_t)N + 1) return ITE_EINVAL;
   if (N_out) *N_out = (int)N;
   if (d_out) *d_out = (int)d;

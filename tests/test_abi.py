@@ -161,6 +161,26 @@ def test_checkpoint_header_is_read_without_a_device():
     assert info(img, len(img), None, None, None, out, 4, None) == _lib.ITE_EINVAL
 
 
+def test_checkpoint_parser_refuses_a_header_whose_tensor_count_wraps():
+    # d = 16 and N = 2^19 + 4 bonds of 2^20 (each site 2 * 2^20 * 16 * 2^20 =
+    # 2^45 doubles): chi = [1, M, ..., M, M - 2, 1, 2, 1] with M = 2^20 makes
+    # the total exactly 2^64 + 64 doubles, which a 64-bit sum wraps to 64.  The
+    # image carries those 64 doubles; the parser must still refuse it.
+    import numpy as np
+    from paper_2606_02930_gb300 import _lib
+    M, d = 1 << 20, 16
+    N = (1 << 19) + 4
+    chi = [1] + [M] * (N - 4) + [M - 2, 1, 2, 1]
+    assert len(chi) == N + 1
+    total = sum(2 * chi[i] * d * chi[i + 1] for i in range(N))
+    assert total == 2 ** 64 + 64
+    img = _checkpoint(N, d, M, chi, total % 2 ** 64)
+    n = ctypes.c_size_t()
+    st = _lib.lib.ite_mps_checkpoint_info(img, len(img), None, None, None, None, 0,
+                                          ctypes.byref(n))
+    assert st == _lib.ITE_EINVAL
+
+
 def test_checkpoint_parser_survives_arbitrary_bytes():
     # random byte strings and randomly mutated valid images: the parser
     # returns ITE_OK or ITE_EINVAL and never reads past the buffer's end
