@@ -45,6 +45,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # 512 x 512 split from the ncu capture of this kernel source summarised in
 # profiles/k_jacobi_persistent_split512.md (None once the kernel changes).
 JACOBI_TRAFFIC_BYTES = 4.334592e6 + 1.230848e6
+JACOBI_TRAFFIC_NOTE = ("dram bytes per launch on the 512 x 512 bulk split (ncu, "
+                       "profiles/k_jacobi_persistent_split512.md); the matrix is L2-resident, "
+                       "the kernel is FP64-bound")
 WORKLOAD = ("heisenberg_bulk: XXX chain N=64 J=1 OBC, D=5, chi_max=256, cutoff 1e-10, "
             "backward Euler on geometric grid 1e-3->1e3 (40 steps), shift=current energy, "
             "saturated synthetic start (chi=256 bulk)")
@@ -62,6 +65,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="steps of the timed sequence replayed in plain FP64 for comparison")
     ap.add_argument("--precision", choices=["fp64", "fp64_tc"], default="fp64_tc",
                     help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores")
     ap.add_argument("--only", choices=["heff", "split"], default=None,
@@ -99,40 +104,54 @@ def bond_weights():
 
 
 def oracle_bond_sample(n_bonds):
-    """Time the oracle on n_bonds bulk two-site updates (projection of the
-    right-hand side, GMRES(10) on (1 - c s) X + c H_eff X, truncated SVD split,
-    environment updates) at chi = 256.  Returns seconds per bulk update."""
-    from oracle import linsolve as ls, mpo as ompo
-    rng = np.random.default_rng(SEED)
-
-    def cr(*s):
-        return (rng.standard_normal(s) + 1j * rng.standard_normal(s)) / np.sqrt(2 * s[0])
-
+    """Time the oracle on the start of one tau-step of the real workload: the
+    gauge move and right environments of the start state, then the first
+    two-site updates of the left-to-right pass up to and including n_bonds
+    bulk (chi = 256) bonds (projection of the right-hand side, GMRES(10) on
+    (1 - c s) X + c H_eff X, truncated SVD split, environment updates), with
+    the first step's dtau and shift = the state's energy.  Returns (seconds
+    of the setup, seconds per bulk update, updates timed)."""
+    from oracle import linsolve as ls, mpo as ompo, mps as omps
+    from paper_2606_02930_gb300 import inputs
     Ws = ompo.heisenberg_mpo(N_SITES)
-    c, s = 0.1, -10.0
-    L, R = cr(CHI, D_MPO, CHI), cr(CHI, D_MPO, CHI)
-    Lo, Ro = cr(CHI, CHI), cr(CHI, CHI)
-    A1, A2 = cr(CHI, D_SITE, CHI), cr(CHI, D_SITE, CHI)
+    A = inputs.random_isometric_mps(N_SITES, D_SITE, CHI, SEED)
+    s = omps.expect_mpo(A, Ws)
+    c = TAU0                               # backward Euler, first grid step
     t0 = time.perf_counter()
-    for b in range(n_bonds):
-        i = 20 + b
-        B = ls.project_two_site(Lo, A1, A2, Ro)
-        X0 = np.tensordot(A1, A2, axes=([2], [0]))
-        mv = lambda V: (1 - c * s) * V + c * ls.heff_apply(L, Ws[i], Ws[i + 1], R, V)
+    x = ls.right_canonicalize_svd(A)
+    b = A
+    Rop, Rov = ls._build_right_envs(Ws, x, [("op", x), ("ov", b)])
+    Lop = np.ones((1, 1, 1), complex)
+    Lov = np.ones((1, 1), complex)
+    t_setup = time.perf_counter() - t0
+    alpha = 1.0 - c * s
+    first_bulk = int(np.ceil(np.log2(CHI))) if D_SITE == 2 else 0
+    t_bulk, n_done, i = 0.0, 0, 0
+    while n_done < n_bonds:
+        t1 = time.perf_counter()
+        B = ls.project_two_site(Lov, b[i], b[i + 1], Rov[i + 1])
+        X0 = np.tensordot(x[i], x[i + 1], axes=([2], [0]))
+        mv = lambda V: alpha * V + c * ls.heff_apply(Lop, Ws[i], Ws[i + 1], Rop[i + 1], V)
         X, _ = ls.gmres(mv, B, X0, 10)
-        U, SV, _, _ = ls.split_two_site(X, CHI, CUTOFF, True)
-        ls.left_env_update(L, U, Ws[i], U)
-        ls.left_overlap_update(Lo, U, A1)
-    return (time.perf_counter() - t0) / n_bonds
+        x[i], x[i + 1], _, _ = ls.split_two_site(X, CHI, CUTOFF, True)
+        Lop = ls.left_env_update(Lop, x[i], Ws[i], x[i])
+        Lov = ls.left_overlap_update(Lov, x[i], b[i])
+        if i >= first_bulk:
+            t_bulk += time.perf_counter() - t1
+            n_done += 1
+        i += 1
+    return t_setup, t_bulk / n_bonds, i
 
 
 def cpu_baseline_line(n_bonds):
-    t_bond = oracle_bond_sample(n_bonds)
-    per_step = t_bond * bond_weights()
-    return {"value": 1.0 / per_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"{n_bonds} bulk chi=256 two-site updates of the oracle (RHS projection, "
-                       f"GMRES(10), truncated SVD, environment updates) timed on the host, scaled "
-                       f"by the {bond_weights():.1f} bulk-equivalent updates of one tau-step")}
+    t_setup, t_bond, done = oracle_bond_sample(n_bonds)
+    per_step = t_setup + t_bond * bond_weights()
+    return {"value": 1.0 / per_step, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle, extrapolated",
+            "sample": (f"the oracle's gauge move and environments of the start state "
+                       f"({t_setup:.1f} s) and the first {done} two-site updates of its sweep "
+                       f"({n_bonds} bulk chi=256 updates timed: {t_bond:.2f} s each), the step "
+                       f"extrapolated as setup + {bond_weights():.1f} bulk-equivalent updates")}
 
 
 class ClockSampler:
@@ -218,8 +237,8 @@ def run_reference(args, rank, world):
     vals = []
     t0 = time.perf_counter()
     for _ in range(K):
-        t = oracle_bond_sample(args.bonds) * bond_weights()
-        vals.append(t)
+        t_setup, t_bond, _ = oracle_bond_sample(args.bonds)
+        vals.append(t_setup + t_bond * bond_weights())
     tot = time.perf_counter() - t0
     value = 1.0 / statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -227,18 +246,68 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"{args.bonds} bulk bonds per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": (f"each step: {args.bonds} bulk chi=256 two-site updates "
-                                        f"scaled by {bond_weights():.1f} bulk-equivalent updates "
-                                        f"per tau-step; wall {tot:.1f} s")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle, extrapolated",
+                             "sample": (f"each step: the oracle's gauge move and environments "
+                                        f"of the start state and its sweep up to {args.bonds} "
+                                        f"bulk chi=256 two-site updates, extrapolated to "
+                                        f"{bond_weights():.1f} bulk-equivalent updates per "
+                                        f"tau-step; wall {tot:.1f} s")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def heff_kernel_rates(api, ctx, H, precision, reps=5):
+    """Kernel-level H_eff TFLOP/s (algorithmic FLOP count) at the bulk shapes
+    chi = 256 and chi = 512 (d = 2, D = 5), CUDA events on the context stream."""
+    import torch
+    from paper_2606_02930_gb300 import inputs  # noqa: F401  (same module set as the step)
+    rng = np.random.default_rng(SEED)
+    out = {}
+    api.set_kernel_precision(ctx, precision)
+    stream = torch.cuda.current_stream()
+    try:
+        for chi in (256, 512):
+            def dev(*shape):
+                a = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(shape[-1])
+                return torch.from_numpy(a).to("cuda")
+            L, R, X = dev(D_MPO, chi, chi), dev(D_MPO, chi, chi), dev(chi, D_SITE, D_SITE, chi)
+            Y = torch.empty_like(X)
+            flops = 8.0 * (2 * D_MPO * D_SITE ** 2 * chi ** 3 + 2 * D_MPO ** 2 * D_SITE ** 3 * chi ** 2)
+            for _ in range(2):
+                api.k_heff(ctx, H, 20, L, R, X, Y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                api.k_heff(ctx, H, 20, L, R, X, Y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[f"chi{chi}"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+    finally:
+        api.set_kernel_precision(ctx, "fp64")
+    return out
+
+
+def reference_energies():
+    """Oracle energies of the first steps of the timed sequence (fixed mode,
+    backward Euler, from the start state), written by
+    tests/golden/make_bench_reference.py; None when absent."""
+    path = os.path.join(ROOT, "tests", "golden", "bench_reference_energies.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
 
 
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
     from paper_2606_02930_gb300 import api, inputs
+    from paper_2606_02930_gb300 import _lib as L
+    import ctypes as C
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -249,78 +318,139 @@ def run_ours(args, rank, world, local_rank):
     H = api.mpo_create_heisenberg(ctx, N_SITES)
     A0 = inputs.random_isometric_mps(N_SITES, D_SITE, CHI, replica_seed(rank))
     psi = api.mps_create(ctx, A0, CHI)
+    start = api.mps_create(ctx, A0, CHI)       # the start state, kept on the device
     nodes = api.grid_geometric(TAU0, TAU_MAX, K_GRID)
-    state = {"k": 0, "s": api.energy(ctx, H, psi)}
+    s0 = api.energy(ctx, H, start)
     opts = api.solver_opts(precision=args.precision)
 
-    def one_step(p):
-        k = state["k"] % K_GRID
-        info = api.implicit_step(ctx, H, p, nodes[k + 1] - nodes[k], args.scheme, state["s"], CHI, CUTOFF,
-                                 opts)
-        state["k"] += 1
-        state["s"] = info["energy"]
-        return info
-
-    for _ in range(args.warmup):
-        one_step(psi)
+    # Every measured sequence is the same: K steps k = 0..K-1 of the grid from
+    # the start state, shift = the energy of the current state.
+    def run(n, o, events=None, host_io=None):
+        api.mps_copy(ctx, start, psi)
+        s, infos = s0, []
+        for k in range(n):
+            if host_io is not None:
+                host_io.before()
+            kk = k % K_GRID
+            info = api.implicit_step(ctx, H, psi, nodes[kk + 1] - nodes[kk], args.scheme, s, CHI,
+                                     CUTOFF, o)
+            if host_io is not None:
+                host_io.after()
+            if events is not None:
+                events[k].record(stream)
+            s = info["energy"]
+            infos.append(info)
+        return infos
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    run(args.warmup, opts)
+
     # ---- device-timed region: state resident in HBM
     clocks = ClockSampler(local_rank)
+    api.mps_copy(ctx, start, psi)
     barrier()
     clocks.start()
     launches0 = api.kernel_launches()
     api.svd_stats(ctx)
     api.profile_start(ctx)
     e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0.record(stream)
-    infos = [one_step(psi) for _ in range(args.steps)]
-    e1.record(stream)
+    # run() copies the start state in first; that device copy (134 MB) is
+    # timed with the steps
+    infos = run(args.steps, opts, events=ev)
     barrier()
     prof = api.profile_stop(ctx)
     svd = api.svd_stats(ctx)
     launches = api.kernel_launches() - launches0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = e0.elapsed_time(ev[-1])
+    step_ms = [e0.elapsed_time(ev[0])] + [ev[k - 1].elapsed_time(ev[k]) for k in range(1, args.steps)]
     t_max = max_over_ranks(ms, dist, "cuda")
     value = whole_job_rate(world, args.steps, t_max * 1e-3)
 
-    # ---- end to end through the C ABI with host buffers (pinned)
+    # ---- end to end through the C ABI with host buffers (pinned): the same
+    # K steps from the same start state; every step uploads the state from
+    # host memory and reads the new state back
     cap = [1] + inputs.bond_profile(N_SITES, D_SITE, CHI) + [1]
     cap_doubles = sum(2 * cap[i] * D_SITE * cap[i + 1] for i in range(N_SITES))
     host = torch.empty(cap_doubles, dtype=torch.float64, pin_memory=True)
-    from paper_2606_02930_gb300 import _lib as L
-    import ctypes as C
     lib = L.lib
-    host_chi = np.zeros(N_SITES + 1, np.int32)
     hptr = C.cast(C.c_void_p(host.data_ptr()), C.POINTER(C.c_double))
-    n = C.c_size_t()
-    L.check(lib.ite_mps_bond_dims(psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
-    L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
-    h2d = d2h = 0
+
+    class HostIO:
+        def __init__(self):
+            self.chi = np.zeros(N_SITES + 1, np.int32)
+            self.n = C.c_size_t()
+            self.h2d = self.d2h = 0
+            L.check(lib.ite_mps_bond_dims(start.h, self.chi.ctypes.data_as(C.POINTER(C.c_int)),
+                                          C.byref(self.n)))
+            L.check(lib.ite_mps_get(ctx.h, start.h, hptr, cap_doubles), ctx.h)
+
+        def before(self):
+            L.check(lib.ite_mps_set(ctx.h, psi.h, self.chi.ctypes.data_as(C.POINTER(C.c_int)),
+                                    hptr), ctx.h)
+            self.h2d += 8 * self.n.value
+
+        def after(self):
+            L.check(lib.ite_mps_bond_dims(psi.h, self.chi.ctypes.data_as(C.POINTER(C.c_int)),
+                                          C.byref(self.n)))
+            L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
+            self.d2h += 8 * self.n.value
+
+    hio = HostIO()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        L.check(lib.ite_mps_set(ctx.h, psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)), hptr),
-                ctx.h)
-        h2d += 8 * n.value
-        one_step(psi)
-        L.check(lib.ite_mps_bond_dims(psi.h, host_chi.ctypes.data_as(C.POINTER(C.c_int)),
-                                      C.byref(n)))
-        L.check(lib.ite_mps_get(ctx.h, psi.h, hptr, cap_doubles), ctx.h)
-        d2h += 8 * n.value
+    e2e_infos = run(args.steps, opts, host_io=hio)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_same = all(a["energy"] == b["energy"] for a, b in zip(infos, e2e_infos))
+
+    # ---- plain FP64 arm on the first steps of the same sequence
+    n64 = min(args.steps, args.fp64_steps)
+    fp64 = None
+    if n64 > 0 and args.precision != "fp64":
+        ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
+        f0 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        f0.record(stream)
+        infos64 = run(n64, api.solver_opts(precision="fp64"), events=ev64)
+        barrier()
+        ms64 = f0.elapsed_time(ev64[-1])
+        ms_same = sum(step_ms[:n64])
+        fp64 = {"steps": n64, "ms_per_step": ms64 / n64,
+                "tau_steps_per_s": n64 / (ms64 * 1e-3),
+                "this_precision_ms_per_step_same_steps": ms_same / n64,
+                "speedup_over_fp64": ms64 / ms_same,
+                "max_rel_energy_diff_vs_this_precision": max(
+                    abs(a["energy"] - b["energy"]) / abs(b["energy"]) for a, b in zip(infos64, infos))}
+
+    ref = reference_energies()
+    delta_e = None
+    if ref is not None and ref.get("scheme") == args.scheme and rank == 0:
+        e_ref = ref["energies"]
+        nref = min(len(e_ref), args.steps)
+        delta_e = {"reference": ref["what"], "steps": nref,
+                   args.precision: max(abs(infos[k]["energy"] - e_ref[k]) / abs(e_ref[k])
+                                       for k in range(nref))}
+        if fp64 is not None:
+            n = min(nref, n64)
+            delta_e["fp64"] = max(abs(infos64[k]["energy"] - e_ref[k]) / abs(e_ref[k])
+                                  for k in range(n))
+            delta_e["fp64_steps"] = n
+
+    heff_rates = heff_kernel_rates(api, ctx, H, args.precision) if rank == 0 else None
 
     heff = prof["heff"]
     heff_tf = heff["flops"] / (heff["ms"] * 1e-3) / 1e12 if heff["ms"] > 0 else 0.0
     jac, lq = prof["jacobi"], prof["lq"]
-    jac_tf = svd["jacobi_fp64_flops"] / (jac["ms"] * 1e-3) / 1e12 if jac["ms"] > 0 else 0.0
+    jac_dev_tf = svd["jacobi_fp64_flops"] / (jac["ms"] * 1e-3) / 1e12 if jac["ms"] > 0 else 0.0
+    jac_alg = svd["svd_alg_flops"]
+    jac_tf = jac_alg / (jac["ms"] * 1e-3) / 1e12 if jac["ms"] > 0 else 0.0
     lq_tf = lq["flops"] / (lq["ms"] * 1e-3) / 1e12 if lq["ms"] > 0 else 0.0
     breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -328,33 +458,41 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_SITES, "chi_max": CHI, "cutoff": CUTOFF,
                        "scheme": SCHEME_NAMES[args.scheme], "precision": args.precision,
+                       "steps_timed": f"grid steps 0..{args.steps - 1} from the start state",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state 134 MB + environments 0.7 GB per chain)"},
             "e2e": {"value": whole_job_rate(world, args.steps, e2e_s), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+                    "h2d_bytes_per_step": hio.h2d // args.steps,
+                    "d2h_bytes_per_step": hio.d2h // args.steps,
+                    "same_steps_as_value": True, "same_energies_as_value": e2e_same},
             "gpu_launches": int(launches),
             "roofline": {"kernel": "k_jacobi_persistent (one-sided Jacobi of the SVD splits)",
                          "bound": "alu", "achieved": jac_tf, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": jac_tf / FP64_PEAK_TFLOPS,
                          "traffic": JACOBI_TRAFFIC_BYTES,
-                         "traffic_note": ("dram bytes per launch on the 512 x 512 bulk split "
-                                          "(ncu, profiles/k_jacobi_persistent_split512.md); the "
-                                          "matrix is L2-resident, the kernel is FP64-bound"),
+                         "traffic_note": JACOBI_TRAFFIC_NOTE,
+                         "achieved_note": ("algorithmic SVD work (22 n^3-class count: 8.7 GFLOP "
+                                           "per 512 x 512 split, scaled by m n min(m,n)) over "
+                                           "the Jacobi kernel's CUDA-event time"),
+                         "device_counted_tflops": jac_dev_tf,
                          "launches": jac["count"], "ms_per_launch": jac["ms"] / max(1, jac["count"]),
-                         "flops_per_launch": svd["jacobi_fp64_flops"] / max(1, jac["count"]),
-                         "peak_note": ("FP64 pipe peak derived from unit counts and clocks "
-                                       "(152 SMs x 4 FLOP/clk x 2.07 GHz); no measured FP64 peak"),
+                         "peak_note": ("derived, not measured: FP64 pipe from unit counts and "
+                                       "clocks (152 SMs x 4 FLOP/clk x 2.07 GHz)"),
                          "share_of_step": jac["ms"] / max(1e-9, prof["step"]["ms"])},
             "roofline_other": {
                 "lq": {"kernel": "k_lq_persistent (Householder LQ of the SVD splits)", "bound": "alu",
                        "achieved": lq_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": lq_tf / FP64_PEAK_TFLOPS,
                        "share_of_step": lq["ms"] / max(1e-9, prof["step"]["ms"])},
-                "heff": {"kernel": "two-site H_eff (FP64-class tensor-core GEMMs + k_mix)",
-                         "achieved_fp64_equiv": heff_tf, "unit": "TFLOP/s",
-                         "vs_fp64_pipe": heff_tf / FP64_PEAK_TFLOPS,
+                "heff": {"kernel": "two-site H_eff in the step", "precision": args.precision,
+                         "achieved": heff_tf, "unit": "TFLOP/s",
                          "share_of_step": heff["ms"] / max(1e-9, prof["step"]["ms"])}},
+            "heff_kernel": {"precision": args.precision, "shapes": "d=2, D=5, chi_l=chi_r=chi",
+                            **(heff_rates or {})},
+            "fp64_arm": fp64,
+            "delta_e_vs_oracle": delta_e,
             "stage_ms_per_step": breakdown,
+            "step_ms": [round(x, 3) for x in step_ms],
             "heff_calls_per_step": heff["count"] // max(1, args.steps),
             "svd_jacobi": svd,
             "energies": [i["energy"] for i in infos],

@@ -1,0 +1,123 @@
+"""Parity at the benchmarked configuration itself.
+
+The Heisenberg chain of 64 sites (J = 1, open ends, MPO bond dimension 5),
+chi_max = 256, discarded-weight cutoff 1e-10, from the benchmark's own
+saturated start state (random isometries with bond weights exp(-b/64), seed
+2000, so the cap of 256 binds at every bulk bond) and shift = the energy of
+that state.  One backward-Euler step in both precision modes and one
+trapezoid step, each against the oracle's step from the same tensors (Eq. 4,
+one sweep of GMRES(10) local solves, App. B and App. D), with the bar of
+reading c12: relative energy error and infidelity <= 1e-10 at the same chi and
+cutoff, and the same rank at every bond (reported bond by bond on failure).
+Also the tensor-core H_eff at the bulk shapes chi = 256 and chi = 512, sampled
+element by element against entries the oracle computes one by one."""
+import numpy as np
+import pytest
+
+from oracle import linsolve as ls, mpo as ompo, mps as omps, step as ostep
+from paper_2606_02930_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N, CHI, CUTOFF, SEED = 64, 256, 1e-10, 2000
+TOL = 1e-10
+# the step sizes of the benchmark's geometric grid 1e-3 -> 1e3 (40 steps):
+# its first step, and a late one where the local systems are far from the
+# identity (c (E_max - s) of order 10)
+DTAUS = (1e-3, 0.5)
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_02930_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.ctx_create(0)
+
+
+@pytest.fixture(scope="module")
+def start():
+    Ws = ompo.heisenberg_mpo(N)
+    A = inputs.random_isometric_mps(N, 2, CHI, SEED)
+    return Ws, A, omps.expect_mpo(A, Ws)
+
+
+_oracle_cache = {}
+
+
+def oracle_step(start, scheme, dt):
+    key = (scheme, dt)
+    if key not in _oracle_cache:
+        Ws, A, s = start
+        _oracle_cache[key] = ostep.implicit_step(Ws, A, dt, scheme, s, CHI, CUTOFF)
+    return _oracle_cache[key]
+
+
+def infid(a, b):
+    return 1.0 - abs(omps.overlap(a, b)) / (omps.norm(a) * omps.norm(b))
+
+
+@pytest.mark.parametrize("scheme,precision,dt", [("be", "fp64_tc", DTAUS[0]),
+                                                 ("be", "fp64", DTAUS[0]),
+                                                 ("be", "fp64_tc", DTAUS[1]),
+                                                 ("tr", "fp64_tc", DTAUS[1])])
+def test_bench_configuration_step_matches_oracle(api, ctx, start, scheme, precision, dt):
+    Ws, A, s = start
+    H = api.mpo_create_heisenberg(ctx, N)
+    psi = api.mps_create(ctx, A, CHI)
+    s_gpu = api.energy(ctx, H, psi)
+    assert abs(s_gpu - s) <= 1e-12 * abs(s)
+    ginfo = api.implicit_step(ctx, H, psi, dt, scheme, s, CHI, CUTOFF,
+                              api.solver_opts(precision=precision))
+    ost, oinfo = oracle_step(start, scheme, dt)
+    got = psi.tensors()
+    ranks_o = np.array(omps.bond_dims(ost))
+    ranks_g = np.array([t.shape[2] for t in got[:-1]])
+    mismatch = np.nonzero(ranks_o != ranks_g)[0]
+    assert mismatch.size == 0, f"rank differs at bonds {mismatch.tolist()}: " \
+                               f"{ranks_o[mismatch].tolist()} vs {ranks_g[mismatch].tolist()}"
+    rel = abs(ginfo["energy"] - oinfo.energy) / abs(oinfo.energy)
+    inf = infid(ost, got)
+    assert rel <= TOL, f"relative energy error {rel:.3e}"
+    assert inf <= TOL, f"infidelity {inf:.3e}"
+    assert abs(ginfo["norm_before"] - oinfo.norm_before) <= TOL * oinfo.norm_before
+    assert ginfo["max_chi"] == oinfo.max_chi == CHI
+
+
+@pytest.mark.parametrize("chi", [256, 512])
+def test_tensor_core_heff_at_bulk_shapes(api, ctx, chi):
+    # the bulk two-site block of the chi = 256 workload, and chi = 512; sampled
+    # outputs Y[a, s', t', b] against the oracle's sum for that one entry
+    import torch
+    from tests.gpu_util import L_to_lib, R_to_lib, crandn, to_dev, to_host
+    d, D = 2, 5
+    Ws = ompo.heisenberg_mpo(40)
+    i = 20
+    rng = np.random.default_rng(chi)
+    L, R = crandn(rng, chi, D, chi) / chi, crandn(rng, chi, D, chi) / chi
+    X = crandn(rng, chi, d, d, chi)
+    H = api.mpo_create_heisenberg(ctx, 40)
+    api.set_kernel_precision(ctx, "fp64_tc")
+    try:
+        Y = torch.empty((chi, d, d, chi), dtype=torch.complex128, device="cuda")
+        api.k_heff(ctx, H, i, to_dev(L_to_lib(L)), to_dev(R_to_lib(R)), to_dev(X), Y)
+        Yh = to_host(Y)
+    finally:
+        api.set_kernel_precision(ctx, "fp64")
+    # one output entry: sum L[a,w,a'] W1[w,s',s,v] W2[v,t',t,w'] R[b,w',b'] X[a',s,t,b']
+    W2 = np.einsum("wpsv,vqtu->wpqstu", Ws[i], Ws[i + 1])
+    scale = np.abs(Yh).max()
+    for a, sp, tp, b in zip(rng.integers(chi, size=24), rng.integers(d, size=24),
+                            rng.integers(d, size=24), rng.integers(chi, size=24)):
+        LX = np.einsum("wk,kstc->wstc", L[a], X)                 # (w, s, t, b')
+        T = np.einsum("wstu,wstc->uc", W2[:, sp, tp], LX)         # (w', b')
+        want = np.einsum("uc,uc->", T, R[b])
+        assert abs(Yh[a, sp, tp, b] - want) <= 1e-12 * scale
+    # the sampled entries agree with the full oracle product on a slice
+    full = ls.heff_apply(L[:2], Ws[i], Ws[i + 1], R[:3], X)
+    assert np.abs(Yh[:2, :, :, :3] - full).max() <= 1e-12 * scale
