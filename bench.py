@@ -67,9 +67,12 @@ def parse():
     ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="steps of the timed sequence replayed in plain FP64 for comparison")
-    ap.add_argument("--precision", choices=["fp64", "fp64_tc"], default="fp64_tc",
-                    help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores")
-    ap.add_argument("--only", choices=["heff", "split"], default=None,
+    ap.add_argument("--precision", choices=["fp64", "fp64_tc", "mixed_bf16", "mixed_tf32"],
+                    default="fp64_tc",
+                    help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores; "
+                         "mixed_*: local solves converged by refinement with bf16/tf32 inner "
+                         "matvecs")
+    ap.add_argument("--only", choices=["heff", "split", "heff_lp"], default=None,
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
     ap.add_argument("--scheme", choices=["be", "tr", "gl2", "gl3"], default="be",
                     help="time stepper of the chain workload (the headline runs backward Euler)")
@@ -78,6 +81,8 @@ def parse():
                     help="batch: a bounded sample of the batched workload served side by side; "
                          "chi_study: bond-dimension growth and step cost of an evolution; "
                          "metts: independent METTS chains served side by side")
+    ap.add_argument("--lp-shape", default="all",
+                    help="--only heff_lp: all, heisenberg512, heisenberg1024 or anderson512")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
     ap.add_argument("--slots", type=int, default=4, help="concurrent jobs in the batch sample")
     ap.add_argument("--study-n", type=int, default=100, help="chain length of the chi study")
@@ -287,6 +292,68 @@ def heff_kernel_rates(api, ctx, H, precision, reps=5):
             out[f"chi{chi}"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
     finally:
         api.set_kernel_precision(ctx, "fp64")
+    return out
+
+
+def measured_peaks():
+    """(bf16 burst TFLOP/s, sustained, source) from MEASURED_PEAKS.json, else
+    the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, 1700.0, "fallback"
+
+
+LP_SHAPES = (("heisenberg", 2, 5, 512), ("heisenberg", 2, 5, 1024), ("anderson", 4, 6, 512))
+
+
+def heff_lp_rates(api, ctx, precisions=("mixed_bf16",), reps=10, shapes=LP_SHAPES):
+    """Kernel-level TFLOP/s of the low-precision H_eff matvec (operands
+    prepared once, as in a local solve) at bulk shapes with chi >= 512, by the
+    algorithmic FLOP count, CUDA events on the context stream; fraction of the
+    measured bf16 burst peak (tf32: half of it, the nominal tf32/bf16 ratio)."""
+    import torch
+    from paper_2606_02930_gb300 import inputs
+    peak_bf16, _, src = measured_peaks()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(SEED)
+    out = {}
+    for model, d, D, chi in shapes:
+        if model == "heisenberg":
+            H = api.mpo_create_heisenberg(ctx, 40)
+            i = 20
+        else:
+            eps, V = inputs.flat_band_bath(39)
+            H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
+            i = 20
+
+        def dev(*shape):
+            a = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(shape[-1])
+            return torch.from_numpy(a).to("cuda")
+        L, R, X = dev(D, chi, chi), dev(D, chi, chi), dev(chi, d, d, chi)
+        Y = torch.empty_like(X)
+        flops = 8.0 * (2 * D * d ** 2 * chi ** 3 + 2 * D ** 2 * d ** 3 * chi ** 2)
+        for prec in precisions:
+            api.k_heff_lp_prepare(ctx, H, i, L, R, prec)
+            for _ in range(3):
+                api.k_heff_lp_apply(ctx, H, i, X, Y, 1.0, X, 0.5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                api.k_heff_lp_apply(ctx, H, i, X, Y, 1.0, X, 0.5)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            tf = flops / (ms * 1e-3) / 1e12
+            peak = peak_bf16 if prec == "mixed_bf16" else 0.5 * peak_bf16
+            out[f"{model}_d{d}_D{D}_chi{chi}_{prec}"] = {
+                "ms": ms, "tflops": tf, "peak": peak, "frac": tf / peak,
+                "peak_note": (f"{src} bf16 burst" if prec == "mixed_bf16"
+                              else f"{src} bf16 burst x 1/2 (nominal tf32 ratio)")}
+        del L, R, X, Y
     return out
 
 
@@ -672,6 +739,12 @@ def run_only(args):
         a = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(shape[-1])
         return torch.from_numpy(a).to("cuda")
 
+    if args.only == "heff_lp":
+        prec = args.precision if args.precision.startswith("mixed") else "mixed_bf16"
+        shapes = tuple(sh for sh in LP_SHAPES if args.lp_shape in ("all", f"{sh[0]}{sh[3]}"))
+        print(json.dumps({"only": "heff_lp", **heff_lp_rates(api, ctx, (prec,), args.steps,
+                                                             shapes)}), flush=True)
+        return
     H = api.mpo_create_heisenberg(ctx, N_SITES)
     api.set_kernel_precision(ctx, args.precision)
     if args.only == "heff":

@@ -90,8 +90,18 @@ typedef enum {
 /* Arithmetic of the contractions.  ITE_FP64: complex128 everywhere on the
  * FP64 pipes.  ITE_FP64_TC: the same algorithm, with every large contraction
  * computed to FP64-class accuracy on the bf16 tensor cores by exact slicing
- * (ite_k_zgemm mode 1); everything else stays FP64. */
-typedef enum { ITE_FP64 = 0, ITE_FP64_TC = 1 } ite_precision;
+ * (ite_k_zgemm mode 1); everything else stays FP64.
+ * ITE_MIXED_BF16 / ITE_MIXED_TF32: each local solve of the sweep (App. B) is
+ * converged by iterative refinement: the residual B - A X is formed with the
+ * FP64-class contraction of ITE_FP64_TC, and each correction solves A D = r by
+ * one GMRES(krylov_dim) cycle whose H_eff matvecs use bf16 (or tf32) operands
+ * with fp32 accumulation on the tensor cores; X += D, until |r| <= refine_tol
+ * |B| or refine_max corrections.  A correction that does not halve |r| moves
+ * the inner matvecs up one precision (bf16 -> tf32 -> FP64-class).  Krylov
+ * vectors, the Hessenberg solve, environments, SVDs, norms and energies stay
+ * FP64 (environments FP64-class), so the converged local solution carries the
+ * FP64-class residual.  local_tol and max_cycles do not apply in these modes. */
+typedef enum { ITE_FP64 = 0, ITE_FP64_TC = 1, ITE_MIXED_BF16 = 2, ITE_MIXED_TF32 = 3 } ite_precision;
 
 /* Spectrum shift s of each step.  FIXED: the caller's value.  CURRENT_ENERGY:
  * s_k = <psi_{k-1}|H|psi_{k-1}> (App. D shifts H by the energy of the state
@@ -114,6 +124,10 @@ typedef struct {
                          restarted from the last iterate (default 1, as App. D;
                          <= 0 counts as 1); a cycle that ends early (breakdown
                          or local_tol reached) ends the solve                  */
+  int refine_max;     /* mixed modes: most refinement corrections per local
+                         solve (default 10)                                    */
+  double refine_tol;  /* mixed modes: stop at |B - A X| <= refine_tol |B|
+                         (default 1e-10)                                       */
 } ite_solver_opts;
 
 /* Per-step report. */
@@ -152,6 +166,8 @@ unsigned long long ite_kernel_launches(void);
  * entries; unused ones are zero. */
 #define ITE_PROFILE_SLOTS 16
 ite_status ite_profile_start(ite_ctx ctx);
+/* Category 9: the low-precision H_eff matvecs of the mixed modes (FLOPs by
+ * the same algorithmic count as category 0, which they are not part of). */
 ite_status ite_profile_stop(ite_ctx ctx, double ms[ITE_PROFILE_SLOTS],
                             double flops[ITE_PROFILE_SLOTS], long long counts[ITE_PROFILE_SLOTS]);
 /* SVD statistics since the last call (then reset): splits performed, total

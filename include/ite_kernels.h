@@ -22,8 +22,32 @@ extern "C" {
 /* Precision of the contractions inside the kernel-level calls below
  * (ite_k_heff, ite_k_env_left/right, ite_k_local_solve): ITE_FP64 (default)
  * or ITE_FP64_TC (FP64-class products on the tensor cores, as in the step's
- * tensor-core mode).  ITE_EINVAL for any other value. */
+ * tensor-core mode), or ITE_MIXED_BF16 / ITE_MIXED_TF32: ite_k_heff and the
+ * environment updates then run as ITE_FP64_TC, and ite_k_local_solve runs the
+ * mixed modes' refinement (ite.h, ite_precision) with refine_tol = local_tol
+ * (1e-10 when 0) and at most 20 corrections.  ITE_EINVAL for any other
+ * value. */
 ite_status ite_ctx_set_kernel_precision(ite_ctx ctx, int precision);
+
+/* Low-precision two-site H_eff of the mixed modes (the inner matvec of their
+ * refinement; App. B's effective Hamiltonian), in two calls.  prepare copies
+ * the environments L (D_i, chl_bra, chl_ket) and R (D_{i+2}, chr_ket, chr_bra),
+ * laid out as for ite_k_heff, into the context's operand buffer as embedded
+ * real matrices in bf16 (precision ITE_MIXED_BF16) or tf32 (ITE_MIXED_TF32);
+ * apply then computes, for any number of X,
+ *   Y = alpha * H_eff X + gamma * Z
+ * with X, Y, Z as in ite_k_heff, the three contractions on the tensor cores
+ * with fp32 accumulation and the alpha/gamma combination in FP64.  apply
+ * uses the last prepare on this context and returns ITE_EINVAL if that was
+ * for another MPO, bond or shape.  The relative error of Y - gamma Z is of
+ * the order of the operand unit roundoff (2^-8 bf16, 2^-11 tf32) times the
+ * conditioning of the sums. */
+ite_status ite_k_heff_lp_prepare(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                                 int chr_ket, int chr_bra, const double* L, const double* R,
+                                 int precision);
+ite_status ite_k_heff_lp_apply(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                               int chr_ket, int chr_bra, const double* X, double* Y,
+                               const double alpha[2], const double* Z, const double gamma[2]);
 
 /* Two-site effective Hamiltonian on sites (i, i+1) of the MPO (the dominant
  * operation of the local solves, App. B):
@@ -98,6 +122,19 @@ ite_status ite_k_barrier_selftest(ite_ctx ctx, int blocks, int absent);
  * contractions of the two-site effective Hamiltonian (App. B).  flags bit 0
  * selects 32-wide K tiles (64-byte swizzle) instead of 64-wide (128-byte).
  * ITE_ETIMEOUT if a bounded wait inside the kernel ran out. */
+/* The persistent tensor-core GEMM of the low-precision H_eff (mixed modes):
+ * for every batch entry b and K split s,
+ *   C[b*sCb + s*sCs + m*ldc + n] = sum_{k in split s} A[b*sAb + m*lda + k] B[b*sBb + n*ldb + k]
+ * with A, B K-major bf16 (tf32 == 0) or fp32 read as tf32 (tf32 != 0), fp32
+ * accumulation in tensor memory, C fp32.  bn (128 or 256) is the N tile; K
+ * is cut into `splits` nearly equal ranges of 128-byte tiles (splits > 1 needs
+ * sCs > 0).  Leading dimensions and batch strides are in elements and must be
+ * multiples of 16 bytes; pointers 16-byte aligned; a batch stride of 0 shares
+ * that operand across the batch.  ITE_ETIMEOUT if a bounded wait ran out. */
+ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void* A, long long lda,
+                         long long sAb, const void* B, long long ldb, long long sBb, float* C,
+                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits);
+
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
                            const void* B, long long ldb, float* C, long long ldc, int flags);
 

@@ -17,7 +17,7 @@ ITE_MODEL_HEISENBERG, ITE_MODEL_ANDERSON = 0, 1
 ITE_JOB_GRID_GEOMETRIC, ITE_JOB_GRID_PANELS = 0, 1
 (ITE_BACKWARD_EULER, ITE_TRAPEZOID, ITE_GAUSS_LEGENDRE_2, ITE_GAUSS_LEGENDRE_3, ITE_FORWARD_EULER,
  ITE_HEUN) = range(6)
-ITE_FP64, ITE_FP64_TC = 0, 1
+ITE_FP64, ITE_FP64_TC, ITE_MIXED_BF16, ITE_MIXED_TF32 = 0, 1, 2, 3
 ITE_SHIFT_FIXED, ITE_SHIFT_CURRENT_ENERGY = 0, 1
 STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR",
                 4: "ITE_ENOTCONV", 5: "ITE_ETIMEOUT", 6: "ITE_ECUDA", 7: "ITE_PENDING"}
@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "ITE_OK", 1: "ITE_EINVAL", 2: "ITE_ENOMEM", 3: "ITE_ESINGULAR
 class ite_solver_opts(C.Structure):
     _fields_ = [("krylov_dim", C.c_int), ("sweeps", C.c_int), ("local_tol", C.c_double),
                 ("sweep_tol", C.c_double), ("fit_sweeps", C.c_int), ("precision", C.c_int),
-                ("max_cycles", C.c_int)]
+                ("max_cycles", C.c_int), ("refine_max", C.c_int), ("refine_tol", C.c_double)]
 
 
 class ite_step_info(C.Structure):
@@ -126,6 +126,11 @@ SIGNATURES = {
     "ite_k_env_left": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "ite_k_env_right": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "ite_k_heff_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _pd, _vp, _pd]),
+    "ite_k_heff_lp_prepare": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i]),
+    "ite_k_gemm_lp": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _vp,
+                           C.c_longlong, C.c_longlong, _vp, C.c_longlong, C.c_longlong,
+                           C.c_longlong, _i, _i, _i]),
+    "ite_k_heff_lp_apply": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _pd, _vp, _pd]),
     "ite_k_local_solve": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _d, _d, _i, _d, _pi, _pd]),
     "ite_k_gemm_bf16": (_i, [_vp, _i, _i, _i, _vp, C.c_longlong, _vp, C.c_longlong, _vp,
                              C.c_longlong, _i]),

@@ -34,15 +34,20 @@ def _c128(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
 
 
-PRECISIONS = {"fp64": L.ITE_FP64, "fp64_tc": L.ITE_FP64_TC}
+PRECISIONS = {"fp64": L.ITE_FP64, "fp64_tc": L.ITE_FP64_TC, "mixed_bf16": L.ITE_MIXED_BF16,
+              "mixed_tf32": L.ITE_MIXED_TF32}
 
 
 def solver_opts(krylov_dim=10, sweeps=1, local_tol=0.0, sweep_tol=0.0, fit_sweeps=1,
-                precision="fp64", max_cycles=1):
+                precision="fp64", max_cycles=1, refine_max=None, refine_tol=None):
     o = L.ite_solver_opts()
     lib.ite_solver_opts_default(C.byref(o))
     o.krylov_dim, o.sweeps, o.local_tol = krylov_dim, sweeps, local_tol
     o.max_cycles = max_cycles
+    if refine_max is not None:
+        o.refine_max = refine_max
+    if refine_tol is not None:
+        o.refine_tol = refine_tol
     o.sweep_tol, o.fit_sweeps = sweep_tol, fit_sweeps
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return o
@@ -368,6 +373,24 @@ def k_heff(ctx, H, i, L_env, R_env, X, Y, alpha=1.0, Z=None, gamma=0.0):
                          _dptr(g)), ctx.h)
 
 
+def k_heff_lp_prepare(ctx, H, i, L_env, R_env, precision="mixed_bf16"):
+    """Embed the environments for the low-precision H_eff (device tensors laid
+    out as for k_heff)."""
+    D0, chlB, chlK = L_env.shape
+    D2, chrK, chrB = R_env.shape
+    check(lib.ite_k_heff_lp_prepare(ctx.h, H.h, i, chlB, chlK, chrK, chrB, _p(L_env), _p(R_env),
+                                    PRECISIONS[precision]), ctx.h)
+
+
+def k_heff_lp_apply(ctx, H, i, X, Y, alpha=1.0, Z=None, gamma=0.0):
+    """Y = alpha H_eff X + gamma Z with the operands of the last k_heff_lp_prepare."""
+    chlK, chrK = X.shape[0], X.shape[3]
+    chlB, chrB = Y.shape[0], Y.shape[3]
+    check(lib.ite_k_heff_lp_apply(ctx.h, H.h, i, chlB, chlK, chrK, chrB, _p(X), _p(Y),
+                                  _dptr(_cpair(alpha)), _p(Z) if Z is not None else None,
+                                  _dptr(_cpair(gamma))), ctx.h)
+
+
 def k_env_left(ctx, H, i, Lin, bra, ket, Lout):
     check(lib.ite_k_env_left(ctx.h, H.h, i, bra.shape[0], ket.shape[0], bra.shape[2], ket.shape[2],
                              _p(Lin), _p(bra), _p(ket), _p(Lout)), ctx.h)
@@ -401,7 +424,8 @@ def k_barrier_selftest(ctx, blocks, absent):
 
 
 # ------------------------------------------------------------------ profiling
-PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step", "lq", "jacobi")
+PROFILE_CATEGORIES = ("heff", "env", "solve", "svd", "gauge", "project", "step", "lq", "jacobi",
+                      "heff_lp")
 PROFILE_SLOTS = 16
 
 
@@ -440,6 +464,25 @@ def k_gemm_bf16(ctx, A, B, Cout, k_tile=64):
     check(lib.ite_k_gemm_bf16(ctx.h, M, N, K, C.c_void_p(A.data_ptr()), A.stride(0),
                               C.c_void_p(B.data_ptr()), B.stride(0), C.c_void_p(Cout.data_ptr()),
                               Cout.stride(0), 1 if k_tile == 32 else 0), ctx.h)
+
+
+def k_gemm_lp(ctx, A, B, Cout, bn=256, splits=1):
+    """Cout[b][s] (fp32) = A[b] B[b]^T over K split s on the tensor cores.  A
+    (batch, M, K) or (M, K), B (batch, N, K) or (N, K): bf16 (kind::f16) or
+    float32 (read as tf32) CUDA tensors, K contiguous; a 2-D operand is shared
+    by the batch.  Cout (splits, batch, M, N) float32."""
+    import torch
+    tf32 = A.dtype == torch.float32
+    A3 = A if A.dim() == 3 else A.unsqueeze(0)
+    B3 = B if B.dim() == 3 else B.unsqueeze(0)
+    batch = max(A3.shape[0], B3.shape[0])
+    M, K = A3.shape[1], A3.shape[2]
+    N = B3.shape[1]
+    check(lib.ite_k_gemm_lp(ctx.h, M, N, K, batch, C.c_void_p(A3.data_ptr()), A3.stride(1),
+                            A3.stride(0) if A.dim() == 3 else 0, C.c_void_p(B3.data_ptr()),
+                            B3.stride(1), B3.stride(0) if B.dim() == 3 else 0,
+                            C.c_void_p(Cout.data_ptr()), Cout.stride(2), Cout.stride(1),
+                            Cout.stride(0), 1 if tf32 else 0, bn, splits), ctx.h)
 
 
 def k_zgemm(ctx, A, B, Cout, mode=1, conjA=False, conjB=False, alpha=1.0, beta=0.0, transA=False,

@@ -62,6 +62,41 @@ cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long 
                          long long ldc, int M, int N, int K, int* err, cudaStream_t st,
                          int bk = 64);
 
+// Low-precision GEMM (lp_gemm.cu): C[b][split] (fp32) = A[b] B[b]^T over the
+// split's K range, A (M x K) and B (N x K) K-major in bf16 or, with tf32, fp32
+// read as tf32 by kind::tf32 MMAs; fp32 accumulation in TMEM.  Leading
+// dimensions and batch strides in elements, multiples of 16 bytes; a batch
+// stride of 0 shares the operand across the batch.  bn = 128 or 256 (N tile);
+// splits > 1 needs sCs (the output stride between K splits).  *err is set if
+// a bounded wait ran out.
+struct LpGemmArgs {
+  int M, N, K, batch, splits, bn;
+  bool tf32;
+  const void* A; long long lda, sAb;
+  const void* B; long long ldb, sBb;
+  float* C; long long ldc, sCb, sCs;
+};
+cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st);
+int lp_gemm_splits_used(const LpGemmArgs& g);
+int lp_gemm_sm_count();
+
+// Two-site H_eff with low-precision operands (heff_lp.cu): prepare embeds L
+// and R once into `ops` (heff_lp_operand_bytes); apply computes
+// Y = alpha H_eff X + gamma Z with bf16 (or tf32) tensor-core contractions and
+// fp32 accumulation, using `scratch` (heff_lp_scratch_bytes).  Layouts as in
+// the FP64 heff: L[w][a_bra][a_ket], R[w][b_ket][b_bra], X/Y/Z [a][s][t][b].
+size_t heff_lp_operand_bytes(int D0, int D2, int chlB, int chlK, int chrK, int chrB, bool tf32);
+size_t heff_lp_scratch_bytes(int d, int D0, int D2, int chlB, int chlK, int chrK, int chrB,
+                             bool tf32);
+cudaError_t heff_lp_prepare(const cplx* L, const cplx* R, int D0, int D2, int chlB, int chlK,
+                            int chrK, int chrB, bool tf32, void* ops, size_t ops_bytes,
+                            cudaStream_t st);
+struct MixPlan;
+cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, int D2, int chlB,
+                          int chlK, int chrK, int chrB, bool tf32, const cplx* X, cplx* Y,
+                          cplx alpha, const cplx* Z, cplx gamma, void* scratch,
+                          size_t scratch_bytes, int* err, cudaStream_t st);
+
 // FP64-accurate complex GEMM on the bf16 tensor cores (exact 7-bit slicing,
 // see tc_zgemm.cu): same contract as zgemm; scratch of at least
 // zgemm_emu_scratch_bytes(M, N, K) bytes; *err set if a bounded wait ran out.

@@ -89,7 +89,15 @@ struct ite_ctx_s {
   size_t bytes = 0;
   // workspace
   Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu,
-      ws_ovm;
+      ws_ovm, ws_lpops, ws_lpscr, ws_R, ws_D;
+  // mixed modes: precision of the inner matvecs while a refinement correction
+  // runs (-1: none, 0: bf16, 1: tf32), and what the operand buffer holds
+  int lp_level = -1;
+  struct LpPrepared {
+    const void* H = nullptr;
+    int i = -1, dims[4] = {0, 0, 0, 0}, level = -1;
+  } lp_prep;
+  long long refinements = 0, lp_matvecs = 0;
   GmresState* gm = nullptr;
   double* dscal = nullptr;     // device scalars
   cplx* dcplx = nullptr;       // device complex scalars
@@ -203,7 +211,7 @@ ite_status sync(ite_ctx ctx) {
 }
 
 // ------------------------------------------------------------------ profiling
-enum { P_HEFF = 0, P_ENV, P_SOLVE, P_SVD, P_GAUGE, P_PROJ, P_STEP, P_LQ, P_JACOBI, P_NCAT };
+enum { P_HEFF = 0, P_ENV, P_SOLVE, P_SVD, P_GAUGE, P_PROJ, P_STEP, P_LQ, P_JACOBI, P_HEFF_LP, P_NCAT };
 static_assert(P_NCAT <= ITE_PROFILE_SLOTS, "profile categories exceed the ABI's slots");
 
 size_t prof_event(ite_ctx ctx) {
@@ -240,7 +248,7 @@ struct Scope {
 struct KernelMode {
   ite_ctx c;
   explicit KernelMode(ite_ctx ctx) : c(ctx) {
-    c->gemm_mode = c->kernel_precision == ITE_FP64_TC ? 1 : 0;
+    c->gemm_mode = c->kernel_precision == ITE_FP64 ? 0 : 1;
     cudaMemsetAsync(reinterpret_cast<int*>(c->dcounter) + 10, 0, sizeof(int), c->stream);
   }
   ~KernelMode() { c->gemm_mode = 0; }
@@ -303,6 +311,52 @@ ite_status heff(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int
   CS(gemm(ctx, (int)(chlB * d2), chrB, D2 * chrK, T2, (long long)D2 * chrK, 1, false, R, chrB, 1,
           false, Y, chrB, alpha, C(0), Z, gamma));
   return ITE_OK;
+}
+
+// Low-precision H_eff from the operands prepared for (H, i, dims) at
+// ctx->lp_level (bf16 or tf32): Y = alpha H_eff X + gamma Z.
+ite_status heff_lp(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int chrB,
+                   const cplx* X, cplx* Y, cplx alpha, const cplx* Z, cplx gamma) {
+  const int d = H->d, D0 = H->D[i], D1 = H->D[i + 1], D2 = H->D[i + 2];
+  const auto& pp = ctx->lp_prep;
+  if (pp.H != H || pp.i != i || pp.dims[0] != chlB || pp.dims[1] != chlK || pp.dims[2] != chrK ||
+      pp.dims[3] != chrB || pp.level != ctx->lp_level)
+    return fail(ctx, ITE_EINVAL, "low-precision H_eff: operands prepared for another bond or shape");
+  const long long d2 = (long long)d * d;
+  const double flops = 8.0 * ((double)D0 * d2 * chlB * chlK * chrK + (double)D2 * d2 * chlB * chrK * chrB +
+                              2.0 * D1 * D1 * d2 * d * chlB * chrK);
+  Scope sc(ctx, P_HEFF_LP, flops);
+  const bool tf32 = ctx->lp_level == 1;
+  CS(buf_ensure(ctx, ctx->ws_lpscr, heff_lp_scratch_bytes(d, D0, D2, chlB, chlK, chrK, chrB, tf32)));
+  CK(heff_lp_apply(ctx->ws_lpops.p, H->plan2[i], d, D0, D2, chlB, chlK, chrK, chrB, tf32, X, Y,
+                   alpha, Z, gamma, ctx->ws_lpscr.p, ctx->ws_lpscr.n,
+                   reinterpret_cast<int*>(ctx->dcounter) + 10, ctx->stream));
+  ctx->lp_matvecs += 1;
+  return ITE_OK;
+}
+
+// Embeds L and R for heff_lp at precision level (0 bf16, 1 tf32).
+ite_status heff_lp_setup(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrK, int chrB,
+                         const cplx* L, const cplx* R, int level) {
+  const int D0 = H->D[i], D2 = H->D[i + 2];
+  const bool tf32 = level == 1;
+  CS(buf_ensure(ctx, ctx->ws_lpops, heff_lp_operand_bytes(D0, D2, chlB, chlK, chrK, chrB, tf32)));
+  CK(heff_lp_prepare(L, R, D0, D2, chlB, chlK, chrK, chrB, tf32, ctx->ws_lpops.p, ctx->ws_lpops.n,
+                     ctx->stream));
+  auto& pp = ctx->lp_prep;
+  pp.H = H;
+  pp.i = i;
+  pp.dims[0] = chlB; pp.dims[1] = chlK; pp.dims[2] = chrK; pp.dims[3] = chrB;
+  pp.level = level;
+  return ITE_OK;
+}
+
+// The local operator's H_eff: low precision inside a refinement correction,
+// else the FP64 (or FP64-class) contraction.
+ite_status apply_heff(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
+                      const cplx* R, const cplx* X, cplx* Y, cplx alpha, const cplx* Z, cplx gamma) {
+  if (ctx->lp_level >= 0) return heff_lp(ctx, H, i, chl, chl, chr, chr, X, Y, alpha, Z, gamma);
+  return heff(ctx, H, i, chl, chl, chr, chr, L, R, X, Y, alpha, Z, gamma);
 }
 
 ite_status env_left(ite_ctx ctx, ite_mpo H, int i, int chlB, int chlK, int chrB, int chrK,
@@ -497,7 +551,7 @@ ite_status gmres_cycle(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cp
   double* bn2 = ctx->dscal + 1;
   const cplx ca = alpha, cc = c;
   // r0 = B - A X0
-  CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, X, V, cc, X, ca));
+  CS(apply_heff(ctx, H, i, chl, chr, L, R, X, V, cc, X, ca));
   CK(vec_axpby(V, B, C(1), C(-1), n, ctx->stream));
   CK(vec_norm2(V, n, r0n2, ctx->dscal + 16, nullptr, ctx->stream));
   CK(vec_norm2(B, n, bn2, ctx->dscal + 16, nullptr, ctx->stream));
@@ -506,7 +560,7 @@ ite_status gmres_cycle(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cp
   for (int j = 0; j < m; ++j) {
     cplx* vj = V + j * n;
     cplx* w = V + (j + 1) * n;
-    CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, vj, w, cc, vj, ca));
+    CS(apply_heff(ctx, H, i, chl, chr, L, R, vj, w, cc, vj, ca));
     CK(vec_block_dot(V, n, j + 1, w, n, gs->h, ctx->partial, active, ctx->stream));
     CK(vec_block_axpy(V, n, j + 1, nullptr, gs->h, -1.0, w, n, active, ctx->stream));
     CK(vec_block_dot(V, n, j + 1, w, n, gs->h + 32, ctx->partial, active, ctx->stream));
@@ -872,6 +926,71 @@ ite_status local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cp
   return ITE_OK;
 }
 
+// Mixed modes (reading c13 of the local solve): iterative refinement.  The
+// residual r = B - (alpha X + c H_eff X) comes from the FP64-class
+// contraction; each correction solves (alpha + c H_eff) D = r by one
+// GMRES(m) cycle from D = 0 whose matvecs use low-precision operands, then
+// X += D.  Stops when |r| <= refine_tol |B| or after refine_max corrections.
+// A correction that leaves |r| above half its previous value moves the inner
+// matvecs up one precision (bf16 -> tf32 -> FP64-class); blocks too small for
+// the tensor-core tiles use the FP64-class matvec throughout.
+ite_status local_solve_mixed(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, const cplx* L,
+                             const cplx* R, const cplx* B, cplx* X, cplx alpha, cplx c, int m,
+                             int precision, int refine_max, double refine_tol, int* steps,
+                             double* res) {
+  const int d = H->d;
+  const long long n = (long long)chl * d * d * chr;
+  CS(buf_ensure(ctx, ctx->ws_R, (size_t)n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_D, (size_t)n * sizeof(cplx)));
+  cplx* r = P<cplx>(ctx->ws_R);
+  cplx* D = P<cplx>(ctx->ws_D);
+  struct LevelGuard {
+    ite_ctx c;
+    ~LevelGuard() { c->lp_level = -1; }
+  } guard{ctx};
+  ctx->lp_level = -1;
+  const double work = (double)H->D[i] * d * d * chl * (double)chl * chr;
+  int level = precision == ITE_MIXED_TF32 ? 1 : 0;
+  if (work < kEmuMinWork || chl < 16 || chr < 16) level = 2;
+  int prepared = -1, total = 0;
+  double rho = 0.0, rho_prev = 0.0, bnorm = 0.0;
+  for (int it = 0;; ++it) {
+    // r = B - alpha X - c H_eff X (FP64-class)
+    ctx->lp_level = -1;
+    CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, X, r, csub(C(0), c), X, csub(C(0), alpha)));
+    CK(vec_axpby(r, B, C(1), C(1), n, ctx->stream));
+    CK(vec_norm2(r, n, ctx->dscal + 3, ctx->dscal + 16, nullptr, ctx->stream));
+    if (it == 0) CK(vec_norm2(B, n, ctx->dscal + 4, ctx->dscal + 16, nullptr, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hr->d[0], ctx->dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CS(sync(ctx));
+    rho = std::sqrt(ctx->hr->d[0]);
+    if (it == 0) bnorm = std::sqrt(ctx->hr->d[1]);
+    if (!std::isfinite(rho)) return fail(ctx, ITE_ESINGULAR, "non-finite residual in the refinement");
+    if (!(bnorm > 0.0) || rho <= refine_tol * bnorm || it >= refine_max) break;
+    if (it > 0 && rho > 0.5 * rho_prev && level < 2) ++level;
+    rho_prev = rho;
+    if (level < 2 && prepared != level) {
+      CS(heff_lp_setup(ctx, H, i, chl, chl, chr, chr, L, R, level));
+      prepared = level;
+    }
+    CK(vec_zero(D, n, ctx->stream));
+    ctx->lp_level = level < 2 ? level : -1;
+    int k = 0;
+    double rr = 0.0;
+    CS(gmres_cycle(ctx, H, i, chl, chr, L, R, r, D, alpha, c, m, 0.0, &k, &rr));
+    ctx->lp_level = -1;
+    total += k;
+    ctx->refinements += 1;
+    CK(vec_axpby(X, D, C(1), C(1), n, ctx->stream));
+  }
+  if (steps) *steps = total;
+  if (res) *res = bnorm > 0.0 ? rho / bnorm : 0.0;
+  return ITE_OK;
+}
+
+bool mixed_precision(int p) { return p == ITE_MIXED_BF16 || p == ITE_MIXED_TF32; }
+
 // Two-site sweep solving (alpha I + c H) x = b, or (fit mode) x ~ alpha b + beta H b.
 ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, cplx alpha, cplx cbeta,
                  int chi_max, double cutoff, const ite_solver_opts& o, SweepStats& stats) {
@@ -902,8 +1021,12 @@ ite_status sweep(ite_ctx ctx, ite_mpo H, ite_mps x, ite_mps b, bool fit, cplx al
         CS(project(ctx, d, chl, bl, bm, br, chr, e.LO[i], b->site[i], b->site[i + 1], e.RO[i + 2], B));
         int steps = 0;
         double res = 0.0;
-        CS(local_solve(ctx, H, i, chl, chr, e.LE[i], e.RE[i + 2], B, X, alpha, cbeta, o.krylov_dim,
-                       o.max_cycles, o.local_tol, &steps, &res));
+        if (mixed_precision(o.precision))
+          CS(local_solve_mixed(ctx, H, i, chl, chr, e.LE[i], e.RE[i + 2], B, X, alpha, cbeta,
+                               o.krylov_dim, o.precision, o.refine_max, o.refine_tol, &steps, &res));
+        else
+          CS(local_solve(ctx, H, i, chl, chr, e.LE[i], e.RE[i + 2], B, X, alpha, cbeta, o.krylov_dim,
+                         o.max_cycles, o.local_tol, &steps, &res));
         stats.steps += steps;
         stats.max_res = std::max(stats.max_res, res);
       } else {
@@ -1080,6 +1203,8 @@ void ite_solver_opts_default(ite_solver_opts* o) {
   o->sweep_tol = 0.0;
   o->fit_sweeps = 1;
   o->precision = ITE_FP64;
+  o->refine_max = 10;
+  o->refine_tol = 1e-10;
 }
 
 ite_status ite_ctx_create(int device, void* stream, ite_alloc_fn alloc, ite_free_fn release,
@@ -1133,7 +1258,8 @@ void ite_ctx_destroy(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu, &ctx->ws_ovm};
+                 &ctx->ws_emu, &ctx->ws_ovm, &ctx->ws_lpops, &ctx->ws_lpscr, &ctx->ws_R,
+                 &ctx->ws_D};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
@@ -1318,7 +1444,8 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
       (scheme != ITE_BACKWARD_EULER && scheme != ITE_TRAPEZOID &&
        scheme != ITE_GAUSS_LEGENDRE_2 && scheme != ITE_GAUSS_LEGENDRE_3 &&
        scheme != ITE_FORWARD_EULER && scheme != ITE_HEUN) ||
-      (o.precision != ITE_FP64 && o.precision != ITE_FP64_TC) || psi->N < 2)
+      (o.precision != ITE_FP64 && o.precision != ITE_FP64_TC && !mixed_precision(o.precision)) ||
+      (mixed_precision(o.precision) && (o.refine_max < 0 || !(o.refine_tol >= 0.0))) || psi->N < 2)
     return fail(ctx, ITE_EINVAL, "invalid step arguments");
   CS(ensure_work(ctx, psi));
   CS(ensure_workspace(ctx, H, psi->cap, psi->d, o.krylov_dim));
@@ -1327,7 +1454,7 @@ ite_status step_impl(ite_ctx ctx, ite_mpo H, ite_mps psi, double dtau, int schem
     ite_ctx c;
     ~ModeGuard() { c->gemm_mode = 0; }
   } mode_guard{ctx};
-  ctx->gemm_mode = o.precision == ITE_FP64_TC ? 1 : 0;
+  ctx->gemm_mode = o.precision == ITE_FP64 ? 0 : 1;
   CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
   SweepStats st;
   ite_mps x = psi->work_x;
@@ -2133,9 +2260,40 @@ ite_status ite_correlator(ite_ctx ctx, ite_mps psi, const double* O, int i, cons
 
 // ------------------------------------------------------------------ kernel-level entry points
 ite_status ite_ctx_set_kernel_precision(ite_ctx ctx, int precision) {
-  if (!ctx || (precision != ITE_FP64 && precision != ITE_FP64_TC)) return ITE_EINVAL;
+  if (!ctx || (precision != ITE_FP64 && precision != ITE_FP64_TC && !mixed_precision(precision)))
+    return ITE_EINVAL;
   ctx->kernel_precision = precision;
   return ITE_OK;
+}
+
+ite_status ite_k_heff_lp_prepare(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                                 int chr_ket, int chr_bra, const double* L, const double* R,
+                                 int precision) {
+  if (!ctx || !H || !L || !R || i < 0 || i + 1 >= H->N || chl_bra < 1 || chl_ket < 1 ||
+      chr_ket < 1 || chr_bra < 1 || !mixed_precision(precision))
+    return ITE_EINVAL;
+  CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
+  CS(heff_lp_setup(ctx, H, i, chl_bra, chl_ket, chr_ket, chr_bra, (const cplx*)L, (const cplx*)R,
+                   precision == ITE_MIXED_TF32 ? 1 : 0));
+  return kernel_finish(ctx);
+}
+
+ite_status ite_k_heff_lp_apply(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                               int chr_ket, int chr_bra, const double* X, double* Y,
+                               const double alpha[2], const double* Z, const double gamma[2]) {
+  if (!ctx || !H || !X || !Y || !alpha || i < 0 || i + 1 >= H->N || chl_bra < 1 || chl_ket < 1 ||
+      chr_ket < 1 || chr_bra < 1)
+    return ITE_EINVAL;
+  CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
+  struct LevelGuard {
+    ite_ctx c;
+    ~LevelGuard() { c->lp_level = -1; }
+  } guard{ctx};
+  ctx->lp_level = ctx->lp_prep.level;
+  const cplx g = gamma ? C(gamma[0], gamma[1]) : C(0);
+  CS(heff_lp(ctx, H, i, chl_bra, chl_ket, chr_ket, chr_bra, (const cplx*)X, (cplx*)Y,
+             C(alpha[0], alpha[1]), (const cplx*)Z, g));
+  return kernel_finish(ctx);
 }
 
 ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_ket,
@@ -2198,11 +2356,39 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   CS(buf_ensure(ctx, ctx->ws_T2, (size_t)H->Dmax * n * sizeof(cplx)));
   int s = 0;
   double r = 0.0;
-  CS(local_solve(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B, (cplx*)X,
-                 C(alpha), C(c), krylov_dim, 1, local_tol, &s, &r));
+  if (mixed_precision(ctx->kernel_precision))
+    CS(local_solve_mixed(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B,
+                         (cplx*)X, C(alpha), C(c), krylov_dim, ctx->kernel_precision, 20,
+                         local_tol > 0.0 ? local_tol : 1e-10, &s, &r));
+  else
+    CS(local_solve(ctx, H, i, chl, chr, (const cplx*)L, (const cplx*)R, (const cplx*)B, (cplx*)X,
+                   C(alpha), C(c), krylov_dim, 1, local_tol, &s, &r));
   if (steps) *steps = s;
   if (rel_res) *rel_res = r;
   return kernel_finish(ctx);
+}
+
+ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void* A, long long lda,
+                         long long sAb, const void* B, long long ldb, long long sBb, float* Cm,
+                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits) {
+  const int eb = tf32 ? 4 : 2;
+  if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || batch < 1 || lda < K || ldb < K ||
+      ldc < N || (lda * eb) % 16 || (ldb * eb) % 16 || (sAb * eb) % 16 || (sBb * eb) % 16 ||
+      sAb < 0 || sBb < 0 || sCb < 0 || sCs < 0 || (bn != 128 && bn != 256) || splits < 1 ||
+      (splits > 1 && sCs == 0))
+    return ITE_EINVAL;
+  int* err = reinterpret_cast<int*>(ctx->dcounter) + 8;
+  CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  LpGemmArgs g = {};
+  g.M = M; g.N = N; g.K = K; g.batch = batch; g.splits = splits; g.bn = bn; g.tf32 = tf32 != 0;
+  g.A = A; g.lda = lda; g.sAb = sAb;
+  g.B = B; g.ldb = ldb; g.sBb = sBb;
+  g.C = Cm; g.ldc = ldc; g.sCb = sCb; g.sCs = sCs;
+  CK(lp_gemm(g, err, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->counter, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CS(sync(ctx));
+  if (ctx->hr->counter != 0) return fail(ctx, ITE_ETIMEOUT, "tensor-core GEMM wait ran out");
+  return ITE_OK;
 }
 
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
@@ -2315,8 +2501,10 @@ void internal_release_workspace(ite_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
-                 &ctx->ws_emu, &ctx->ws_ovm};
+                 &ctx->ws_emu, &ctx->ws_ovm, &ctx->ws_lpops, &ctx->ws_lpscr, &ctx->ws_R,
+                 &ctx->ws_D};
   for (Buf* b : bufs) buf_free(ctx, *b);
+  ctx->lp_prep = ite_ctx_s::LpPrepared();
 }
 
 }  // namespace ite

@@ -1,0 +1,317 @@
+// Two-site H_eff in low precision (bf16 or tf32 operands, fp32 accumulation on
+// the tensor cores) for the inner solves of the mixed-precision mode:
+//
+//   Y[a,s',t',b] = alpha sum L[w][a][a'] W2[w s t -> w'' s' t'] R[w''][b'][b]
+//                        X[a',s,t,b'] + gamma Z[a,s',t',b]
+//
+// in three contractions, the same order as the FP64 path (App. B's two-site
+// effective Hamiltonian):
+//   1. T1_w = L_w X for every MPO channel w: one batched real GEMM of the
+//      row-embedded L (rows 2a, 2a+1 = [Re, -Im], [Im, Re] along a') with the
+//      K-major X^T ((Re, Im) interleaved along a'), giving Re and Im rows;
+//   2. T2[(a s' t')][(w'' b')] = sum over the non-zero two-site MPO entries of
+//      T1[w][a][(s t b')]: the channel/physical mix, written as the K-major
+//      complex-interleaved A operand of step 3;
+//   3. Y32 = T2 R~ with the column-embedded R~ (rows 2b, 2b+1 = [Re, -Im],
+//      [Im, Re] along (w'' b')), whose fp32 output is complex-interleaved;
+//   then Y = alpha Y32 + gamma Z in FP64.
+// The embedded L and R depend only on the environments, so a local solve
+// prepares them once (heff_lp_prepare) and reuses them for every matvec.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ite {
+namespace {
+
+template <bool TF32>
+struct Lp;
+template <>
+struct Lp<false> {
+  typedef __nv_bfloat16 T;
+  static __device__ __forceinline__ T from(double x) { return __double2bfloat16(x); }
+  static __device__ __forceinline__ T fromf(float x) { return __float2bfloat16_rn(x); }
+};
+template <>
+struct Lp<true> {
+  typedef float T;
+  static __device__ __forceinline__ float fromf(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+  }
+  static __device__ __forceinline__ float from(double x) { return fromf((float)x); }
+};
+
+// Lemb[w][2a + co][2a' + ci] from L[w][a][a'] (chlB x chlK per channel)
+template <bool TF32>
+__global__ void k_lp_embed_L(const cplx* __restrict__ L, int D0, int chlB, int chlK,
+                             typename Lp<TF32>::T* __restrict__ out, long long ld) {
+  typedef typename Lp<TF32>::T T;
+  const long long tot = (long long)D0 * chlB * chlK;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % chlK);
+    const long long wa = e / chlK;
+    const int a = (int)(wa % chlB), w = (int)(wa / chlB);
+    const cplx v = L[e];
+    const T re = Lp<TF32>::from(v.x), im = Lp<TF32>::from(v.y), mim = Lp<TF32>::from(-v.y);
+    T* r0 = out + ((long long)w * 2 * chlB + 2 * a) * ld + 2 * k;
+    T* r1 = r0 + ld;
+    r0[0] = re;
+    r0[1] = mim;
+    r1[0] = im;
+    r1[1] = re;
+  }
+}
+
+// Remb[2b + co][2(w chrK + b') + ci] from R[w][b'][b] (chrK x chrB per channel)
+template <bool TF32>
+__global__ void k_lp_embed_R(const cplx* __restrict__ R, int D2, int chrK, int chrB,
+                             typename Lp<TF32>::T* __restrict__ out, long long ld) {
+  typedef typename Lp<TF32>::T T;
+  const long long tot = (long long)D2 * chrK * chrB;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e % chrB);
+    const long long k = e / chrB;                      // w chrK + b'
+    const cplx v = R[e];
+    const T re = Lp<TF32>::from(v.x), im = Lp<TF32>::from(v.y), mim = Lp<TF32>::from(-v.y);
+    T* r0 = out + (long long)(2 * b) * ld + 2 * k;
+    T* r1 = r0 + ld;
+    r0[0] = re;
+    r0[1] = mim;
+    r1[0] = im;
+    r1[1] = re;
+  }
+}
+
+// XT[n][2a' + c] = X[a'][n] (re, im), a 32 x 32 tile transpose through
+// shared memory: coalesced reads along n, paired writes along a'
+template <bool TF32>
+__global__ void k_lp_xt(const cplx* __restrict__ X, int rows, long long n_cols,
+                        typename Lp<TF32>::T* __restrict__ XT, long long ld) {
+  typedef typename Lp<TF32>::T T;
+  __shared__ cplx tile[32][33];
+  const long long n0 = (long long)blockIdx.x * 32;
+  const int a0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int a = a0 + y;
+    const long long n = n0 + threadIdx.x;
+    if (a < rows && n < n_cols) tile[y][threadIdx.x] = X[(long long)a * n_cols + n];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const long long n = n0 + y;
+    const int a = a0 + threadIdx.x;
+    if (a < rows && n < n_cols) {
+      const cplx v = tile[threadIdx.x][y];
+      T* dst = XT + n * ld + 2 * a;
+      dst[0] = Lp<TF32>::from(v.x);
+      dst[1] = Lp<TF32>::from(v.y);
+    }
+  }
+}
+
+// T2[(a s' t')][2 (w'' chrK + b') + c] = sum_e val_e T1[w_e][a][(s_e t_e) chrK + b']
+// with T1[w][2a + c][n] fp32 (n = (s t) chrK + b'); the plan's rows are
+// (s', t', w''), its columns (w, s, t).  One thread per (a, b').
+template <bool TF32>
+__global__ void k_lp_mix(MixPlan pl, const float* __restrict__ T1, int chlB, int chrK, int d,
+                         int D2, long long N1, typename Lp<TF32>::T* __restrict__ T2,
+                         long long ld2) {
+  typedef typename Lp<TF32>::T T;
+  const int bp = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (bp >= chrK) return;
+  const int dd = d * d;
+  const long long wstride = 2LL * chlB * N1;
+  const float* base = T1 + (2LL * a) * N1 + bp;
+  for (int k = 0; k < pl.nrows; ++k) {
+    float re = 0.f, im = 0.f;
+    const int e1 = __ldg(pl.row_ptr + k + 1);
+    for (int e = __ldg(pl.row_ptr + k); e < e1; ++e) {
+      const int j = __ldg(pl.col + e);                  // (w d + s) d + t
+      const int w = j / dd, st = j - w * dd;
+      const float* p = base + w * wstride + (long long)st * chrK;
+      const float xr = p[0], xi = p[N1];
+      const cplx v = pl.val[e];
+      const float vr = (float)v.x, vi = (float)v.y;
+      re = fmaf(vr, xr, fmaf(-vi, xi, re));
+      im = fmaf(vr, xi, fmaf(vi, xr, im));
+    }
+    const int wpp = k % D2, spt = k / D2;               // k = (s' d + t') D2 + w''
+    T* dst = T2 + ((long long)a * dd + spt) * ld2 + 2LL * ((long long)wpp * chrK + bp);
+    dst[0] = Lp<TF32>::fromf(re);
+    dst[1] = Lp<TF32>::fromf(im);
+  }
+}
+
+// Y[m][b] = alpha sum_sp (Y32[sp][m][2b], Y32[sp][m][2b+1]) + gamma Z[m][b]
+__global__ void k_lp_combine(const float* __restrict__ Y32, int splits, long long slab, long long M,
+                             int ncols, cplx alpha, const cplx* __restrict__ Z, cplx gamma,
+                             cplx* __restrict__ Y) {
+  const long long tot = M * ncols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+      const float2 v = reinterpret_cast<const float2*>(Y32 + sp * slab)[e];
+      re += v.x;
+      im += v.y;
+    }
+    cplx out = cmul(alpha, cmake(re, im));
+    if (Z) out = cadd(out, cmul(gamma, Z[e]));
+    Y[e] = out;
+  }
+}
+
+int grid_of(long long tot, int threads) {
+  long long g = (tot + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// The N tile and K split of one GEMM, from a model of its time on `sms` SMs:
+// waves of units, each costing its MMA work plus a fixed epilogue share.
+void pick_tiles(int M, int N, int K, int batch, bool tf32, int sms, int* bn, int* splits) {
+  const int BK = tf32 ? 32 : 64;
+  const int nkb = (K + BK - 1) / BK;
+  double best = 1e300;
+  *bn = 256;
+  *splits = 1;
+  for (int b : {256, 128}) {
+    const long long tiles = (long long)batch * ((M + 127) / 128) * ((N + b - 1) / b);
+    for (int s = 1; s <= 8; ++s) {
+      if (s > 1 && nkb / s < 4) break;
+      const long long per = (nkb + s - 1) / s;
+      const long long units = tiles * s;
+      const long long waves = (units + sms - 1) / sms;
+      // MMA time ~ b columns x per k-tiles (a 128-wide tile runs at about
+      // 0.8 of the 256-wide rate); epilogue ~ b columns; split-K adds a pass
+      const double t = waves * (b * per * (b == 128 ? 1.25 : 1.0) + 4.0 * b) + (s > 1 ? 0.02 * M * (double)N / sms : 0.0);
+      if (t < best) {
+        best = t;
+        *bn = b;
+        *splits = s;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t heff_lp_operand_bytes(int D0, int D2, int chlB, int chlK, int chrK, int chrB, bool tf32) {
+  const int eb = tf32 ? 4 : 2, al = 16 / eb;
+  const long long ldl = round_up(2LL * chlK, al), ldr = round_up(2LL * D2 * chrK, al);
+  return (size_t)(D0 * 2LL * chlB * ldl + 2LL * chrB * ldr) * eb + 512;
+}
+
+size_t heff_lp_scratch_bytes(int d, int D0, int D2, int chlB, int chlK, int chrK, int chrB,
+                             bool tf32) {
+  const int eb = tf32 ? 4 : 2, al = 16 / eb;
+  const long long N1 = (long long)d * d * chrK, M3 = (long long)chlB * d * d;
+  const long long ldx = round_up(2LL * chlK, al), ld2 = round_up(2LL * D2 * chrK, al);
+  const size_t xt = (size_t)N1 * ldx * eb;
+  const size_t t1 = (size_t)D0 * 2 * chlB * N1 * 4;
+  const size_t t2 = (size_t)M3 * ld2 * eb;
+  const size_t y32 = (size_t)8 * M3 * 2 * chrB * 4;
+  return xt + t1 + t2 + y32 + 4 * 256;
+}
+
+cudaError_t heff_lp_prepare(const cplx* L, const cplx* R, int D0, int D2, int chlB, int chlK,
+                            int chrK, int chrB, bool tf32, void* ops, size_t ops_bytes,
+                            cudaStream_t st) {
+  if (ops_bytes < heff_lp_operand_bytes(D0, D2, chlB, chlK, chrK, chrB, tf32))
+    return cudaErrorInvalidValue;
+  const int eb = tf32 ? 4 : 2, al = 16 / eb;
+  const long long ldl = round_up(2LL * chlK, al), ldr = round_up(2LL * D2 * chrK, al);
+  char* p = static_cast<char*>(ops);
+  void* Lemb = p;
+  void* Remb = p + round_up((long long)D0 * 2 * chlB * ldl * eb, 256);
+  const long long nl = (long long)D0 * chlB * chlK, nr = (long long)D2 * chrK * chrB;
+  count_launches(2);
+  if (tf32) {
+    k_lp_embed_L<true><<<grid_of(nl, 256), 256, 0, st>>>(L, D0, chlB, chlK, (float*)Lemb, ldl);
+    k_lp_embed_R<true><<<grid_of(nr, 256), 256, 0, st>>>(R, D2, chrK, chrB, (float*)Remb, ldr);
+  } else {
+    k_lp_embed_L<false><<<grid_of(nl, 256), 256, 0, st>>>(L, D0, chlB, chlK, (__nv_bfloat16*)Lemb, ldl);
+    k_lp_embed_R<false><<<grid_of(nr, 256), 256, 0, st>>>(R, D2, chrK, chrB, (__nv_bfloat16*)Remb, ldr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, int D2, int chlB,
+                          int chlK, int chrK, int chrB, bool tf32, const cplx* X, cplx* Y,
+                          cplx alpha, const cplx* Z, cplx gamma, void* scratch,
+                          size_t scratch_bytes, int* err, cudaStream_t st) {
+  if (scratch_bytes < heff_lp_scratch_bytes(d, D0, D2, chlB, chlK, chrK, chrB, tf32))
+    return cudaErrorInvalidValue;
+  const int eb = tf32 ? 4 : 2, al = 16 / eb;
+  const long long N1 = (long long)d * d * chrK, M3 = (long long)chlB * d * d;
+  const long long ldl = round_up(2LL * chlK, al), ldr = round_up(2LL * D2 * chrK, al);
+  const long long ldx = round_up(2LL * chlK, al), ld2 = round_up(2LL * D2 * chrK, al);
+  const char* po = static_cast<const char*>(ops);
+  const void* Lemb = po;
+  const void* Remb = po + round_up((long long)D0 * 2 * chlB * ldl * eb, 256);
+  char* p = static_cast<char*>(scratch);
+  void* XT = p;
+  p += round_up(N1 * ldx * eb, 256);
+  float* T1 = reinterpret_cast<float*>(p);
+  p += round_up((long long)D0 * 2 * chlB * N1 * 4, 256);
+  void* T2 = p;
+  p += round_up(M3 * ld2 * eb, 256);
+  float* Y32 = reinterpret_cast<float*>(p);
+  const int sms = lp_gemm_sm_count() > 0 ? lp_gemm_sm_count() : 148;
+  cudaError_t e;
+  // 0. X^T in the operand precision
+  {
+    dim3 grid((unsigned)((N1 + 31) / 32), (unsigned)((chlK + 31) / 32));
+    count_launches(1);
+    if (tf32) k_lp_xt<true><<<grid, dim3(32, 8), 0, st>>>(X, chlK, N1, (float*)XT, ldx);
+    else k_lp_xt<false><<<grid, dim3(32, 8), 0, st>>>(X, chlK, N1, (__nv_bfloat16*)XT, ldx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // 1. T1[w] = Lemb[w] XT^T: (2 chlB) x N1 per channel, K = 2 chlK
+  {
+    LpGemmArgs g = {};
+    g.M = 2 * chlB; g.N = (int)N1; g.K = 2 * chlK; g.batch = D0; g.tf32 = tf32;
+    g.A = Lemb; g.lda = ldl; g.sAb = 2LL * chlB * ldl;
+    g.B = XT; g.ldb = ldx; g.sBb = 0;
+    g.C = T1; g.ldc = N1; g.sCb = 2LL * chlB * N1; g.sCs = 0;
+    pick_tiles(g.M, g.N, g.K, g.batch, tf32, sms, &g.bn, &g.splits);
+    g.splits = 1;                       // the mix reads one T1 slab
+    if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;
+  }
+  // 2. mix into the K-major complex-interleaved T2
+  {
+    dim3 grid((unsigned)((chrK + 127) / 128), (unsigned)chlB);
+    count_launches(1);
+    if (tf32) k_lp_mix<true><<<grid, 128, 0, st>>>(plan2, T1, chlB, chrK, d, D2, N1, (float*)T2, ld2);
+    else k_lp_mix<false><<<grid, 128, 0, st>>>(plan2, T1, chlB, chrK, d, D2, N1, (__nv_bfloat16*)T2, ld2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // 3. Y32[sp] = T2 Remb^T: M3 x (2 chrB), K = 2 D2 chrK, split over K
+  int splits = 1;
+  {
+    LpGemmArgs g = {};
+    g.M = (int)M3; g.N = 2 * chrB; g.K = (int)(2LL * D2 * chrK); g.batch = 1; g.tf32 = tf32;
+    g.A = T2; g.lda = ld2; g.sAb = 0;
+    g.B = Remb; g.ldb = ldr; g.sBb = 0;
+    g.C = Y32; g.ldc = 2LL * chrB; g.sCb = 0; g.sCs = M3 * 2LL * chrB;
+    pick_tiles(g.M, g.N, g.K, 1, tf32, sms, &g.bn, &g.splits);
+    splits = lp_gemm_splits_used(g);
+    if (splits > 8) return cudaErrorInvalidValue;
+    if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;
+  }
+  // 4. Y = alpha Y32 + gamma Z
+  count_launches(1);
+  k_lp_combine<<<grid_of(M3 * chrB, 256), 256, 0, st>>>(Y32, splits, M3 * 2LL * chrB, M3, chrB,
+                                                         alpha, Z, gamma, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace ite
