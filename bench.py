@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--bonds", type=int, default=6, help="bulk bonds in the CPU sample")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="steps of the timed sequence replayed in plain FP64 for comparison")
+    ap.add_argument("--mixed-steps", type=int, default=3,
+                    help="steps of the sequence replayed with converged local solves, mixed bf16 "
+                         "against plain FP64 (equal accuracy)")
     ap.add_argument("--precision", choices=["fp64", "fp64_tc", "mixed_bf16", "mixed_tf32"],
                     default="fp64_tc",
                     help="fp64: FP64 pipes; fp64_tc: FP64-class contractions on the tensor cores; "
@@ -76,14 +79,20 @@ def parse():
                     help="time one kernel-level call at the bulk shape (for profiler captures)")
     ap.add_argument("--scheme", choices=["be", "tr", "gl2", "gl3"], default="be",
                     help="time stepper of the chain workload (the headline runs backward Euler)")
-    ap.add_argument("--workload", choices=["chain", "batch", "chi_study", "metts"],
+    ap.add_argument("--workload", choices=["chain", "batch", "chi_study", "metts", "anderson",
+                                           "serve"],
                     default="chain",
                     help="batch: a bounded sample of the batched workload served side by side; "
                          "chi_study: bond-dimension growth and step cost of an evolution; "
-                         "metts: independent METTS chains served side by side")
+                         "metts: independent METTS chains served side by side; "
+                         "anderson: the first steps of the impurity-model evolution; "
+                         "serve: a Poisson stream of impurity evolutions through the server")
     ap.add_argument("--lp-shape", default="all",
                     help="--only heff_lp: all, heisenberg512, heisenberg1024 or anderson512")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--serve-baths", default="9,19,29", help="serve: bath sizes drawn from")
+    ap.add_argument("--serve-chis", default="16,32,64", help="serve: bond caps drawn from")
     ap.add_argument("--slots", type=int, default=4, help="concurrent jobs in the batch sample")
     ap.add_argument("--study-n", type=int, default=100, help="chain length of the chi study")
     ap.add_argument("--study-m", type=int, default=8, help="chi study runs to tau_max = 2^m")
@@ -357,11 +366,12 @@ def heff_lp_rates(api, ctx, precisions=("mixed_bf16",), reps=10, shapes=LP_SHAPE
     return out
 
 
-def reference_energies():
-    """Oracle energies of the first steps of the timed sequence (fixed mode,
-    backward Euler, from the start state), written by
-    tests/golden/make_bench_reference.py; None when absent."""
-    path = os.path.join(ROOT, "tests", "golden", "bench_reference_energies.json")
+def reference_energies(converged=False):
+    """Oracle energies of the first steps of the timed sequence (backward
+    Euler from the start state; fixed effort or converged local solves),
+    written by tests/golden/make_bench_reference.py; None when absent."""
+    name = "bench_reference_energies" + ("_converged" if converged else "") + ".json"
+    path = os.path.join(ROOT, "tests", "golden", name)
     try:
         with open(path) as f:
             return json.load(f)
@@ -496,6 +506,43 @@ def run_ours(args, rank, world, local_rank):
                 "max_rel_energy_diff_vs_this_precision": max(
                     abs(a["energy"] - b["energy"]) / abs(b["energy"]) for a, b in zip(infos64, infos))}
 
+    # ---- equal accuracy: local solves converged, mixed bf16 refinement
+    # against plain FP64 GMRES restarted to the same relative residual
+    mixed = None
+    nmx = min(args.steps, args.mixed_steps)
+    if nmx > 0 and rank == 0:
+        arms = {}
+        for name, o in (("mixed_bf16", api.solver_opts(precision="mixed_bf16", refine_tol=1e-10,
+                                                        refine_max=20)),
+                        ("fp64_converged", api.solver_opts(precision="fp64", local_tol=1e-10,
+                                                           max_cycles=200))):
+            evx = [torch.cuda.Event(enable_timing=True) for _ in range(nmx)]
+            x0 = torch.cuda.Event(enable_timing=True)
+            barrier()
+            x0.record(stream)
+            inf_x = run(nmx, o, events=evx)
+            barrier()
+            msx = x0.elapsed_time(evx[-1])
+            arms[name] = {"steps": nmx, "ms_per_step": msx / nmx, "tau_steps_per_s": nmx / (msx * 1e-3),
+                          "energies": [i["energy"] for i in inf_x],
+                          "max_local_residual": max(i["max_local_residual"] for i in inf_x)}
+        ref_c = reference_energies(converged=True)
+        if ref_c is not None:
+            e_ref = ref_c["energies"]
+            for name, a in arms.items():
+                n = min(len(e_ref), nmx)
+                a["delta_e_vs_converged_oracle"] = max(abs(a["energies"][k] - e_ref[k]) / abs(e_ref[k])
+                                                       for k in range(n))
+        mixed = {"what": ("the same steps with every local solve converged: mixed bf16 "
+                          "(refinement to |r| <= 1e-10 |B|, bf16 inner GMRES(10), FP64-class "
+                          "residuals) against plain FP64 GMRES(10) restarted to |r| <= 1e-10 |B|"),
+                 **arms,
+                 "speedup_mixed_over_fp64": arms["fp64_converged"]["ms_per_step"]
+                 / arms["mixed_bf16"]["ms_per_step"],
+                 "max_rel_energy_diff": max(abs(a - b) / abs(b) for a, b in
+                                            zip(arms["mixed_bf16"]["energies"],
+                                                arms["fp64_converged"]["energies"]))}
+
     ref = reference_energies()
     delta_e = None
     if ref is not None and ref.get("scheme") == args.scheme and rank == 0:
@@ -511,6 +558,7 @@ def run_ours(args, rank, world, local_rank):
             delta_e["fp64_steps"] = n
 
     heff_rates = heff_kernel_rates(api, ctx, H, args.precision) if rank == 0 else None
+    lp_rates = heff_lp_rates(api, ctx, ("mixed_bf16", "mixed_tf32")) if rank == 0 else None
 
     heff = prof["heff"]
     heff_tf = heff["flops"] / (heff["ms"] * 1e-3) / 1e12 if heff["ms"] > 0 else 0.0
@@ -557,6 +605,8 @@ def run_ours(args, rank, world, local_rank):
             "heff_kernel": {"precision": args.precision, "shapes": "d=2, D=5, chi_l=chi_r=chi",
                             **(heff_rates or {})},
             "fp64_arm": fp64,
+            "equal_accuracy": mixed,
+            "heff_lp_kernel": lp_rates,
             "delta_e_vs_oracle": delta_e,
             "stage_ms_per_step": breakdown,
             "step_ms": [round(x, 3) for x in step_ms],
@@ -726,6 +776,136 @@ def run_chi_study(args):
     print(json.dumps(out), flush=True)
 
 
+def run_anderson(args):
+    """The first --steps steps of the Anderson-impurity evolution: impurity plus
+    99 bath sites (N = 100, d = 4, MPO bond dimension 6), flat band of
+    half-bandwidth 1 linearly discretised, Gamma = 0.05, U = 0.3, eps_d = -U/2,
+    chi_max = 512, cutoff 1e-14, backward Euler on the geometric grid
+    1e-2 -> 1e4 (50 steps), shift = the current energy (App. D), from a seeded
+    random product state (seed 3000), in --precision.  Every step is one
+    synchronous call timed by CUDA events on the context stream, with the
+    library's stage timers.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    from paper_2606_02930_gb300 import api, inputs
+    torch.cuda.init()
+    n_bath, chi, cutoff = 99, 512, 1e-14
+    eps, V = inputs.flat_band_bath(n_bath)
+    ctx = api.ctx_create(0)
+    H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
+    vecs = inputs.random_product_state(n_bath + 1, 4, 3000)
+    psi = api.mps_create_product(ctx, vecs, chi)
+    nodes = api.grid_geometric(1e-2, 1e4, 50)
+    opts = api.solver_opts(precision=args.precision)
+    s = api.energy(ctx, H, psi)
+    stream = torch.cuda.current_stream()
+    steps = []
+    api.svd_stats(ctx)
+    for k in range(args.steps):
+        api.profile_start(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = api.implicit_step(ctx, H, psi, nodes[k + 1] - nodes[k], "be", s, chi, cutoff, opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = api.profile_stop(ctx)
+        svd = api.svd_stats(ctx)
+        ms = e0.elapsed_time(e1)
+        s = info["energy"]
+        steps.append({"k": k, "dtau": float(nodes[k + 1] - nodes[k]), "ms": ms,
+                      "energy": info["energy"], "max_chi": info["max_chi"],
+                      "max_discarded_weight": info["max_discarded_weight"],
+                      "gmres_steps": info["gmres_steps"],
+                      "max_local_residual": info["max_local_residual"],
+                      "stage_shares": {kk: round(v["ms"] / ms, 4) for kk, v in prof.items()
+                                       if kk != "step" and v["ms"] > 0},
+                      "svd_sweeps_mean": svd["sweeps_mean"]})
+    out = {"workload": "anderson", "metric": "tau-steps/s of the first steps, stage shares",
+           "config": {"model": "Anderson impurity + 99 bath sites (N=100, d=4, D=6), flat band "
+                               "D=1, Gamma=0.05, U=0.3, eps_d=-U/2",
+                      "chi_max": chi, "cutoff": cutoff, "scheme": "backward_euler",
+                      "grid": "geometric 1e-2 -> 1e4, 50 steps", "shift": "current energy",
+                      "start": "random product state, seed 3000", "precision": args.precision},
+           "steps": steps,
+           "tau_steps_per_s": len(steps) / (sum(x["ms"] for x in steps) * 1e-3)}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """A Poisson stream of impurity evolutions through the server, after the
+    served workload's arrival process (mean rate --rate per second, seed 5000)
+    and parameter draws (U ~ U[0.05, 0.6], Gamma ~ U[0.02, 0.1], tau_max from
+    {1e2, 1e3, 1e4}, geometric grids from 1e-2 with ceil(10 log10(tau_max /
+    1e-2)) steps, random product starts), with the bath sizes and bond caps
+    scaled down to --serve-baths and --serve-chis so that the stream finishes
+    in minutes.  The same requests run served (--slots workers, mixed bf16)
+    and one at a time in plain FP64 (1 worker); both arms converge every local
+    solve (refinement / restarted GMRES to 1e-8), so they reach equal
+    accuracy.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    from paper_2606_02930_gb300 import api, inputs
+    torch.cuda.init()
+    rng = np.random.default_rng(5000)
+    n = args.jobs
+    baths = [int(x) for x in args.serve_baths.split(",")]
+    chis = [int(x) for x in args.serve_chis.split(",")]
+    gaps = rng.exponential(1.0 / args.rate, size=n)
+    Us = rng.uniform(0.05, 0.6, n)
+    Gs = rng.uniform(0.02, 0.1, n)
+    nbs = rng.choice(baths, n)
+    cxs = rng.choice(chis, n)
+    tms = rng.choice([1e2, 1e3, 1e4], n)
+
+    def make(prec):
+        if prec == "fp64":
+            o = api.solver_opts(precision="fp64", local_tol=1e-8, max_cycles=200)
+        else:
+            o = api.solver_opts(precision=prec, refine_tol=1e-8, refine_max=20)
+        jobs = []
+        for i in range(n):
+            eps, V = inputs.flat_band_bath(int(nbs[i]), gamma=float(Gs[i]))
+            K = int(np.ceil(10 * np.log10(tms[i] / 1e-2)))
+            jobs.append(api.Job("anderson", int(nbs[i]),
+                                inputs.random_product_state(int(nbs[i]) + 1, 4, 5000 + i),
+                                int(cxs[i]), 1e-14, 1e-2, float(tms[i]), K, scheme="be",
+                                U=float(Us[i]), eps_d=-0.5 * float(Us[i]), eps=eps, V=V, opts=o))
+        return jobs
+
+    def stream(jobs, slots):
+        srv = api.Server(0, n_slots=slots)
+        tickets = []
+        for j, g in zip(jobs, gaps):
+            time.sleep(float(g))
+            tickets.append(srv.submit(j))
+        res = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+        srv.close()
+        assert all(r["status"] == 0 for r in res), [r["status"] for r in res]
+        lat = np.array([r["latency_ms"] for r in res])
+        return {"tau_steps_per_s": st["tau_steps_per_s"], "wall_ms": st["wall_ms"],
+                "p50_latency_ms": float(np.percentile(lat, 50)),
+                "p99_latency_ms": float(np.percentile(lat, 99)),
+                "peak_running": st["peak_running"],
+                "energies": [float(r["energy"]) for r in res]}
+
+    warm = make("mixed_bf16")[:2]
+    api.evolve_batch(warm, n_slots=2)
+    served = stream(make("mixed_bf16"), args.slots)
+    single = stream(make("fp64"), 1)
+    dE = max(abs(a - b) / abs(b) for a, b in zip(served["energies"], single["energies"]))
+    out = {"workload": "serve", "metric": "p50/p99 latency and tau-steps/s of a served stream",
+           "config": {"requests": n, "rate_per_s": args.rate, "seed": 5000,
+                      "bath_sites": baths, "chi_max": chis, "tau_max": [1e2, 1e3, 1e4],
+                      "U": [0.05, 0.6], "Gamma": [0.02, 0.1], "cutoff": 1e-14,
+                      "scaled": "bath sizes and bond caps scaled down from the served "
+                                "workload's {49,99,199} and {128,...,1024}"},
+           "served_mixed_bf16": {k: v for k, v in served.items() if k != "energies"},
+           "one_at_a_time_fp64": {k: v for k, v in single.items() if k != "energies"},
+           "max_rel_energy_diff": dE,
+           "throughput_ratio": served["tau_steps_per_s"] / single["tau_steps_per_s"],
+           "p99_ratio": single["p99_latency_ms"] / served["p99_latency_ms"]}
+    print(json.dumps(out), flush=True)
+
+
 def run_only(args):
     """Time one kernel-level entry point at the workload's bulk shape: the
     two-site H_eff (chi = 256, d = 2, D = 5) or the truncated SVD split of a
@@ -787,6 +967,12 @@ def main():
         return
     if args.workload == "metts":
         run_metts(args)
+        return
+    if args.workload == "anderson":
+        run_anderson(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -126,7 +126,7 @@ ite_status ite_k_barrier_selftest(ite_ctx ctx, int blocks, int absent);
  * for every batch entry b and K split s,
  *   C[b*sCb + s*sCs + m*ldc + n] = sum_{k in split s} A[b*sAb + m*lda + k] B[b*sBb + n*ldb + k]
  * with A, B K-major bf16 (tf32 == 0) or fp32 read as tf32 (tf32 != 0), fp32
- * accumulation in tensor memory, C fp32.  bn (128 or 256) is the N tile; K
+ * accumulation in tensor memory, C fp32.  bn (128, 192 or 256) is the N tile; K
  * is cut into `splits` nearly equal ranges of 128-byte tiles (splits > 1 needs
  * sCs > 0).  Leading dimensions and batch strides are in elements and must be
  * multiples of 16 bytes; pointers 16-byte aligned; a batch stride of 0 shares

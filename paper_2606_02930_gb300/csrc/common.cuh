@@ -62,7 +62,7 @@ cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long 
                          long long ldc, int M, int N, int K, int* err, cudaStream_t st,
                          int bk = 64);
 
-// Low-precision GEMM (lp_gemm.cu): C[b][split] (fp32) = A[b] B[b]^T over the
+// Low-precision GEMM (lp_gemm.cu): C[b][split] (fp32 or bf16) = A[b] B[b]^T over the
 // split's K range, A (M x K) and B (N x K) K-major in bf16 or, with tf32, fp32
 // read as tf32 by kind::tf32 MMAs; fp32 accumulation in TMEM.  Leading
 // dimensions and batch strides in elements, multiples of 16 bytes; a batch
@@ -74,7 +74,8 @@ struct LpGemmArgs {
   bool tf32;
   const void* A; long long lda, sAb;
   const void* B; long long ldb, sBb;
-  float* C; long long ldc, sCb, sCs;
+  void* C; long long ldc, sCb, sCs;   // fp32, or bf16 with out_bf16 (elements)
+  bool out_bf16;
 };
 cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st);
 int lp_gemm_splits_used(const LpGemmArgs& g);
@@ -117,6 +118,7 @@ struct MixPlan {
   int* row_ptr;  // device, nrows+1
   int* col;      // device, nnz
   cplx* val;     // device, nnz
+  float2* val32; // device, nnz: val rounded to fp32 (the low-precision contractions)
 };
 struct MixStrides {
   long long ic[3], oc[3];
@@ -203,15 +205,16 @@ cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cud
 // orthogonal; no rotation is accumulated.  One cooperative launch;
 // dev_state (24 device words) returns the sweeps done in word 5, the pairs
 // examined and rotated in words 6 and 7, and a nonzero word 4 if a bounded
-// wait ran out; stamps (rows ints) and wts (rows doubles) are device
-// scratch.  *anorm2 (device) is |A|_F^2: pairs of
+// wait ran out; stamps (rows ints), wts and nref (rows doubles each: tracked
+// and last computed squared row norms) are device scratch.  *anorm2 (device) is |A|_F^2: pairs of
 // rows whose squared norms are both <= skip_rel |A|_F^2 are left as they are.
 // keep_rank is the most rows the caller will keep: the sweeps stop once only
 // rows that cannot be among them are still rotating (keep_rank >= rows
 // disables this).
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
-                        unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st);
+                        unsigned int* dev_state, int* stamps, double* wts, double* nref,
+                        cudaStream_t st);
 // one cooperative launch of `blocks` blocks meeting at the grid barrier, the
 // first `absent` of them never arriving; word 4 of dev_state ends nonzero
 // when the wait ran out (blocks must be co-resident: at most the SM count)

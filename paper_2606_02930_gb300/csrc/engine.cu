@@ -54,8 +54,8 @@ constexpr double kSvdAlgFlopsPerPQK = 8.7e9 / (512.0 * 512.0 * 512.0);
 // such rows against each other (their total weight is exact regardless).
 double skip_weight(double cutoff) { return 1e-3 * std::max(cutoff, kWeightFloor * 0.1); }
 // small SVD workspace for k rows: sigma, sorted (double), beta (complex),
-// wts (double), perm, stamps, done (int)
-size_t small_bytes(long long k) { return (size_t)k * (3 * sizeof(double) + sizeof(cplx) + 3 * sizeof(int)) + 256; }
+// wts, nref (double), perm, stamps, done (int)
+size_t small_bytes(long long k) { return (size_t)k * (4 * sizeof(double) + sizeof(cplx) + 3 * sizeof(int)) + 256; }
 constexpr int kPartialSlots = 608 * kMaxKrylov;
 
 struct HostRead {
@@ -461,7 +461,8 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   double* sorted = sigma + k;
   cplx* beta = reinterpret_cast<cplx*>(sorted + k);
   double* wts = reinterpret_cast<double*>(beta + k);
-  int* perm = reinterpret_cast<int*>(wts + k);
+  double* nref = wts + k;
+  int* perm = reinterpret_cast<int*>(nref + k);
   int* stamps = perm + k;
   // dcounter words: 8-10 GEMM error flags, 16-39 Jacobi state, 40-47 LQ state
   unsigned int* jstate = reinterpret_cast<unsigned int*>(ctx->dcounter) + 16;
@@ -485,7 +486,7 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   {
     Scope jacobi_scope(ctx, P_JACOBI);
     CK(jacobi_rows(R, k, p, kJacobiSweeps, std::max(1e-15, p * kEps), anorm2, skip_weight(cutoff),
-                   chi_max, jstate, stamps, wts, ctx->stream));
+                   chi_max, jstate, stamps, wts, nref, ctx->stream));
   }
   // 4. singular values, order and rank
   int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
@@ -670,7 +671,8 @@ ite_status mpo_finish(ite_mpo H) {
     hs.push_back(h2);
   }
   size_t bytes = 0;
-  for (auto& h : hs) bytes += (h.rp.size() + h.col.size()) * sizeof(int) + h.val.size() * sizeof(cplx) + 64;
+  for (auto& h : hs)
+    bytes += (h.rp.size() + h.col.size()) * sizeof(int) + h.val.size() * (sizeof(cplx) + sizeof(float2)) + 80;
   CS(buf_ensure(ctx, H->plan_mem, bytes));
   char* base = P<char>(H->plan_mem);
   size_t pos = 0;
@@ -689,6 +691,14 @@ ite_status mpo_finish(ite_mpo H) {
     pl.col = reinterpret_cast<int*>(base + pos);
     CK(cudaMemcpy(pl.col, h.col.data(), h.col.size() * sizeof(int), cudaMemcpyHostToDevice));
     pos += h.col.size() * sizeof(int);
+    pos = (pos + 15) & ~size_t(15);
+    pl.val32 = reinterpret_cast<float2*>(base + pos);
+    {
+      std::vector<float2> v32(h.val.size());
+      for (size_t e = 0; e < h.val.size(); ++e) v32[e] = make_float2((float)h.val[e].x, (float)h.val[e].y);
+      CK(cudaMemcpy(pl.val32, v32.data(), v32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    pos += h.val.size() * sizeof(float2);
     plans.push_back(pl);
   }
   H->planL.resize(N);
@@ -2374,7 +2384,7 @@ ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void
   const int eb = tf32 ? 4 : 2;
   if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || batch < 1 || lda < K || ldb < K ||
       ldc < N || (lda * eb) % 16 || (ldb * eb) % 16 || (sAb * eb) % 16 || (sBb * eb) % 16 ||
-      sAb < 0 || sBb < 0 || sCb < 0 || sCs < 0 || (bn != 128 && bn != 256) || splits < 1 ||
+      sAb < 0 || sBb < 0 || sCb < 0 || sCs < 0 || (bn != 128 && bn != 192 && bn != 256) || splits < 1 ||
       (splits > 1 && sCs == 0))
     return ITE_EINVAL;
   int* err = reinterpret_cast<int*>(ctx->dcounter) + 8;

@@ -65,17 +65,20 @@ __global__ void k_lp_embed_L(const cplx* __restrict__ L, int D0, int chlB, int c
   }
 }
 
-// Remb[2b + co][2(w chrK + b') + ci] from R[w][b'][b] (chrK x chrB per channel)
+// Remb[2b + co][2(w chrK + b') + ci] from R[w][b'][b] (chrK x chrB per channel);
+// consecutive threads take consecutive k = w chrK + b', so the embedded rows
+// are written contiguously
 template <bool TF32>
 __global__ void k_lp_embed_R(const cplx* __restrict__ R, int D2, int chrK, int chrB,
                              typename Lp<TF32>::T* __restrict__ out, long long ld) {
   typedef typename Lp<TF32>::T T;
-  const long long tot = (long long)D2 * chrK * chrB;
+  const long long nk = (long long)D2 * chrK;
+  const long long tot = nk * chrB;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e % chrB);
-    const long long k = e / chrB;                      // w chrK + b'
-    const cplx v = R[e];
+    const long long k = e % nk;                        // w chrK + b'
+    const int b = (int)(e / nk);
+    const cplx v = R[k * chrB + b];
     const T re = Lp<TF32>::from(v.x), im = Lp<TF32>::from(v.y), mim = Lp<TF32>::from(-v.y);
     T* r0 = out + (long long)(2 * b) * ld + 2 * k;
     T* r1 = r0 + ld;
@@ -114,31 +117,61 @@ __global__ void k_lp_xt(const cplx* __restrict__ X, int rows, long long n_cols,
 }
 
 // T2[(a s' t')][2 (w'' chrK + b') + c] = sum_e val_e T1[w_e][a][(s_e t_e) chrK + b']
-// with T1[w][2a + c][n] fp32 (n = (s t) chrK + b'); the plan's rows are
-// (s', t', w''), its columns (w, s, t).  One thread per (a, b').
+// with T1[w][2a + c][n] (bf16, n = (s t) chrK + b'); the plan's rows are
+// (s', t', w''), its columns (w, s, t).  One block per (a, MIX_B values of
+// b'): the block stages the bf16 rows T1[w][2a + c][(s t) chrK + b0 ..] it
+// needs in shared memory with 16-byte loads, and the plan (fp32 values,
+// column indices) beside them; then each thread forms every output of its b'.
+constexpr int MIX_B = 128;
 template <bool TF32>
-__global__ void k_lp_mix(MixPlan pl, const float* __restrict__ T1, int chlB, int chrK, int d,
-                         int D2, long long N1, typename Lp<TF32>::T* __restrict__ T2,
-                         long long ld2) {
+__global__ void __launch_bounds__(MIX_B)
+k_lp_mix(MixPlan pl, const __nv_bfloat16* __restrict__ T1, int chlB, int chrK, int d, int D0,
+         int D2, long long N1, typename Lp<TF32>::T* __restrict__ T2, long long ld2) {
   typedef typename Lp<TF32>::T T;
-  const int bp = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y;
-  if (bp >= chrK) return;
+  extern __shared__ uint4 smem_u4[];
   const int dd = d * d;
-  const long long wstride = 2LL * chlB * N1;
-  const float* base = T1 + (2LL * a) * N1 + bp;
+  const int nrow = 2 * D0 * dd;                          // (w, s t, c) rows of MIX_B bf16
+  __nv_bfloat16* st1 = reinterpret_cast<__nv_bfloat16*>(smem_u4);
+  float2* sval = reinterpret_cast<float2*>(st1 + (size_t)nrow * MIX_B);
+  int* scol = reinterpret_cast<int*>(sval + pl.nnz);
+  int* srp = scol + pl.nnz;
+  const int a = blockIdx.y;
+  const int b0 = blockIdx.x * MIX_B;
+  const int t = threadIdx.x;
+  for (int e = t; e < pl.nnz; e += MIX_B) {
+    sval[e] = pl.val32[e];
+    scol[e] = pl.col[e];
+  }
+  for (int k = t; k <= pl.nrows; k += MIX_B) srp[k] = pl.row_ptr[k];
+  // staging: row r = (j, c) with j = w dd + st; 16 chunks of 8 bf16 per row
+  const bool vec = (chrK % 8 == 0) && (N1 % 8 == 0);
+  constexpr int CH = MIX_B / 8;
+  for (int item = t; item < nrow * CH; item += MIX_B) {
+    const int r = item / CH, ch = item - r * CH;
+    const int j = r >> 1, c = r & 1;
+    const int w = j / dd, stt = j - w * dd;
+    const __nv_bfloat16* src = T1 + ((long long)w * 2 * chlB + 2 * a + c) * N1 + (long long)stt * chrK + b0 + ch * 8;
+    __nv_bfloat16* dst = st1 + (size_t)r * MIX_B + ch * 8;
+    const int lim = chrK - (b0 + ch * 8);
+    if (vec && lim >= 8) {
+      *reinterpret_cast<uint4*>(dst) = __ldcs(reinterpret_cast<const uint4*>(src));
+    } else {
+      for (int q = 0; q < 8; ++q) dst[q] = q < lim ? src[q] : __float2bfloat16_rn(0.f);
+    }
+  }
+  __syncthreads();
+  const int bp = b0 + t;
+  if (bp >= chrK) return;
   for (int k = 0; k < pl.nrows; ++k) {
     float re = 0.f, im = 0.f;
-    const int e1 = __ldg(pl.row_ptr + k + 1);
-    for (int e = __ldg(pl.row_ptr + k); e < e1; ++e) {
-      const int j = __ldg(pl.col + e);                  // (w d + s) d + t
-      const int w = j / dd, st = j - w * dd;
-      const float* p = base + w * wstride + (long long)st * chrK;
-      const float xr = p[0], xi = p[N1];
-      const cplx v = pl.val[e];
-      const float vr = (float)v.x, vi = (float)v.y;
-      re = fmaf(vr, xr, fmaf(-vi, xi, re));
-      im = fmaf(vr, xi, fmaf(vi, xr, im));
+    const int e1 = srp[k + 1];
+    for (int e = srp[k]; e < e1; ++e) {
+      const int j = scol[e];                            // (w d + s) d + t
+      const float xr = __bfloat162float(st1[(size_t)(2 * j) * MIX_B + t]);
+      const float xi = __bfloat162float(st1[(size_t)(2 * j + 1) * MIX_B + t]);
+      const float2 v = sval[e];
+      re = fmaf(v.x, xr, fmaf(-v.y, xi, re));
+      im = fmaf(v.x, xi, fmaf(v.y, xr, im));
     }
     const int wpp = k % D2, spt = k / D2;               // k = (s' d + t') D2 + w''
     T* dst = T2 + ((long long)a * dd + spt) * ld2 + 2LL * ((long long)wpp * chrK + bp);
@@ -147,22 +180,29 @@ __global__ void k_lp_mix(MixPlan pl, const float* __restrict__ T1, int chlB, int
   }
 }
 
-// Y[m][b] = alpha sum_sp (Y32[sp][m][2b], Y32[sp][m][2b+1]) + gamma Z[m][b]
+// Y[m][b] = alpha sum_sp (Y32[sp][m][2b], Y32[sp][m][2b+1]) + gamma Z[m][b],
+// formed in fp32 (the product is good to the operand precision only, and
+// GB300's FP64 pipe is 1/64 of its fp32 rate) and stored as FP64.
 __global__ void k_lp_combine(const float* __restrict__ Y32, int splits, long long slab, long long M,
-                             int ncols, cplx alpha, const cplx* __restrict__ Z, cplx gamma,
+                             int ncols, float2 alpha, const cplx* __restrict__ Z, float2 gamma,
                              cplx* __restrict__ Y) {
   const long long tot = M * ncols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
-    double re = 0.0, im = 0.0;
+    float re = 0.f, im = 0.f;
     for (int sp = 0; sp < splits; ++sp) {
-      const float2 v = reinterpret_cast<const float2*>(Y32 + sp * slab)[e];
+      const float2 v = __ldcs(reinterpret_cast<const float2*>(Y32 + sp * slab) + e);
       re += v.x;
       im += v.y;
     }
-    cplx out = cmul(alpha, cmake(re, im));
-    if (Z) out = cadd(out, cmul(gamma, Z[e]));
-    Y[e] = out;
+    float ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
+    if (Z) {
+      const cplx z = __ldcs(Z + e);
+      const float zr = (float)z.x, zi = (float)z.y;
+      ore = fmaf(gamma.x, zr, fmaf(-gamma.y, zi, ore));
+      oim = fmaf(gamma.x, zi, fmaf(gamma.y, zr, oim));
+    }
+    __stcs(Y + e, cmake((double)ore, (double)oim));
   }
 }
 
@@ -176,24 +216,27 @@ int grid_of(long long tot, int threads) {
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
 // The N tile and K split of one GEMM, from a model of its time on `sms` SMs:
-// waves of units, each costing its MMA work plus a fixed epilogue share.
-void pick_tiles(int M, int N, int K, int batch, bool tf32, int sms, int* bn, int* splits) {
+// the busiest SM runs ceil(units / sms) units, each costing its MMA work
+// (columns x K tiles, the full tile width even where it overhangs N; a
+// 128-wide tile runs at about 0.8 of the rate of a wider one) plus a fixed
+// epilogue share; K splits add the pass that sums the partial slabs.
+void pick_tiles(int M, int N, int K, int batch, bool tf32, int sms, int* bn, int* splits,
+                int max_splits) {
   const int BK = tf32 ? 32 : 64;
   const int nkb = (K + BK - 1) / BK;
   double best = 1e300;
   *bn = 256;
   *splits = 1;
-  for (int b : {256, 128}) {
+  for (int b : {256, 192, 128}) {
     const long long tiles = (long long)batch * ((M + 127) / 128) * ((N + b - 1) / b);
-    for (int s = 1; s <= 8; ++s) {
+    for (int s = 1; s <= max_splits; ++s) {
       if (s > 1 && nkb / s < 4) break;
       const long long per = (nkb + s - 1) / s;
       const long long units = tiles * s;
       const long long waves = (units + sms - 1) / sms;
-      // MMA time ~ b columns x per k-tiles (a 128-wide tile runs at about
-      // 0.8 of the 256-wide rate); epilogue ~ b columns; split-K adds a pass
-      const double t = waves * (b * per * (b == 128 ? 1.25 : 1.0) + 4.0 * b) + (s > 1 ? 0.02 * M * (double)N / sms : 0.0);
-      if (t < best) {
+      const double t = waves * (b * per * (b == 128 ? 1.25 : 1.0) + 6.0 * b) +
+                       (s > 1 ? 0.5 * s * (double)M * N / (128.0 * sms) : 0.0);
+      if (t < best * 0.999) {
         best = t;
         *bn = b;
         *splits = s;
@@ -216,7 +259,7 @@ size_t heff_lp_scratch_bytes(int d, int D0, int D2, int chlB, int chlK, int chrK
   const long long N1 = (long long)d * d * chrK, M3 = (long long)chlB * d * d;
   const long long ldx = round_up(2LL * chlK, al), ld2 = round_up(2LL * D2 * chrK, al);
   const size_t xt = (size_t)N1 * ldx * eb;
-  const size_t t1 = (size_t)D0 * 2 * chlB * N1 * 4;
+  const size_t t1 = (size_t)D0 * 2 * chlB * N1 * 2;
   const size_t t2 = (size_t)M3 * ld2 * eb;
   const size_t y32 = (size_t)8 * M3 * 2 * chrB * 4;
   return xt + t1 + t2 + y32 + 4 * 256;
@@ -260,8 +303,8 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
   char* p = static_cast<char*>(scratch);
   void* XT = p;
   p += round_up(N1 * ldx * eb, 256);
-  float* T1 = reinterpret_cast<float*>(p);
-  p += round_up((long long)D0 * 2 * chlB * N1 * 4, 256);
+  __nv_bfloat16* T1 = reinterpret_cast<__nv_bfloat16*>(p);
+  p += round_up((long long)D0 * 2 * chlB * N1 * 2, 256);
   void* T2 = p;
   p += round_up(M3 * ld2 * eb, 256);
   float* Y32 = reinterpret_cast<float*>(p);
@@ -281,17 +324,23 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
     g.M = 2 * chlB; g.N = (int)N1; g.K = 2 * chlK; g.batch = D0; g.tf32 = tf32;
     g.A = Lemb; g.lda = ldl; g.sAb = 2LL * chlB * ldl;
     g.B = XT; g.ldb = ldx; g.sBb = 0;
-    g.C = T1; g.ldc = N1; g.sCb = 2LL * chlB * N1; g.sCs = 0;
-    pick_tiles(g.M, g.N, g.K, g.batch, tf32, sms, &g.bn, &g.splits);
-    g.splits = 1;                       // the mix reads one T1 slab
+    g.C = T1; g.ldc = N1; g.sCb = 2LL * chlB * N1; g.sCs = 0; g.out_bf16 = true;
+    pick_tiles(g.M, g.N, g.K, g.batch, tf32, sms, &g.bn, &g.splits, 1);
     if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;
   }
   // 2. mix into the K-major complex-interleaved T2
   {
-    dim3 grid((unsigned)((chrK + 127) / 128), (unsigned)chlB);
+    dim3 grid((unsigned)((chrK + MIX_B - 1) / MIX_B), (unsigned)chlB);
+    const size_t smem = (size_t)2 * D0 * d * d * MIX_B * 2 +
+                        (size_t)plan2.nnz * (sizeof(float2) + sizeof(int)) +
+                        (size_t)(plan2.nrows + 1) * sizeof(int) + 16;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t ea = tf32 ? cudaFuncSetAttribute(k_lp_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(k_lp_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ea != cudaSuccess) return ea;
     count_launches(1);
-    if (tf32) k_lp_mix<true><<<grid, 128, 0, st>>>(plan2, T1, chlB, chrK, d, D2, N1, (float*)T2, ld2);
-    else k_lp_mix<false><<<grid, 128, 0, st>>>(plan2, T1, chlB, chrK, d, D2, N1, (__nv_bfloat16*)T2, ld2);
+    if (tf32) k_lp_mix<true><<<grid, MIX_B, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (float*)T2, ld2);
+    else k_lp_mix<false><<<grid, MIX_B, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (__nv_bfloat16*)T2, ld2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // 3. Y32[sp] = T2 Remb^T: M3 x (2 chrB), K = 2 D2 chrK, split over K
@@ -302,15 +351,16 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
     g.A = T2; g.lda = ld2; g.sAb = 0;
     g.B = Remb; g.ldb = ldr; g.sBb = 0;
     g.C = Y32; g.ldc = 2LL * chrB; g.sCb = 0; g.sCs = M3 * 2LL * chrB;
-    pick_tiles(g.M, g.N, g.K, 1, tf32, sms, &g.bn, &g.splits);
+    pick_tiles(g.M, g.N, g.K, 1, tf32, sms, &g.bn, &g.splits, 8);
     splits = lp_gemm_splits_used(g);
     if (splits > 8) return cudaErrorInvalidValue;
     if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;
   }
   // 4. Y = alpha Y32 + gamma Z
   count_launches(1);
-  k_lp_combine<<<grid_of(M3 * chrB, 256), 256, 0, st>>>(Y32, splits, M3 * 2LL * chrB, M3, chrB,
-                                                         alpha, Z, gamma, Y);
+  k_lp_combine<<<grid_of(M3 * chrB, 256), 256, 0, st>>>(
+      Y32, splits, M3 * 2LL * chrB, M3, chrB, make_float2((float)alpha.x, (float)alpha.y), Z,
+      make_float2((float)gamma.x, (float)gamma.y), Y);
   return cudaGetLastError();
 }
 

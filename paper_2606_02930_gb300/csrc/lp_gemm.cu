@@ -101,13 +101,18 @@ struct LpShape {
   int batch, splits;    // batch entries and K splits
   int kb_per_split;     // K tiles per split
   int m_tiles, n_tiles;
-  long long ldc, sCb, sCs;   // fp32 output: row stride, batch stride, split stride
+  long long ldc, sCb, sCs;   // output (elements): row stride, batch stride, split stride
+  int out_bf16;         // output rounded to bf16 instead of fp32
 };
+
+// Per epilogue warp: a 32 x 32 fp32 tile (padded rows) through which the
+// warp turns its lane-per-row TMEM reads into row-contiguous stores.
+constexpr int LP_TRANS_BYTES = 4 * 32 * 33 * 4;
 
 template <int BN, bool TF32>
 __global__ void __launch_bounds__(LP_THREADS, 1)
 k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          float* __restrict__ C, LpShape sh, int a_batched, int b_batched, int* err) {
+          void* __restrict__ C, LpShape sh, int a_batched, int b_batched, int* err) {
   constexpr uint32_t A_BYTES = LP_BM * LP_ROW_BYTES;    // 16 KB
   constexpr uint32_t B_BYTES = BN * LP_ROW_BYTES;       // 16 or 32 KB
   constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
@@ -115,7 +120,8 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   constexpr int ELEM = TF32 ? 4 : 2;
   constexpr int BK = LP_ROW_BYTES / ELEM;               // K elements per tile
   constexpr int MMAS = BK / KSTEP;                      // 4 per tile
-  constexpr uint32_t TMEM_COLS = 2 * BN;                // two accumulators
+  // two accumulators of BN columns; the allocation is a power of two
+  constexpr uint32_t TMEM_COLS = 2 * BN <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + LP_STAGES * STAGE_BYTES);
@@ -124,6 +130,8 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* trans = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(tmem_slot + 4) + 15) & ~uintptr_t(15));
   __shared__ int s_fail;
   __shared__ int s_issued, s_consumed, s_mma_any;
 
@@ -254,27 +262,31 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = mt * LP_BM + q * 32 + lane;
-      float* crow = C + (long long)b * sh.sCb + (long long)sp * sh.sCs + (long long)row * sh.ldc;
+      const int row0 = mt * LP_BM + q * 32;
+      const long long cbase = (long long)b * sh.sCb + (long long)sp * sh.sCs;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + buf * BN;
+      float* tp = trans + (warp - 2) * 32 * 33;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         float v[32];
         tmem_ld32(tbase + c * 32, v);
-        const int n0 = nt * BN + c * 32;
-        if (row < sh.M) {
-          const int lim = sh.N - n0;
-          float* dst = crow + n0;
-          if (lim >= 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+        // lane = row: through shared memory, lane = column
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        for (int i = 0; i < 32; ++i) tp[lane * 33 + i] = v[i];
+        __syncwarp();
+        const int col = nt * BN + c * 32 + lane;
+        if (col < sh.N) {
+          const int rows = min(32, sh.M - row0);
+          if (sh.out_bf16) {
+            __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(C) + cbase + col;
+            for (int r = 0; r < rows; ++r)
+              cb[(long long)(row0 + r) * sh.ldc] = __float2bfloat16_rn(tp[r * 33 + lane]);
           } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < lim) dst[i] = v[i];
+            float* cf = reinterpret_cast<float*>(C) + cbase + col;
+            for (int r = 0; r < rows; ++r) cf[(long long)(row0 + r) * sh.ldc] = tp[r * 33 + lane];
           }
         }
+        __syncwarp();
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -340,7 +352,8 @@ cudaError_t make_map3(CUtensorMap* map, const void* base, bool tf32, long long r
 
 template <int BN>
 constexpr size_t lp_smem_bytes() {
-  return 1024 + LP_STAGES * (LP_BM + BN) * LP_ROW_BYTES + (2 * LP_STAGES + 5) * 8 + 16;
+  return 1024 + LP_STAGES * (LP_BM + BN) * LP_ROW_BYTES + (2 * LP_STAGES + 5) * 8 + 16 + 16 +
+         LP_TRANS_BYTES;
 }
 
 struct SmCount {
@@ -357,7 +370,7 @@ struct SmCount {
 SmCount g_sms;
 
 template <int BN, bool TF32>
-cudaError_t launch_lp(const CUtensorMap& ma, const CUtensorMap& mb, float* C, const LpShape& sh,
+cudaError_t launch_lp(const CUtensorMap& ma, const CUtensorMap& mb, void* C, const LpShape& sh,
                       int a_batched, int b_batched, int* err, cudaStream_t st) {
   static std::atomic<unsigned long long> attr_done{0};
   constexpr size_t smem = lp_smem_bytes<BN>();
@@ -386,7 +399,7 @@ int lp_gemm_sm_count() { return g_sms.get(); }
 
 cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st) {
   if (g.M < 1 || g.N < 1 || g.K < 1 || g.batch < 1) return cudaSuccess;
-  if (g.bn != 128 && g.bn != 256) return cudaErrorInvalidValue;
+  if (g.bn != 128 && g.bn != 192 && g.bn != 256) return cudaErrorInvalidValue;
   cudaError_t e = encoder();
   if (e != cudaSuccess) return e;
   const int eb = g.tf32 ? 4 : 2;
@@ -405,6 +418,7 @@ cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st) {
   sh.ldc = g.ldc;
   sh.sCb = g.sCb;
   sh.sCs = g.sCs;
+  sh.out_bf16 = g.out_bf16 ? 1 : 0;
   if (sh.splits > 1 && g.sCs == 0) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   e = make_map3(&ma, g.A, g.tf32, g.M, g.K, g.lda, g.batch, g.sAb, LP_BM);
@@ -414,9 +428,11 @@ cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st) {
   const int ab = (g.sAb != 0 && g.batch > 1) ? 1 : 0, bb = (g.sBb != 0 && g.batch > 1) ? 1 : 0;
   if (g.tf32) {
     if (g.bn == 256) return launch_lp<256, true>(ma, mb, g.C, sh, ab, bb, err, st);
+    if (g.bn == 192) return launch_lp<192, true>(ma, mb, g.C, sh, ab, bb, err, st);
     return launch_lp<128, true>(ma, mb, g.C, sh, ab, bb, err, st);
   }
   if (g.bn == 256) return launch_lp<256, false>(ma, mb, g.C, sh, ab, bb, err, st);
+  if (g.bn == 192) return launch_lp<192, false>(ma, mb, g.C, sh, ab, bb, err, st);
   return launch_lp<128, false>(ma, mb, g.C, sh, ab, bb, err, st);
 }
 

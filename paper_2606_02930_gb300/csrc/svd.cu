@@ -316,73 +316,109 @@ struct PairOut {
   double al, be;       // squared norms before the rotation (every thread)
 };
 
-// Team-wide sums of the four per-thread quantities, then the rotation of the
+// Row norms are tracked (Hestenes): a rotation that makes rows u, v orthogonal
+// moves t|gamma| of squared norm from one to the other, alpha' = alpha - t|g|,
+// beta' = beta + t|g|, so examining a pair needs only the inner product
+// gamma = a_u^H a_v.  A tracked norm that falls below a tenth of the value last
+// computed from the row itself is recomputed from the rotated row (the
+// subtraction loses digits as it shrinks).  wts[row] holds the tracked squared
+// norm, nref[row] the last computed one.
+//
+// Rotation parameters with one square root and one division: with
+// Delta = beta - alpha and g2 = |gamma|^2,
+//   u = 2 / (|Delta| + sqrt(Delta^2 + 4 g2)),  t = sign(Delta) u |gamma|,
+//   c = 1 / sqrt(1 + u^2 g2),  s e^{i theta} = c u sign(Delta) gamma,
+// (sign(0) = +1), the same rotation as t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)) with zeta = Delta / (2 |gamma|).  Squaring Delta limits
+// this form to rows of norm above about 1e-77.
+constexpr int F_ROT = 1, F_COUNT = 2, F_RECOMP_U = 4, F_RECOMP_V = 8;
+constexpr double kRecomputeFrac = 0.1;
+
+// Team-wide sums of the two inner-product partials, then the rotation of the
 // pair formed by thread 0 and shared with the team.  Two block barriers;
 // every read of the shared scratch precedes the barrier before its next write.
-__device__ __forceinline__ void pair_decide(double sa, double sb, double gr, double gi, double tol,
-                                            double skip, double& c, double& sr, double& si,
-                                            PairOut& out) {
-  __shared__ double red[TPW][4];
-  __shared__ double par[4];
+__device__ __forceinline__ void pair_decide(double gr, double gi, double al, double be,
+                                            double ref_u, double ref_v, double tol, double skip,
+                                            double& c, double& sr, double& si, int& flags,
+                                            double& al2, double& be2) {
+  __shared__ double red[TPW][2];
+  __shared__ double par[6];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  sa = warp_allsum(sa);
-  sb = warp_allsum(sb);
   gr = warp_allsum(gr);
   gi = warp_allsum(gi);
   if (lane == 0) {
-    red[w][0] = sa;
-    red[w][1] = sb;
-    red[w][2] = gr;
-    red[w][3] = gi;
+    red[w][0] = gr;
+    red[w][1] = gi;
   }
   __syncthreads();
-  sa = sb = gr = gi = 0.0;
+  gr = gi = 0.0;
 #pragma unroll
   for (int k = 0; k < TPW; ++k) {
-    sa += red[k][0];
-    sb += red[k][1];
-    gr += red[k][2];
-    gi += red[k][3];
+    gr += red[k][0];
+    gi += red[k][1];
   }
-  const double al = sa, be = sb;
   if (tid == 0) {
-    double cc = 1.0, r0 = 0.0, i0 = 0.0;
-    int flags = 0;                             // bit 0 rotate, bit 1 counted
-    const double gabs = sqrt(fma(gr, gr, gi * gi));
+    double cc = 1.0, r0 = 0.0, i0 = 0.0, a2 = al, b2 = be;
+    int f = 0;
+    const double g2 = fma(gr, gr, gi * gi);
     // A pair of rows both below the skip weight can never be kept: their
     // mutual orthogonality does not matter (their total weight does, and
     // rotations preserve it).
-    if (gabs > tol * sqrt(al * be) && gabs > 0.0 && (al > skip || be > skip)) {
-      const double ig = 1.0 / gabs;
-      const double zeta = 0.5 * (be - al) * ig;
-      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-      cc = rsqrt(fma(t, t, 1.0));
-      const double sn = cc * t * ig;
-      r0 = sn * gr;
-      i0 = sn * gi;                            // s e^{i theta}
-      flags = 1;
-      // Only rotations by an angle above tol between two rows above the skip
-      // weight count towards another sweep.  Rotations against rows below it
-      // are still applied, but those rows are never rotated among themselves,
-      // so they stay a non-orthogonal set, and orthogonalising a kept row
-      // against all of them one pair at a time converges only slowly; its
-      // overlap with them changes the kept product at second order.
-      if (fabs(t) > tol && al > skip && be > skip) flags |= 2;
+    if (g2 > tol * tol * al * be && g2 > 0.0 && (al > skip || be > skip)) {
+      const double D = be - al;
+      const double u = 2.0 / (fabs(D) + sqrt(fma(D, D, 4.0 * g2)));
+      const double ug2 = u * u * g2;
+      cc = rsqrt(1.0 + ug2);
+      const double cu = D >= 0.0 ? cc * u : -cc * u;
+      r0 = cu * gr;
+      i0 = cu * gi;                            // s e^{i theta}
+      const double tg = D >= 0.0 ? u * g2 : -u * g2;   // t |gamma|
+      a2 = al - tg;
+      b2 = be + tg;
+      f = F_ROT;
+      // A rotation counts towards another sweep when it changes the heavier
+      // row by more than tol (relative): |t| sqrt(min / max) > tol, i.e. the
+      // angle itself for rows of similar weight, less against a much lighter
+      // row, whose leftover overlap moves the heavier row by only that much.
+      // Rotations against rows below the skip weight never count: those rows
+      // are never rotated among themselves, so they stay a non-orthogonal
+      // set, and orthogonalising a kept row against all of them one pair at a
+      // time converges only slowly; its overlap with them changes the kept
+      // product at second order.
+      const double lo = fmin(al, be), hi = fmax(al, be);
+      if (ug2 * lo > tol * tol * hi && al > skip && be > skip) f |= F_COUNT;
+      if (a2 < kRecomputeFrac * ref_u) f |= F_RECOMP_U;
+      if (b2 < kRecomputeFrac * ref_v) f |= F_RECOMP_V;
     }
     par[0] = cc;
     par[1] = r0;
     par[2] = i0;
-    par[3] = (double)flags;
+    par[3] = (double)f;
+    par[4] = a2;
+    par[5] = b2;
   }
   __syncthreads();
   c = par[0];
   sr = par[1];
   si = par[2];
-  const int flags = (int)par[3];
-  out.rotated = (flags & 1) != 0;
-  out.counted = (flags & 2) != 0;
-  out.al = al;
-  out.be = be;
+  flags = (int)par[3];
+  al2 = par[4];
+  be2 = par[5];
+}
+
+// team-wide sum (every thread gets it); the scratch is read before the next
+// barrier of pair_decide writes its own
+__device__ __forceinline__ double team_sum(double v) {
+  __shared__ double red1[TPW];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  v = warp_allsum(v);
+  __syncthreads();
+  if (lane == 0) red1[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < TPW; ++k) s += red1[k];
+  return s;
 }
 
 // a_u' = c a_u - s e^{-i theta} a_v ;  a_v' = s e^{i theta} a_u + c a_v
@@ -392,15 +428,32 @@ __device__ __forceinline__ void rotate(cplx& x, cplx& y, double c, double sr, do
   y = cmake((sr * x0.x - si * x0.y) + c * y0.x, (sr * x0.y + si * x0.x) + c * y0.y);
 }
 
+// Finishes a pair after its rotation: recomputed norms where flagged, tracked
+// norms written back by thread 0.
+__device__ __forceinline__ void pair_norms_out(int u, int v, int flags, double al2, double be2,
+                                               double su, double sv, double* wts, double* nref) {
+  if (flags & F_RECOMP_U) al2 = team_sum(su);
+  if (flags & F_RECOMP_V) be2 = team_sum(sv);
+  if (threadIdx.x == 0) {
+    wts[u] = al2;
+    wts[v] = be2;
+    if (flags & F_RECOMP_U) nref[u] = al2;
+    if (flags & F_RECOMP_V) nref[v] = be2;
+  }
+}
+
 // One Jacobi rotation on rows u < v (length len <= TPP EPL) of A by the team,
 // the rows held in registers.
 template <int EPL>
-__device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double skip) {
+__device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double skip, double* wts,
+                             double* nref) {
   const int tid = threadIdx.x;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   cplx x[EPL], y[EPL];
-  // rows come from other SMs' rotations: read them through L2
+  // rows and their norms come from other SMs' rotations: read through L2
+  const double al = __ldcg(wts + u), be = __ldcg(wts + v);
+  const double ru = __ldcg(nref + u), rv = __ldcg(nref + v);
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const int e = tid + TPP * i;
@@ -409,29 +462,31 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
   }
   // independent partial sums keep the dependent FP64 chains short
   constexpr int NP = EPL < 4 ? EPL : 4;
-  double pa[NP], pb[NP], pr[NP], pi[NP];
+  double pr[NP], pi[NP];
 #pragma unroll
-  for (int a = 0; a < NP; ++a) pa[a] = pb[a] = pr[a] = pi[a] = 0.0;
+  for (int a = 0; a < NP; ++a) pr[a] = pi[a] = 0.0;
 #pragma unroll
   for (int i = 0; i < EPL; ++i) {
     const int a = i % NP;
-    pa[a] = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, pa[a]));
-    pb[a] = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, pb[a]));
     pr[a] = fma(x[i].x, y[i].x, fma(x[i].y, y[i].y, pr[a]));     // Re(conj(x) y)
     pi[a] = fma(x[i].x, y[i].y, fma(-x[i].y, y[i].x, pi[a]));    // Im(conj(x) y)
   }
-  double sa = 0.0, sb = 0.0, gr = 0.0, gi = 0.0;
+  double gr = 0.0, gi = 0.0;
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
-    sa += pa[a];
-    sb += pb[a];
     gr += pr[a];
     gi += pi[a];
   }
   PairOut out;
-  double c, sr, si;
-  pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
+  double c, sr, si, al2, be2;
+  int flags;
+  pair_decide(gr, gi, al, be, ru, rv, tol, skip, c, sr, si, flags, al2, be2);
+  out.rotated = (flags & F_ROT) != 0;
+  out.counted = (flags & F_COUNT) != 0;
+  out.al = al;
+  out.be = be;
   if (out.rotated) {
+    double su = 0.0, sv = 0.0;
 #pragma unroll
     for (int i = 0; i < EPL; ++i) {
       const int e = tid + TPP * i;
@@ -441,55 +496,90 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
         av[e] = y[i];
       }
     }
+    if (flags & (F_RECOMP_U | F_RECOMP_V)) {
+#pragma unroll
+      for (int i = 0; i < EPL; ++i) {
+        su = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, su));
+        sv = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, sv));
+      }
+    }
+    pair_norms_out(u, v, flags, al2, be2, su, sv, wts, nref);
   }
   return out;
 }
 
 // The same for rows of any length, streamed from memory twice.
-__device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, double skip) {
+__device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, double skip,
+                               double* wts, double* nref) {
   const int tid = threadIdx.x;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
-  double sa = 0, sb = 0, gr = 0, gi = 0;
+  const double al = __ldcg(wts + u), be = __ldcg(wts + v);
+  const double ru = __ldcg(nref + u), rv = __ldcg(nref + v);
+  double gr = 0, gi = 0;
 #pragma unroll 4
   for (int e = tid; e < len; e += TPP) {
     const cplx x = __ldcg(au + e), y = __ldcg(av + e);
-    sa = fma(x.x, x.x, fma(x.y, x.y, sa));
-    sb = fma(y.x, y.x, fma(y.y, y.y, sb));
     gr = fma(x.x, y.x, fma(x.y, y.y, gr));
     gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
   }
   PairOut out;
-  double c, sr, si;
-  pair_decide(sa, sb, gr, gi, tol, skip, c, sr, si, out);
+  double c, sr, si, al2, be2;
+  int flags;
+  pair_decide(gr, gi, al, be, ru, rv, tol, skip, c, sr, si, flags, al2, be2);
+  out.rotated = (flags & F_ROT) != 0;
+  out.counted = (flags & F_COUNT) != 0;
+  out.al = al;
+  out.be = be;
   if (out.rotated) {
+    double su = 0.0, sv = 0.0;
 #pragma unroll 4
     for (int e = tid; e < len; e += TPP) {
       cplx x = __ldcg(au + e), y = __ldcg(av + e);
       rotate(x, y, c, sr, si);
       au[e] = x;
       av[e] = y;
+      su = fma(x.x, x.x, fma(x.y, x.y, su));
+      sv = fma(y.x, y.x, fma(y.y, y.y, sv));
     }
+    pair_norms_out(u, v, flags, al2, be2, su, sv, wts, nref);
   }
   return out;
 }
 
 __device__ __forceinline__ PairOut jacobi_pair(cplx* A, int len, int u, int v, double tol,
-                                               double skip) {
+                                               double skip, double* wts, double* nref) {
   if (u > v) { const int t = u; u = v; v = t; }
-  if (len <= 2 * TPP) return pair_regs<2>(A, len, u, v, tol, skip);
-  if (len <= 4 * TPP) return pair_regs<4>(A, len, u, v, tol, skip);
-  if (len <= 8 * TPP) return pair_regs<8>(A, len, u, v, tol, skip);
-  if (len <= 16 * TPP) return pair_regs<16>(A, len, u, v, tol, skip);
-  return pair_stream(A, len, u, v, tol, skip);
+  if (len <= 2 * TPP) return pair_regs<2>(A, len, u, v, tol, skip, wts, nref);
+  if (len <= 4 * TPP) return pair_regs<4>(A, len, u, v, tol, skip, wts, nref);
+  if (len <= 8 * TPP) return pair_regs<8>(A, len, u, v, tol, skip, wts, nref);
+  if (len <= 16 * TPP) return pair_regs<16>(A, len, u, v, tol, skip, wts, nref);
+  return pair_stream(A, len, u, v, tol, skip, wts, nref);
+}
+
+// Squared norms of rows [r0, r1) by one team, written to wts and nref.
+__device__ void team_row_norms(const cplx* A, int len, int r0, int r1, int step, double* wts,
+                               double* nref) {
+  for (int r = r0; r < r1; r += step) {
+    const cplx* a = A + (long long)r * len;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < len; e += TPP) s = fma(a[e].x, a[e].x, fma(a[e].y, a[e].y, s));
+    s = team_sum(s);
+    if (threadIdx.x == 0) {
+      wts[r] = s;
+      nref[r] = s;
+    }
+  }
 }
 
 // A single pair (rows == 2), one team.
 __global__ void __launch_bounds__(TPP)
 k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_rel,
-               unsigned int* st) {
+               unsigned int* st, double* wts, double* nref) {
   const double a2 = anorm2 ? *anorm2 : 0.0;
-  const PairOut o = jacobi_pair(A, len, 0, 1, tol, skip_rel * a2);
+  team_row_norms(A, len, 0, 2, 1, wts, nref);
+  __syncthreads();
+  const PairOut o = jacobi_pair(A, len, 0, 1, tol, skip_rel * a2, wts, nref);
   if (threadIdx.x == 0) {
     if (o.counted) atomicAdd(st + S_CNT, 1u);
     atomicAdd(st + S_EXAMINED, 1u);
@@ -503,14 +593,14 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
 // instead, so that a pair waits only for its own two rows, measured slower on
 // GB300: the per-pair fence and flag round trip cost more than the barrier.)
 //
-// Termination.  A sweep whose rotations all left the pairs orthogonal to tol
-// ends the iteration.  So does a sweep in which every rotation that still
-// counted involved a row too light to be kept: with maxw the largest
-// min(alpha, beta) over the counted rotations of the sweep, if at least
-// keep_rank rows weigh more than maxw / kKeepMargin the truncation, which
-// keeps at most keep_rank rows, keeps none of the light ones, and finishing
-// those rotations would change each heavier row by only |t| sqrt(beta/alpha).
-// wts[row] holds the row's squared norm when it was last examined.
+// Termination.  A sweep with no counted rotation (every rotation changed the
+// heavier of its rows by at most tol) ends the iteration.  So does a sweep in
+// which every counted rotation was between two rows too light to be kept:
+// with maxw the largest max(alpha, beta) over the counted rotations of the
+// sweep, if at least keep_rank rows weigh more than maxw / kKeepMargin, the
+// truncation, which keeps at most keep_rank rows, keeps none of the rows that
+// still rotate, and their rotations leave every kept row as it is.
+// wts[row] holds the row's tracked squared norm.
 //
 // The counters and maxw of sweep sw live in slot sw % 2.  A sweep's slot is
 // read by every block after the sweep's last barrier; the slot of the
@@ -525,13 +615,16 @@ constexpr double kKeepMargin = 1e-2;
 __global__ void __launch_bounds__(TPP)
 k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double* anorm2,
                     double skip_rel, int max_sweeps, int keep_rank, unsigned int* st, int* stamps,
-                    double* wts) {
+                    double* wts, double* nref) {
   const unsigned int nb = gridDim.x;
   const int tid = threadIdx.x;
   const double skip = skip_rel * (anorm2 ? *anorm2 : 0.0);
   int* counters = reinterpret_cast<int*>(st + S_CNT);
   unsigned long long* maxws = reinterpret_cast<unsigned long long*>(st + S_MAXW);
   unsigned int examined = 0, rotations_done = 0;
+  // the tracked squared norms start from the rows themselves
+  team_row_norms(A, len, blockIdx.x, rows, (int)nb, wts, nref);
+  if (!grid_barrier(st, nb)) return;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int* cnt = counters + (sw & 1);
     unsigned long long* maxw = maxws + (sw & 1);
@@ -551,12 +644,8 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
           const int last = g - (pp - 1);
           if (__ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) continue;
         }
-        const PairOut o = jacobi_pair(A, len, u, v, tol, skip);
+        const PairOut o = jacobi_pair(A, len, u, v, tol, skip, wts, nref);
         ++examined;
-        if (tid == 0) {
-          wts[u] = o.al;
-          wts[v] = o.be;
-        }
         if (o.rotated) {
           ++rotations_done;
           if (tid == 0) {
@@ -565,7 +654,7 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
             if (o.counted) {
               atomicAdd(cnt, 1);
               // squared norms are non-negative: their bit patterns order like them
-              atomicMax(maxw, (unsigned long long)__double_as_longlong(fmin(o.al, o.be)));
+              atomicMax(maxw, (unsigned long long)__double_as_longlong(fmax(o.al, o.be)));
             }
           }
         }
@@ -818,7 +907,8 @@ cudaError_t svd_lq_r(const cplx* W, const cplx* beta, int p, int q, cplx* R, cud
 
 cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
-                        unsigned int* dev_state, int* stamps, double* wts, cudaStream_t st) {
+                        unsigned int* dev_state, int* stamps, double* wts, double* nref,
+                        cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(dev_state, 0, S_WORDS * sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   if (rows < 2) return cudaSuccess;
@@ -829,7 +919,7 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
     // a single pair: one rotation makes it orthogonal; a second launch confirms
     for (int sw = 0; sw < 2; ++sw) {
       count_launches(1);
-      k_jacobi_round<<<1, TPP, 0, st>>>(A, len, tol, anorm2, skip_rel, dev_state);
+      k_jacobi_round<<<1, TPP, 0, st>>>(A, len, tol, anorm2, skip_rel, dev_state, wts, nref);
     }
     return cudaGetLastError();
   }
@@ -839,7 +929,7 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
   int nblk = pp / 2;
   if (nblk > max_blocks) nblk = max_blocks;
   void* args[] = {&A, &rows, &len, (void*)&pp, &tol, &anorm2, &skip_rel, &max_sweeps, &keep_rank,
-                  &dev_state, &stamps, &wts};
+                  &dev_state, &stamps, &wts, &nref};
   count_launches(1);
   return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(TPP), args, 0,
                                      st);

@@ -39,6 +39,7 @@ def ctx(api):
 @pytest.mark.parametrize("M,N,K,batch,bn,splits", [(128, 256, 64, 1, 256, 1),
                                                     (300, 520, 200, 3, 256, 1),
                                                     (257, 130, 1000, 2, 128, 3),
+                                                    (200, 400, 296, 2, 192, 2),
                                                     (1024, 2048, 1024, 1, 256, 2)])
 def test_lp_gemm_matches_exact_products(api, ctx, tf32, M, N, K, batch, bn, splits):
     import torch
