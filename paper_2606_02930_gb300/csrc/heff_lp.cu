@@ -19,28 +19,87 @@
 // prepares them once (heff_lp_prepare) and reuses them for every matvec.
 #include <cuda_bf16.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 
 namespace ite {
 namespace {
+
+// Format conversions by integer operations on the bit patterns.  GB300 runs
+// FP64 instructions, conversions from and to FP64 among them, at 1/64 of the
+// fp32 rate, and these kernels convert every element they move.
+//
+// double -> binary format with `mb` mantissa bits and an 8-bit exponent (bf16:
+// mb = 7, fp32: mb = 23), rounded to nearest even; magnitudes below the
+// format's normal range become signed zero, above it infinity.  Returns the
+// bit pattern in the low 1 + 8 + mb bits.
+template <int MB>
+__device__ __forceinline__ uint32_t dbl_to_e8(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << (8 + MB);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return sign | (0xFFu << MB) | (m ? (1u << (MB - 1)) : 0u);
+  int ex = e - 1023 + 127;
+  if (ex <= 0) return sign;
+  constexpr int SH = 52 - MB;
+  unsigned long long mant = m >> SH;
+  const unsigned long long rem = m & ((1ull << SH) - 1), half = 1ull << (SH - 1);
+  if (rem > half || (rem == half && (mant & 1))) {
+    if (++mant == (1ull << MB)) {
+      mant = 0;
+      ++ex;
+    }
+  }
+  if (ex >= 255) return sign | (0xFFu << MB);
+  return sign | ((uint32_t)ex << MB) | (uint32_t)mant;
+}
+
+// fp32 -> double, exact (subnormal inputs included)
+__device__ __forceinline__ double f32_to_dbl(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  int e = (int)((u >> 23) & 0xFF);
+  uint32_t m = u & 0x7FFFFFu;
+  if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((unsigned long long)m << 29)));
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int lz = __clz(m) - 8;                       // shift the leading 1 to bit 23
+    m = (m << lz) & 0x7FFFFFu;
+    e = 1 - lz;
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                          ((unsigned long long)m << 29)));
+}
+
+__device__ __forceinline__ float dbl_to_f32(double x) { return __uint_as_float(dbl_to_e8<23>(x)); }
 
 template <bool TF32>
 struct Lp;
 template <>
 struct Lp<false> {
   typedef __nv_bfloat16 T;
-  static __device__ __forceinline__ T from(double x) { return __double2bfloat16(x); }
+  typedef __nv_bfloat162 T2;
+  static __device__ __forceinline__ T from(double x) {
+    return __ushort_as_bfloat16((unsigned short)dbl_to_e8<7>(x));
+  }
   static __device__ __forceinline__ T fromf(float x) { return __float2bfloat16_rn(x); }
+  static __device__ __forceinline__ T2 pair(T a, T b) { return __halves2bfloat162(a, b); }
 };
 template <>
 struct Lp<true> {
   typedef float T;
+  typedef float2 T2;
   static __device__ __forceinline__ float fromf(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
   }
-  static __device__ __forceinline__ float from(double x) { return fromf((float)x); }
+  static __device__ __forceinline__ float from(double x) { return fromf(dbl_to_f32(x)); }
+  static __device__ __forceinline__ T2 pair(float a, float b) { return make_float2(a, b); }
 };
 
 // Lemb[w][2a + co][2a' + ci] from L[w][a][a'] (chlB x chlK per channel)
@@ -58,10 +117,8 @@ __global__ void k_lp_embed_L(const cplx* __restrict__ L, int D0, int chlB, int c
     const T re = Lp<TF32>::from(v.x), im = Lp<TF32>::from(v.y), mim = Lp<TF32>::from(-v.y);
     T* r0 = out + ((long long)w * 2 * chlB + 2 * a) * ld + 2 * k;
     T* r1 = r0 + ld;
-    r0[0] = re;
-    r0[1] = mim;
-    r1[0] = im;
-    r1[1] = re;
+    *reinterpret_cast<typename Lp<TF32>::T2*>(r0) = Lp<TF32>::pair(re, mim);
+    *reinterpret_cast<typename Lp<TF32>::T2*>(r1) = Lp<TF32>::pair(im, re);
   }
 }
 
@@ -82,10 +139,8 @@ __global__ void k_lp_embed_R(const cplx* __restrict__ R, int D2, int chrK, int c
     const T re = Lp<TF32>::from(v.x), im = Lp<TF32>::from(v.y), mim = Lp<TF32>::from(-v.y);
     T* r0 = out + (long long)(2 * b) * ld + 2 * k;
     T* r1 = r0 + ld;
-    r0[0] = re;
-    r0[1] = mim;
-    r1[0] = im;
-    r1[1] = re;
+    *reinterpret_cast<typename Lp<TF32>::T2*>(r0) = Lp<TF32>::pair(re, mim);
+    *reinterpret_cast<typename Lp<TF32>::T2*>(r1) = Lp<TF32>::pair(im, re);
   }
 }
 
@@ -110,8 +165,8 @@ __global__ void k_lp_xt(const cplx* __restrict__ X, int rows, long long n_cols,
     if (a < rows && n < n_cols) {
       const cplx v = tile[threadIdx.x][y];
       T* dst = XT + n * ld + 2 * a;
-      dst[0] = Lp<TF32>::from(v.x);
-      dst[1] = Lp<TF32>::from(v.y);
+      *reinterpret_cast<typename Lp<TF32>::T2*>(dst) = Lp<TF32>::pair(Lp<TF32>::from(v.x),
+                                                                     Lp<TF32>::from(v.y));
     }
   }
 }
@@ -121,38 +176,48 @@ __global__ void k_lp_xt(const cplx* __restrict__ X, int rows, long long n_cols,
 // (s', t', w''), its columns (w, s, t).  One block per (a, MIX_B values of
 // b'): the block stages the bf16 rows T1[w][2a + c][(s t) chrK + b0 ..] it
 // needs in shared memory with 16-byte loads, and the plan (fp32 values,
-// column indices) beside them; then each thread forms every output of its b'.
-constexpr int MIX_B = 128;
+// column indices) beside them; then thread (pair p, group g) forms the
+// outputs k = g, g + groups, ... of the two values b' = b0 + 2p, b0 + 2p + 1
+// (paired loads and stores halve the instructions per output).
+constexpr int MIX_B = 64;           // values of b' per block
+constexpr int MIX_P = MIX_B / 2;    // threads per group
 template <bool TF32>
-__global__ void __launch_bounds__(MIX_B)
+__global__ void __launch_bounds__(256)
 k_lp_mix(MixPlan pl, const __nv_bfloat16* __restrict__ T1, int chlB, int chrK, int d, int D0,
          int D2, long long N1, typename Lp<TF32>::T* __restrict__ T2, long long ld2) {
   typedef typename Lp<TF32>::T T;
   extern __shared__ uint4 smem_u4[];
   const int dd = d * d;
-  const int nrow = 2 * D0 * dd;                          // (w, s t, c) rows of MIX_B bf16
+  const int ncol = D0 * dd;                              // (w, s t)
+  const int nrow = 2 * ncol;                             // (w, s t, c) rows of MIX_B bf16
   __nv_bfloat16* st1 = reinterpret_cast<__nv_bfloat16*>(smem_u4);
   float2* sval = reinterpret_cast<float2*>(st1 + (size_t)nrow * MIX_B);
   int* scol = reinterpret_cast<int*>(sval + pl.nnz);
   int* srp = scol + pl.nnz;
+  long long* roff = reinterpret_cast<long long*>(((uintptr_t)(srp + pl.nrows + 1) + 7) & ~uintptr_t(7));
   const int a = blockIdx.y;
   const int b0 = blockIdx.x * MIX_B;
-  const int t = threadIdx.x;
-  for (int e = t; e < pl.nnz; e += MIX_B) {
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int p = tid % MIX_P, g = tid / MIX_P, groups = nthr / MIX_P;
+  for (int e = tid; e < pl.nnz; e += nthr) {
     sval[e] = pl.val32[e];
     scol[e] = pl.col[e];
   }
-  for (int k = t; k <= pl.nrows; k += MIX_B) srp[k] = pl.row_ptr[k];
-  // staging: row r = (j, c) with j = w dd + st; 16 chunks of 8 bf16 per row
+  for (int k = tid; k <= pl.nrows; k += nthr) srp[k] = pl.row_ptr[k];
+  for (int j = tid; j < ncol; j += nthr) {
+    const int w = j / dd, stt = j - w * dd;
+    roff[j] = ((long long)w * 2 * chlB + 2 * a) * N1 + (long long)stt * chrK + b0;
+  }
+  __syncthreads();
+  // staging: row r = 2 j + c; MIX_B / 8 chunks of 8 bf16 per row
   const bool vec = (chrK % 8 == 0) && (N1 % 8 == 0);
   constexpr int CH = MIX_B / 8;
-  for (int item = t; item < nrow * CH; item += MIX_B) {
+  const int lim0 = chrK - b0;
+  for (int item = tid; item < nrow * CH; item += nthr) {
     const int r = item / CH, ch = item - r * CH;
-    const int j = r >> 1, c = r & 1;
-    const int w = j / dd, stt = j - w * dd;
-    const __nv_bfloat16* src = T1 + ((long long)w * 2 * chlB + 2 * a + c) * N1 + (long long)stt * chrK + b0 + ch * 8;
+    const __nv_bfloat16* src = T1 + roff[r >> 1] + (r & 1) * N1 + ch * 8;
     __nv_bfloat16* dst = st1 + (size_t)r * MIX_B + ch * 8;
-    const int lim = chrK - (b0 + ch * 8);
+    const int lim = lim0 - ch * 8;
     if (vec && lim >= 8) {
       *reinterpret_cast<uint4*>(dst) = __ldcs(reinterpret_cast<const uint4*>(src));
     } else {
@@ -160,23 +225,29 @@ k_lp_mix(MixPlan pl, const __nv_bfloat16* __restrict__ T1, int chlB, int chrK, i
     }
   }
   __syncthreads();
-  const int bp = b0 + t;
+  const int bp = b0 + 2 * p;
   if (bp >= chrK) return;
-  for (int k = 0; k < pl.nrows; ++k) {
-    float re = 0.f, im = 0.f;
+  const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(st1);
+  for (int k = g; k < pl.nrows; k += groups) {
+    float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);
     const int e1 = srp[k + 1];
     for (int e = srp[k]; e < e1; ++e) {
       const int j = scol[e];                            // (w d + s) d + t
-      const float xr = __bfloat162float(st1[(size_t)(2 * j) * MIX_B + t]);
-      const float xi = __bfloat162float(st1[(size_t)(2 * j + 1) * MIX_B + t]);
+      const float2 xr = __bfloat1622float2(s2[(size_t)(2 * j) * MIX_P + p]);
+      const float2 xi = __bfloat1622float2(s2[(size_t)(2 * j + 1) * MIX_P + p]);
       const float2 v = sval[e];
-      re = fmaf(v.x, xr, fmaf(-v.y, xi, re));
-      im = fmaf(v.x, xi, fmaf(v.y, xr, im));
+      re.x = fmaf(v.x, xr.x, fmaf(-v.y, xi.x, re.x));
+      re.y = fmaf(v.x, xr.y, fmaf(-v.y, xi.y, re.y));
+      im.x = fmaf(v.x, xi.x, fmaf(v.y, xr.x, im.x));
+      im.y = fmaf(v.x, xi.y, fmaf(v.y, xr.y, im.y));
     }
     const int wpp = k % D2, spt = k / D2;               // k = (s' d + t') D2 + w''
     T* dst = T2 + ((long long)a * dd + spt) * ld2 + 2LL * ((long long)wpp * chrK + bp);
-    dst[0] = Lp<TF32>::fromf(re);
-    dst[1] = Lp<TF32>::fromf(im);
+    *reinterpret_cast<typename Lp<TF32>::T2*>(dst) =
+        Lp<TF32>::pair(Lp<TF32>::fromf(re.x), Lp<TF32>::fromf(im.x));
+    if (bp + 1 < chrK)
+      *reinterpret_cast<typename Lp<TF32>::T2*>(dst + 2) =
+          Lp<TF32>::pair(Lp<TF32>::fromf(re.y), Lp<TF32>::fromf(im.y));
   }
 }
 
@@ -198,11 +269,11 @@ __global__ void k_lp_combine(const float* __restrict__ Y32, int splits, long lon
     float ore = alpha.x * re - alpha.y * im, oim = alpha.x * im + alpha.y * re;
     if (Z) {
       const cplx z = __ldcs(Z + e);
-      const float zr = (float)z.x, zi = (float)z.y;
+      const float zr = dbl_to_f32(z.x), zi = dbl_to_f32(z.y);
       ore = fmaf(gamma.x, zr, fmaf(-gamma.y, zi, ore));
       oim = fmaf(gamma.x, zi, fmaf(gamma.y, zr, oim));
     }
-    __stcs(Y + e, cmake((double)ore, (double)oim));
+    __stcs(Y + e, cmake(f32_to_dbl(ore), f32_to_dbl(oim)));
   }
 }
 
@@ -243,6 +314,86 @@ void pick_tiles(int M, int N, int K, int batch, bool tf32, int sms, int* bn, int
       }
     }
   }
+}
+
+// Tile autotuner: the first time a GEMM shape is seen on a device, every
+// candidate (N tile 128/192/256, K split up to max_splits) is timed on the
+// caller's stream with CUDA events, twice, and the fastest kept for that
+// shape; each candidate writes C, which the real launch then overwrites.
+// While the stream is being captured into a graph, or if timing fails, the
+// model of pick_tiles decides instead.
+struct TileKey {
+  int dev, M, N, K, batch, tf32, obf16, max_splits;
+  bool operator<(const TileKey& o) const {
+    return std::tie(dev, M, N, K, batch, tf32, obf16, max_splits) <
+           std::tie(o.dev, o.M, o.N, o.K, o.batch, o.tf32, o.obf16, o.max_splits);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TileKey, std::pair<int, int>> g_tuned;
+
+cudaError_t tune_tiles(LpGemmArgs& g, int max_splits, int sms, int* err, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const TileKey key{dev, g.M, g.N, g.K, g.batch, g.tf32 ? 1 : 0, g.out_bf16 ? 1 : 0, max_splits};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      g.bn = it->second.first;
+      g.splits = it->second.second;
+      return cudaSuccess;
+    }
+  }
+  pick_tiles(g.M, g.N, g.K, g.batch, g.tf32, sms, &g.bn, &g.splits, max_splits);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return cudaSuccess;
+  const int BK = g.tf32 ? 32 : 64;
+  const int nkb = (g.K + BK - 1) / BK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  float best = 1e30f;
+  int bbn = g.bn, bsp = g.splits;
+  for (int bn : {256, 192, 128}) {
+    for (int sp : {1, 2, 3, 4, 6, 8}) {
+      if (sp > max_splits || (sp > 1 && nkb / sp < 4)) continue;
+      LpGemmArgs c = g;
+      c.bn = bn;
+      c.splits = sp;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (cudaEventRecord(e0, st) != cudaSuccess || lp_gemm(c, err, st) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          ms = 1e30f;
+          cudaGetLastError();
+          break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep == 1) ms = t;
+      }
+      if (ms < best) {
+        best = ms;
+        bbn = bn;
+        bsp = sp;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 1e29f) {
+    g.bn = bbn;
+    g.splits = bsp;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = {bbn, bsp};
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -325,7 +476,7 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
     g.A = Lemb; g.lda = ldl; g.sAb = 2LL * chlB * ldl;
     g.B = XT; g.ldb = ldx; g.sBb = 0;
     g.C = T1; g.ldc = N1; g.sCb = 2LL * chlB * N1; g.sCs = 0; g.out_bf16 = true;
-    pick_tiles(g.M, g.N, g.K, g.batch, tf32, sms, &g.bn, &g.splits, 1);
+    if ((e = tune_tiles(g, 1, sms, err, st)) != cudaSuccess) return e;
     if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;
   }
   // 2. mix into the K-major complex-interleaved T2
@@ -333,14 +484,21 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
     dim3 grid((unsigned)((chrK + MIX_B - 1) / MIX_B), (unsigned)chlB);
     const size_t smem = (size_t)2 * D0 * d * d * MIX_B * 2 +
                         (size_t)plan2.nnz * (sizeof(float2) + sizeof(int)) +
-                        (size_t)(plan2.nrows + 1) * sizeof(int) + 16;
+                        (size_t)(plan2.nrows + 1) * sizeof(int) + 16 +
+                        (size_t)D0 * d * d * sizeof(long long);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaError_t ea = tf32 ? cudaFuncSetAttribute(k_lp_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                          : cudaFuncSetAttribute(k_lp_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ea != cudaSuccess) return ea;
+    if (smem > 48 * 1024) {
+      cudaError_t ea = tf32 ? cudaFuncSetAttribute(k_lp_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_lp_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (ea != cudaSuccess) return ea;
+    }
+    // thread groups per pair of b' values (two or more output rows per thread),
+    // at most 8 (256 threads)
+    int groups = plan2.nrows / 2;
+    groups = groups < 1 ? 1 : (groups > 8 ? 8 : groups);
     count_launches(1);
-    if (tf32) k_lp_mix<true><<<grid, MIX_B, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (float*)T2, ld2);
-    else k_lp_mix<false><<<grid, MIX_B, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (__nv_bfloat16*)T2, ld2);
+    if (tf32) k_lp_mix<true><<<grid, MIX_P * groups, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (float*)T2, ld2);
+    else k_lp_mix<false><<<grid, MIX_P * groups, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (__nv_bfloat16*)T2, ld2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // 3. Y32[sp] = T2 Remb^T: M3 x (2 chrB), K = 2 D2 chrK, split over K
@@ -351,7 +509,7 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
     g.A = T2; g.lda = ld2; g.sAb = 0;
     g.B = Remb; g.ldb = ldr; g.sBb = 0;
     g.C = Y32; g.ldc = 2LL * chrB; g.sCb = 0; g.sCs = M3 * 2LL * chrB;
-    pick_tiles(g.M, g.N, g.K, 1, tf32, sms, &g.bn, &g.splits, 8);
+    if ((e = tune_tiles(g, 8, sms, err, st)) != cudaSuccess) return e;
     splits = lp_gemm_splits_used(g);
     if (splits > 8) return cudaErrorInvalidValue;
     if ((e = lp_gemm(g, err, st)) != cudaSuccess) return e;

@@ -14,9 +14,11 @@
 //   warp 1   one thread issues tcgen05.mma (M = 128, N = BN) into one of two
 //            TMEM accumulators of BN columns and frees ring stages with
 //            tcgen05.commit;
-//   warps 2-5 read a finished accumulator with tcgen05.ld (each warp its TMEM
-//            lane quarter) and store fp32 rows, while the MMAs of the next
-//            tile fill the other accumulator.
+//   warps 2-9 read a finished accumulator with tcgen05.ld (two warps per TMEM
+//            lane quarter, alternate 32-column chunks), turn the lane-per-row
+//            values into row-contiguous stores through shared memory and
+//            store fp32 (or bf16) rows, while the MMAs of the next tile fill
+//            the other accumulator.
 // Work units (batch x split x M tile x N tile) are dealt round-robin to the
 // CTAs.  Every mbarrier wait is bounded: a wait that runs out sets the error
 // word, the CTA stops issuing work, waits (again bounded) for the copies and
@@ -39,7 +41,8 @@ using namespace tc;
 
 constexpr int LP_BM = 128;
 constexpr int LP_STAGES = 4;
-constexpr int LP_THREADS = 192;
+constexpr int LP_EPI_WARPS = 8;             // two warps per TMEM lane quarter
+constexpr int LP_THREADS = 64 + 32 * LP_EPI_WARPS;
 constexpr int LP_ROW_BYTES = 128;          // one K tile: 128 bytes per row
 
 __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
@@ -107,7 +110,7 @@ struct LpShape {
 
 // Per epilogue warp: a 32 x 32 fp32 tile (padded rows) through which the
 // warp turns its lane-per-row TMEM reads into row-contiguous stores.
-constexpr int LP_TRANS_BYTES = 4 * 32 * 33 * 4;
+constexpr int LP_TRANS_BYTES = LP_EPI_WARPS * 32 * 33 * 4;
 
 template <int BN, bool TF32>
 __global__ void __launch_bounds__(LP_THREADS, 1)
@@ -149,7 +152,7 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], LP_EPI_WARPS);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,8 +252,9 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mma_commit(done);
     }
   } else {
-    // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4)
-    const int q = warp & 3;
+    // ---- epilogue warps 2..9: TMEM lane quarter warp % 4; the two warps of a
+    // quarter take alternate 32-column chunks
+    const int q = warp & 3, half = (warp - 2) >> 2;
     int lt = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++lt) {
       int b, sp, mt, nt;
@@ -267,7 +271,7 @@ k_lp_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + buf * BN;
       float* tp = trans + (warp - 2) * 32 * 33;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half; c < BN / 32; c += 2) {
         float v[32];
         tmem_ld32(tbase + c * 32, v);
         // lane = row: through shared memory, lane = column

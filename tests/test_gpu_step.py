@@ -398,3 +398,29 @@ def test_explicit_steps_match_oracle_and_blow_up(api, ctx, scheme):
         elif z_max <= 2.0:
             assert ginfo["norm_before"] <= 1.0 + 1e-12
     assert grew
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc", "mixed_bf16"])
+def test_anderson_reduced_bath_saturated_step(api, ctx, precision):
+    # the impurity workload on a reduced bath: impurity + 10 bath sites
+    # (N = 11, d = 4, MPO bond dimension 6), flat band Gamma = 0.05,
+    # U = 0.3, eps_d = -U/2, cutoff 1e-14, chi = 64 saturated (random
+    # isometries), backward Euler dtau = 0.05 with the energy shift; the fixed
+    # modes against the oracle's fixed-effort step (1e-10), the mixed mode
+    # against its converged step (1e-8)
+    nb, chi, cutoff, dt = 10, 64, 1e-14, 0.05
+    eps, V = inputs.flat_band_bath(nb)
+    Ws = ompo.anderson_mpo(-0.15, 0.3, eps, V)
+    H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
+    A = inputs.random_isometric_mps(nb + 1, 4, chi, 3002)
+    mixed = precision.startswith("mixed")
+    okw = dict(local_tol=1e-12, max_cycles=100) if mixed else {}
+    opts = (api.solver_opts(precision=precision, refine_tol=1e-11, refine_max=20) if mixed
+            else api.solver_opts(precision=precision))
+    pairs = run_pair(api, ctx, Ws, H, A, np.array([0.0, dt]), "be", chi, cutoff,
+                     shift_mode="energy", opts=opts, okw=okw)
+    bar = 1e-8 if mixed else TOL
+    for ost, oinfo, gst, ginfo in pairs:
+        assert abs(ginfo["energy"] - oinfo.energy) <= bar * abs(oinfo.energy)
+        assert infid(ost, gst) <= bar
+        assert ginfo["max_chi"] == oinfo.max_chi
