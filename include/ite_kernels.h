@@ -130,10 +130,13 @@ ite_status ite_k_barrier_selftest(ite_ctx ctx, int blocks, int absent);
  * is cut into `splits` nearly equal ranges of 128-byte tiles (splits > 1 needs
  * sCs > 0).  Leading dimensions and batch strides are in elements and must be
  * multiples of 16 bytes; pointers 16-byte aligned; a batch stride of 0 shares
- * that operand across the batch.  ITE_ETIMEOUT if a bounded wait ran out. */
+ * that operand across the batch.  flags bit 0 computes 256-row tiles on pairs
+ * of CTAs (a cluster of two sharing each MMA, cta_group::2).  ITE_ETIMEOUT if
+ * a bounded wait ran out. */
 ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void* A, long long lda,
                          long long sAb, const void* B, long long ldb, long long sBb, float* C,
-                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits);
+                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits,
+                         int flags);
 
 ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long long lda,
                            const void* B, long long ldb, float* C, long long ldc, int flags);

@@ -129,7 +129,7 @@ SIGNATURES = {
     "ite_k_heff_lp_prepare": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i]),
     "ite_k_gemm_lp": (_i, [_vp, _i, _i, _i, _i, _vp, C.c_longlong, C.c_longlong, _vp,
                            C.c_longlong, C.c_longlong, _vp, C.c_longlong, C.c_longlong,
-                           C.c_longlong, _i, _i, _i]),
+                           C.c_longlong, _i, _i, _i, _i]),
     "ite_k_heff_lp_apply": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _pd, _vp, _pd]),
     "ite_k_local_solve": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _d, _d, _i, _d, _pi, _pd]),
     "ite_k_gemm_bf16": (_i, [_vp, _i, _i, _i, _vp, C.c_longlong, _vp, C.c_longlong, _vp,

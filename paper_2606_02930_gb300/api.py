@@ -466,7 +466,7 @@ def k_gemm_bf16(ctx, A, B, Cout, k_tile=64):
                               Cout.stride(0), 1 if k_tile == 32 else 0), ctx.h)
 
 
-def k_gemm_lp(ctx, A, B, Cout, bn=256, splits=1):
+def k_gemm_lp(ctx, A, B, Cout, bn=256, splits=1, pair=False):
     """Cout[b][s] (fp32) = A[b] B[b]^T over K split s on the tensor cores.  A
     (batch, M, K) or (M, K), B (batch, N, K) or (N, K): bf16 (kind::f16) or
     float32 (read as tf32) CUDA tensors, K contiguous; a 2-D operand is shared
@@ -482,7 +482,7 @@ def k_gemm_lp(ctx, A, B, Cout, bn=256, splits=1):
                             A3.stride(0) if A.dim() == 3 else 0, C.c_void_p(B3.data_ptr()),
                             B3.stride(1), B3.stride(0) if B.dim() == 3 else 0,
                             C.c_void_p(Cout.data_ptr()), Cout.stride(2), Cout.stride(1),
-                            Cout.stride(0), 1 if tf32 else 0, bn, splits), ctx.h)
+                            Cout.stride(0), 1 if tf32 else 0, bn, splits, 1 if pair else 0), ctx.h)
 
 
 def k_zgemm(ctx, A, B, Cout, mode=1, conjA=False, conjB=False, alpha=1.0, beta=0.0, transA=False,

@@ -76,6 +76,15 @@ struct LpGemmArgs {
   const void* B; long long ldb, sBb;
   void* C; long long ldc, sCb, sCs;   // fp32, or bf16 with out_bf16 (elements)
   bool out_bf16;
+  // complex output (splits 1, batch 1, N even): columns 2b, 2b+1 of the
+  // product are (Re, Im) of complex column b, and the epilogue stores
+  // C[m][b] (complex double, ldc in complex units) = alpha prod + gamma Z[m][b]
+  // (fp32 arithmetic, Z may be NULL; Z has the leading dimension of C)
+  bool out_complex;
+  float2 alpha, gamma;
+  const cplx* Z;
+  // 256 x bn tiles on CTA pairs (cluster of two, cta_group::2 MMAs)
+  bool pair;
 };
 cudaError_t lp_gemm(const LpGemmArgs& g, int* err, cudaStream_t st);
 int lp_gemm_splits_used(const LpGemmArgs& g);

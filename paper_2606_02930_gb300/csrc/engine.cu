@@ -2380,7 +2380,8 @@ ite_status ite_k_local_solve(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
 
 ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void* A, long long lda,
                          long long sAb, const void* B, long long ldb, long long sBb, float* Cm,
-                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits) {
+                         long long ldc, long long sCb, long long sCs, int tf32, int bn, int splits,
+                         int flags) {
   const int eb = tf32 ? 4 : 2;
   if (!ctx || !A || !B || !Cm || M < 1 || N < 1 || K < 1 || batch < 1 || lda < K || ldb < K ||
       ldc < N || (lda * eb) % 16 || (ldb * eb) % 16 || (sAb * eb) % 16 || (sBb * eb) % 16 ||
@@ -2394,6 +2395,7 @@ ite_status ite_k_gemm_lp(ite_ctx ctx, int M, int N, int K, int batch, const void
   g.A = A; g.lda = lda; g.sAb = sAb;
   g.B = B; g.ldb = ldb; g.sBb = sBb;
   g.C = Cm; g.ldc = ldc; g.sCb = sCb; g.sCs = sCs;
+  g.pair = (flags & 1) != 0;
   CK(lp_gemm(g, err, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hr->counter, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CS(sync(ctx));

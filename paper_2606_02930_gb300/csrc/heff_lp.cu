@@ -14,7 +14,7 @@
 //      complex-interleaved A operand of step 3;
 //   3. Y32 = T2 R~ with the column-embedded R~ (rows 2b, 2b+1 = [Re, -Im],
 //      [Im, Re] along (w'' b')), whose fp32 output is complex-interleaved;
-//   then Y = alpha Y32 + gamma Z in FP64.
+//   then Y = alpha Y32 + gamma Z, stored as complex FP64.
 // The embedded L and R depend only on the environments, so a local solve
 // prepares them once (heff_lp_prepare) and reuses them for every matvec.
 #include <cuda_bf16.h>
@@ -24,58 +24,10 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "convert.cuh"
 
 namespace ite {
 namespace {
-
-// Format conversions by integer operations on the bit patterns.  GB300 runs
-// FP64 instructions, conversions from and to FP64 among them, at 1/64 of the
-// fp32 rate, and these kernels convert every element they move.
-//
-// double -> binary format with `mb` mantissa bits and an 8-bit exponent (bf16:
-// mb = 7, fp32: mb = 23), rounded to nearest even; magnitudes below the
-// format's normal range become signed zero, above it infinity.  Returns the
-// bit pattern in the low 1 + 8 + mb bits.
-template <int MB>
-__device__ __forceinline__ uint32_t dbl_to_e8(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t sign = (uint32_t)(b >> 63) << (8 + MB);
-  const int e = (int)((b >> 52) & 0x7FF);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7FF) return sign | (0xFFu << MB) | (m ? (1u << (MB - 1)) : 0u);
-  int ex = e - 1023 + 127;
-  if (ex <= 0) return sign;
-  constexpr int SH = 52 - MB;
-  unsigned long long mant = m >> SH;
-  const unsigned long long rem = m & ((1ull << SH) - 1), half = 1ull << (SH - 1);
-  if (rem > half || (rem == half && (mant & 1))) {
-    if (++mant == (1ull << MB)) {
-      mant = 0;
-      ++ex;
-    }
-  }
-  if (ex >= 255) return sign | (0xFFu << MB);
-  return sign | ((uint32_t)ex << MB) | (uint32_t)mant;
-}
-
-// fp32 -> double, exact (subnormal inputs included)
-__device__ __forceinline__ double f32_to_dbl(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  int e = (int)((u >> 23) & 0xFF);
-  uint32_t m = u & 0x7FFFFFu;
-  if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((unsigned long long)m << 29)));
-  if (e == 0) {
-    if (m == 0) return __longlong_as_double((long long)sign);
-    const int lz = __clz(m) - 8;                       // shift the leading 1 to bit 23
-    m = (m << lz) & 0x7FFFFFu;
-    e = 1 - lz;
-  }
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) |
-                                          ((unsigned long long)m << 29)));
-}
-
-__device__ __forceinline__ float dbl_to_f32(double x) { return __uint_as_float(dbl_to_e8<23>(x)); }
 
 template <bool TF32>
 struct Lp;
@@ -253,7 +205,9 @@ k_lp_mix(MixPlan pl, const __nv_bfloat16* __restrict__ T1, int chlB, int chrK, i
 
 // Y[m][b] = alpha sum_sp (Y32[sp][m][2b], Y32[sp][m][2b+1]) + gamma Z[m][b],
 // formed in fp32 (the product is good to the operand precision only, and
-// GB300's FP64 pipe is 1/64 of its fp32 rate) and stored as FP64.
+// GB300's FP64 pipe is 1/64 of its fp32 rate) and stored as FP64.  A
+// separate pass: folded into the GEMM's epilogue, the dependent loads of Z
+// row by row made that epilogue the bottleneck.
 __global__ void k_lp_combine(const float* __restrict__ Y32, int splits, long long slab, long long M,
                              int ncols, float2 alpha, const cplx* __restrict__ Z, float2 gamma,
                              cplx* __restrict__ Y) {
@@ -317,32 +271,39 @@ void pick_tiles(int M, int N, int K, int batch, bool tf32, int sms, int* bn, int
 }
 
 // Tile autotuner: the first time a GEMM shape is seen on a device, every
-// candidate (N tile 128/192/256, K split up to max_splits) is timed on the
-// caller's stream with CUDA events, twice, and the fastest kept for that
-// shape; each candidate writes C, which the real launch then overwrites.
+// candidate (N tile 128/192/256, one CTA or a CTA pair per tile, K split up
+// to max_splits) is timed on the caller's stream with CUDA events, twice, and
+// the fastest kept for that shape; each candidate writes C, which the real
+// launch then overwrites.
 // While the stream is being captured into a graph, or if timing fails, the
 // model of pick_tiles decides instead.
 struct TileKey {
-  int dev, M, N, K, batch, tf32, obf16, max_splits;
+  int dev, M, N, K, batch, tf32, mode, max_splits;
   bool operator<(const TileKey& o) const {
-    return std::tie(dev, M, N, K, batch, tf32, obf16, max_splits) <
-           std::tie(o.dev, o.M, o.N, o.K, o.batch, o.tf32, o.obf16, o.max_splits);
+    return std::tie(dev, M, N, K, batch, tf32, mode, max_splits) <
+           std::tie(o.dev, o.M, o.N, o.K, o.batch, o.tf32, o.mode, o.max_splits);
   }
 };
 std::mutex g_tune_mu;
-std::map<TileKey, std::pair<int, int>> g_tuned;
+struct TileChoice {
+  int bn, splits;
+  bool pair;
+};
+std::map<TileKey, TileChoice> g_tuned;
 
 cudaError_t tune_tiles(LpGemmArgs& g, int max_splits, int sms, int* err, cudaStream_t st) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const TileKey key{dev, g.M, g.N, g.K, g.batch, g.tf32 ? 1 : 0, g.out_bf16 ? 1 : 0, max_splits};
+  const TileKey key{dev, g.M, g.N, g.K, g.batch, g.tf32 ? 1 : 0,
+                     g.out_complex ? 2 : (g.out_bf16 ? 1 : 0), max_splits};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      g.bn = it->second.first;
-      g.splits = it->second.second;
+      g.bn = it->second.bn;
+      g.splits = it->second.splits;
+      g.pair = it->second.pair;
       return cudaSuccess;
     }
   }
@@ -360,12 +321,15 @@ cudaError_t tune_tiles(LpGemmArgs& g, int max_splits, int sms, int* err, cudaStr
   }
   float best = 1e30f;
   int bbn = g.bn, bsp = g.splits;
+  bool bpair = false;
+  for (int pr = 0; pr < (g.M >= 256 ? 2 : 1); ++pr)
   for (int bn : {256, 192, 128}) {
     for (int sp : {1, 2, 3, 4, 6, 8}) {
       if (sp > max_splits || (sp > 1 && nkb / sp < 4)) continue;
       LpGemmArgs c = g;
       c.bn = bn;
       c.splits = sp;
+      c.pair = pr == 1;
       float ms = 1e30f;
       for (int rep = 0; rep < 2; ++rep) {
         if (cudaEventRecord(e0, st) != cudaSuccess || lp_gemm(c, err, st) != cudaSuccess ||
@@ -382,6 +346,7 @@ cudaError_t tune_tiles(LpGemmArgs& g, int max_splits, int sms, int* err, cudaStr
         best = ms;
         bbn = bn;
         bsp = sp;
+        bpair = c.pair;
       }
     }
   }
@@ -390,8 +355,9 @@ cudaError_t tune_tiles(LpGemmArgs& g, int max_splits, int sms, int* err, cudaStr
   if (best < 1e29f) {
     g.bn = bbn;
     g.splits = bsp;
+    g.pair = bpair;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[key] = {bbn, bsp};
+    g_tuned[key] = {bbn, bsp, bpair};
   }
   return cudaSuccess;
 }

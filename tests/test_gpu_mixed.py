@@ -35,13 +35,15 @@ def ctx(api):
     return api.ctx_create(0)
 
 
+@pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("tf32", [False, True])
 @pytest.mark.parametrize("M,N,K,batch,bn,splits", [(128, 256, 64, 1, 256, 1),
                                                     (300, 520, 200, 3, 256, 1),
                                                     (257, 130, 1000, 2, 128, 3),
                                                     (200, 400, 296, 2, 192, 2),
                                                     (1024, 2048, 1024, 1, 256, 2)])
-def test_lp_gemm_matches_exact_products(api, ctx, tf32, M, N, K, batch, bn, splits):
+def test_lp_gemm_matches_exact_products(api, ctx, tf32, M, N, K, batch, bn, splits, pair):
+    # pair: 256-row tiles computed by a pair of CTAs sharing each MMA
     import torch
     g = torch.Generator().manual_seed(M * 7 + N + K)
     dt = torch.float32 if tf32 else torch.bfloat16
@@ -53,7 +55,7 @@ def test_lp_gemm_matches_exact_products(api, ctx, tf32, M, N, K, batch, bn, spli
         A = (A.view(torch.int32) & ~0x1FFF).view(torch.float32)
         B = (B.view(torch.int32) & ~0x1FFF).view(torch.float32)
     Cd = torch.full((splits, batch, M, N), float("nan"), dtype=torch.float32, device="cuda")
-    api.k_gemm_lp(ctx, A.cuda(), B.cuda(), Cd, bn=bn, splits=splits)
+    api.k_gemm_lp(ctx, A.cuda(), B.cuda(), Cd, bn=bn, splits=splits, pair=pair)
     got = Cd.double().sum(0).cpu()
     want = torch.einsum("bmk,nk->bmn", A.double(), B.double())
     bound = K * 2.0 ** -24 * torch.einsum("bmk,nk->bmn", A.double().abs(), B.double().abs())
