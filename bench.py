@@ -776,6 +776,49 @@ def run_chi_study(args):
     print(json.dumps(out), flush=True)
 
 
+def oracle_anderson_sample(chi, n_bonds):
+    """The oracle on the impurity workload at a saturated bond dimension chi
+    (random isometries, seed 3000): seconds per bulk two-site update of the
+    first step (gauge move and environments untimed; backward Euler, dtau =
+    1e-2, shift = the state's energy), over n_bonds updates from the
+    impurity end; and the number of bulk-equivalent updates of a step."""
+    from oracle import linsolve as ls, mpo as ompo, mps as omps
+    from paper_2606_02930_gb300 import inputs
+    n_bath, d = 99, 4
+    eps, V = inputs.flat_band_bath(n_bath)
+    Ws = ompo.anderson_mpo(-0.15, 0.3, eps, V)
+    N = n_bath + 1
+    A = inputs.random_isometric_mps(N, d, chi, 3000)
+    s = omps.expect_mpo(A, Ws)
+    c = 1e-2
+    x = ls.right_canonicalize_svd(A)
+    Rop, Rov = ls._build_right_envs(Ws, x, [("op", x), ("ov", A)])
+    Lop, Lov = np.ones((1, 1, 1), complex), np.ones((1, 1), complex)
+    alpha = 1.0 - c * s
+    cap = [1] + inputs.bond_profile(N, d, chi) + [1]
+    first_bulk = next(i for i in range(N - 1) if cap[i] == chi and cap[i + 2] == chi)
+    t_bulk, n_done, i = 0.0, 0, 0
+    while n_done < n_bonds:
+        t1 = time.perf_counter()
+        B = ls.project_two_site(Lov, A[i], A[i + 1], Rov[i + 1])
+        X0 = np.tensordot(x[i], x[i + 1], axes=([2], [0]))
+        mv = lambda V: alpha * V + c * ls.heff_apply(Lop, Ws[i], Ws[i + 1], Rop[i + 1], V)
+        X, _ = ls.gmres(mv, B, X0, 10)
+        x[i], x[i + 1], _, _ = ls.split_two_site(X, chi, 1e-14, True)
+        Lop = ls.left_env_update(Lop, x[i], Ws[i], x[i])
+        Lov = ls.left_overlap_update(Lov, x[i], A[i])
+        if i >= first_bulk:
+            t_bulk += time.perf_counter() - t1
+            n_done += 1
+        i += 1
+
+    def fl(chl, chr_):
+        return 6 * d * d * chl * chr_ * (chl + chr_) + 2 * 36 * d ** 3 * chl * chr_
+    bulk = fl(chi, chi)
+    equiv = 2.0 * sum(fl(cap[j], cap[j + 2]) / bulk for j in range(N - 1))
+    return t_bulk / n_bonds, equiv
+
+
 def run_anderson(args):
     """The first --steps steps of the Anderson-impurity evolution: impurity plus
     99 bath sites (N = 100, d = 4, MPO bond dimension 6), flat band of
@@ -827,6 +870,16 @@ def run_anderson(args):
                       "start": "random product state, seed 3000", "precision": args.precision},
            "steps": steps,
            "tau_steps_per_s": len(steps) / (sum(x["ms"] for x in steps) * 1e-3)}
+    if not args.no_cpu_baseline:
+        t64, eq64 = oracle_anderson_sample(64, 2)
+        out["cpu_baseline"] = {
+            "kind": "oracle, extrapolated", "cores": os.cpu_count(),
+            "seconds_per_bulk_update_chi64": t64, "bulk_equivalent_updates": eq64,
+            "seconds_per_step_chi64": t64 * eq64,
+            "seconds_per_step_chi512_extrapolated": t64 * eq64 * (512 / 64) ** 3,
+            "sample": ("the oracle's first two bulk two-site updates of a step at a saturated "
+                       "chi = 64 (random isometries, seed 3000), times the step's "
+                       "bulk-equivalent updates at chi = 64, then the chi^3 law to chi = 512")}
     print(json.dumps(out), flush=True)
 
 

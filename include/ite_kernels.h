@@ -147,7 +147,7 @@ ite_status ite_k_gemm_bf16(ite_ctx ctx, int M, int N, int K, const void* A, long
  * B[k sBk + j sBn]; C is row-major with leading dimension ldc (complex
  * units).  mode 0: native FP64 arithmetic.  mode 1: FP64-class accuracy from
  * the bf16 tensor cores by exact 7-bit slicing of A and B (error below about
- * K 2^-48 max|A row| max|B column|).  alpha, beta may be NULL (1, 0). */
+ * K 2^-52 max|A row| max|B column|).  alpha, beta may be NULL (1, 0). */
 ite_status ite_k_zgemm(ite_ctx ctx, int mode, int M, int N, int K, const double* A, long long sAm,
                        long long sAk, int conjA, const double* B, long long sBk, long long sBn,
                        int conjB, double* C, long long ldc, const double alpha[2],

@@ -7,24 +7,31 @@
 //    A^ (rows 2r, 2r+1 = [Re, -Im], [Im, Re] interleaved along K) with the
 //    K-major B^T (rows = columns of B, (Re, Im) interleaved along K);
 //  * every row of A^ and every row of B^T is scaled by its own power of two
-//    2^e (largest magnitude < 2^e) and cut into S = 7 signed 7-bit digits,
-//    x = 2^e sum_p a_p 2^(-7p) (truncation error < 2^(e-49)); each digit is an
-//    integer in [-127, 127], exact in bf16.  The slicing uses integer
-//    operations on the bit patterns only;
-//  * digit products a_p b_q (|.| < 2^14) of the same weight d = p + q are
-//    accumulated by tcgen05.mma in one fp32 TMEM accumulator per d = 2..S+1
-//    over K-chunks of 128 real terms, so every partial sum is an integer below
-//    (d-1) 128 2^14 <= 2^24 and fp32 accumulation is exact;
+//    2^e (largest magnitude < 2^e), rounded to the nearest multiple of
+//    2^(e-56) (error <= 2^(e-57)) and cut into S = 8 balanced base-128
+//    digits, x = 2^e sum_p a_p 2^(-7p) with a_1 in [-128, 128] and the lower
+//    digits in [-64, 64], zero-centred so that the rounding and the dropped
+//    products below are unbiased.  Each digit is exact in bf16.  The slicing
+//    uses integer operations on the bit patterns only;
+//  * digit products a_p b_q of the same weight d = p + q are accumulated by
+//    tcgen05.mma in one fp32 TMEM accumulator per d = 2..S+1 over K-chunks of
+//    128 real terms: |a_1 b_1| <= 2^14 and every other product is at most
+//    2^13, so every partial sum is an integer of magnitude below
+//    128 (2 2^13 + (S-2) 2^12) < 2^24 and fp32 accumulation is exact;
 //  * after each chunk the epilogue warps convert the accumulators to integers
 //    and add them exactly into two int64 registers per output
-//    (hi = sum_{d<=4} v_d 2^(7(4-d)), lo = sum_{d>=5} v_d 2^(7(8-d))); the
-//    result is 2^(eA+eB) (hi 2^-28 + lo 2^-56), rounded once to FP64.
-//  Products of weight d > S+1 are dropped; with the truncation this gives an
-//  error below about K 2^-48 |A_row| |B_col| (max-norms), i.e. FP64-class.
+//    (hi = sum_{d<=4} v_d 2^(7(4-d)), lo = sum_{d>=5} v_d 2^(7(S+1-d))); the
+//    result is 2^(eA+eB) (hi 2^-28 + lo 2^-7(S+1)), rounded once to FP64.
+//  Products of weight d > S+1 are dropped (both digits are low ones: at most
+//  (S-1) 2^12 2^(-7(S+2)) < 2^-55 per term, of either sign); with the
+//  rounding this gives an error below about K 2^-54 |A_row| |B_col|
+//  (max-norms) in the worst case and about sqrt(K) of that for unrelated
+//  terms: FP64-class, at the rounding level of an FP64 product of the same
+//  length.
 //
 // Tiles: 128 real rows x 32 columns, K tiles of 32 (64-byte swizzle); a ring
-// of 3 stages each holding the 7 digit tiles of A and of B (70 KB); 7
-// accumulators of 32 columns, double-buffered (448 TMEM columns) so the
+// of 2 stages each holding the 8 digit tiles of A and of B (80 KB); 8
+// accumulators of 32 columns, double-buffered (512 TMEM columns) so the
 // epilogue of one chunk overlaps the MMAs of the next.  Warps 0-3: epilogue
 // (TMEM lane quarters), warp 4: TMA producer, warp 5: MMA issuer.  All waits
 // are bounded.
@@ -42,12 +49,15 @@ namespace {
 
 using namespace tc;
 
-constexpr int S = 7;
+constexpr int S = 8;
 constexpr int BM = 128, BN = 32, BK = 32;
 constexpr int KC = 128;                         // real K terms per exact chunk
 constexpr int KB_PER_CHUNK = KC / BK;           // 4
-constexpr int STAGES = 3;
-constexpr int ACC_COLS = S * BN;                // 224 per buffer
+constexpr int STAGES = 2;
+constexpr int ACC_COLS = S * BN;                // 256 per buffer
+static_assert(S == 8, "the epilogue's lo word is scaled by 2^-7(S+1) = 2^-63");
+static_assert(128 * (2 * (1 << 13) + (S - 2) * (1 << 12)) < (1 << 24) && 128 * (1 << 14) < (1 << 24),
+              "chunk sums must stay exact in fp32");
 constexpr int THREADS = 192;
 constexpr uint32_t A_SLICE = BM * BK * 2;       // 8 KB
 constexpr uint32_t B_SLICE = BN * BK * 2;       // 2 KB
@@ -183,7 +193,7 @@ k_zgemm_slices(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
           for (int j = 0; j < BN; ++j) hi[j] += (long long)__float2int_rn(v[j]) << sh;
         } else {
-          const int sh = 7 * (8 - d);
+          const int sh = 7 * (S + 1 - d);
 #pragma unroll
           for (int j = 0; j < BN; ++j) lo[j] += (long long)__float2int_rn(v[j]) << sh;
         }
@@ -194,7 +204,7 @@ k_zgemm_slices(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (!ok) {
       if (lane == 0) atomicExch(err, 1);
     } else {
-      // value of real row rr, column n: 2^(eA+eB) (hi 2^-28 + lo 2^-56)
+      // value of real row rr, column n: 2^(eA+eB) (hi 2^-28 + lo 2^-7(S+1))
       const int rr = m0 + warp * 32 + lane;
       const int ea = (rr < Mr) ? eA[rr >> 1] : 0;
       double val[BN];
@@ -202,7 +212,7 @@ k_zgemm_slices(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int j = 0; j < BN; ++j) {
         const int n = n0 + j;
         const int eb = (n < N) ? eB[n] : 0;
-        const double base = fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-56);
+        const double base = fma((double)hi[j], 0x1p-28, (double)lo[j] * 0x1p-63);
         val[j] = base * pow2(ea + eb);
       }
       // lanes 2i / 2i+1 hold Re / Im of complex row rr/2: the even lane
@@ -251,7 +261,9 @@ __device__ __forceinline__ int scale_exponent(unsigned long long mb) {
   return E - 1023 + 1;
 }
 
-// T = floor(|x| 2^(7S - e)) < 2^(7S), from the bit pattern
+// T = |x| 2^(7S - e) rounded to the nearest integer (ties up), from the bit
+// pattern.  With max|x| < 2^e the row maximum has a shift of 3 and is exact;
+// T < 2^(7S) for every entry of the row.
 __device__ __forceinline__ unsigned long long fixed_digits(double x, int e) {
   const unsigned long long b = mag_bits(x);
   const int E = (int)(b >> 52);
@@ -260,13 +272,27 @@ __device__ __forceinline__ unsigned long long fixed_digits(double x, int e) {
   if (E == 0) Ee = 1; else mant |= 0x0010000000000000ull;
   const int shift = Ee - 1075 + 7 * S - e;      // |x| = mant 2^(Ee-1075)
   if (shift >= 0) return shift >= 64 ? 0ull : mant << shift;
-  return (-shift) >= 64 ? 0ull : mant >> (-shift);
+  const int r = -shift;
+  return r >= 64 ? 0ull : (mant + (1ull << (r - 1))) >> r;
 }
 
-__device__ __forceinline__ __nv_bfloat16 digit(unsigned long long T, int p, bool neg) {
-  const int a = (int)((T >> (7 * (S - p))) & 127ull);
-  return __float2bfloat16_rn((float)(neg ? -a : a));
+// Balanced base-128 digits of T: T = sum_p g_p 2^(7(S-p)) with the leading
+// g_1 in [0, 128] and g_p in [-64, 63] for p >= 2 (a low digit >= 64 becomes
+// g - 128 with a carry into the next one), all negated for x < 0.  The low
+// digits are then centred on zero, so neither the dropped low-weight
+// products nor the rounding give the sums a bias toward zero.
+__device__ __forceinline__ void balanced_digits(unsigned long long T, bool neg, int (&g)[S]) {
+  int carry = 0;
+#pragma unroll
+  for (int p = S; p >= 1; --p) {
+    int v = (int)((T >> (7 * (S - p))) & 127ull) + carry;
+    carry = 0;
+    if (p > 1 && v >= 64) { v -= 128; carry = 1; }
+    g[p - 1] = neg ? -v : v;
+  }
 }
+
+__device__ __forceinline__ __nv_bfloat16 bf(int v) { return __float2bfloat16_rn((float)v); }
 
 // A (M x K complex, element (r,k) at A[r sAm + k sAk], conj) -> digits of the
 // real rows 2r (Re, -Im interleaved) and 2r+1 (Im, Re), one warp per row r.
@@ -299,11 +325,13 @@ __global__ void k_slice_rows_A(const cplx* __restrict__ A, long long sAm, long l
       re = v.x;
       im = conj ? -v.y : v.y;
     }
-    const unsigned long long Tr = fixed_digits(re, e), Ti = fixed_digits(im, e);
-    const bool nr = re < 0.0, ni = im < 0.0;
+    int gr[S], gi[S];
+    balanced_digits(fixed_digits(re, e), re < 0.0, gr);
+    balanced_digits(fixed_digits(im, e), im < 0.0, gi);
+#pragma unroll
     for (int p = 1; p <= S; ++p) {
       __nv_bfloat16* blk = out + (long long)(p - 1) * Mr * Kp;
-      const __nv_bfloat16 dr = digit(Tr, p, nr), di = digit(Ti, p, ni), dmi = digit(Ti, p, !ni);
+      const __nv_bfloat16 dr = bf(gr[p - 1]), di = bf(gi[p - 1]), dmi = bf(-gi[p - 1]);
       __nv_bfloat162 even, oddv;
       even.x = dr; even.y = dmi;                 // row 2r:   Re, -Im
       oddv.x = di; oddv.y = dr;                  // row 2r+1: Im,  Re
@@ -343,12 +371,14 @@ __global__ void k_slice_cols_B(const cplx* __restrict__ B, long long sBk, long l
       re = v.x;
       im = conj ? -v.y : v.y;
     }
-    const unsigned long long Tr = fixed_digits(re, e), Ti = fixed_digits(im, e);
-    const bool nr = re < 0.0, ni = im < 0.0;
+    int gr[S], gi[S];
+    balanced_digits(fixed_digits(re, e), re < 0.0, gr);
+    balanced_digits(fixed_digits(im, e), im < 0.0, gi);
+#pragma unroll
     for (int p = 1; p <= S; ++p) {
       __nv_bfloat162 pr;
-      pr.x = digit(Tr, p, nr);
-      pr.y = digit(Ti, p, ni);
+      pr.x = bf(gr[p - 1]);
+      pr.y = bf(gi[p - 1]);
       *reinterpret_cast<__nv_bfloat162*>(out + ((long long)(p - 1) * N + n) * Kp + 2 * kk) = pr;
     }
   }

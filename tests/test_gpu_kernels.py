@@ -64,7 +64,7 @@ def test_heff_matches_oracle(api, ctx, model, dims):
 def test_heff_and_env_tensor_core_mode(api, model, dims):
     # kernel-level H_eff and environment update with the contractions on the
     # tensor cores (FP64-class slicing): same results as the oracle within
-    # the emulation's bound K 2^-48 relative to the largest products
+    # the emulation's bound K 2^-52 relative to the largest products
     kctx = api.ctx_create(0)
     api.set_kernel_precision(kctx, "fp64_tc")
     Ws = _models()[model]

@@ -1,10 +1,11 @@
-"""FP64-class complex GEMM on the bf16 tensor cores (exact 7-bit slicing)
+"""FP64-class complex GEMM on the bf16 tensor cores (exact slicing into 7-bit digits)
 against the FP64 product computed on the host.
 
-Error model: each operand entry is truncated to 49 bits below its row (A) or
-column (B) maximum and digit products of weight above 8 are dropped, so
-|C - C_exact|_ij <= c K 2^-48 max_k|A_ik| max_k|B_kj| with c small; the test
-allows c = 8 and reports the worst ratio."""
+Error model: each operand entry is truncated to 56 bits below its row (A) or
+column (B) maximum and digit products of weight above 9 are dropped (each
+below 2^-53 of the largest product), so
+|C - C_exact|_ij <= c K 2^-52 max_k|A_ik| max_k|B_kj| with c small; the test
+allows c = 8 and reports the worst ratio (native FP64 meets the same bar)."""
 import numpy as np
 import pytest
 
@@ -59,9 +60,9 @@ def test_emulated_zgemm_matches_fp64(api, ctx, M, N, K, tA, tB, cA, cB):
         got = Cd.cpu().numpy()
         rowmax = np.maximum(np.abs(opA.real), np.abs(opA.imag)).max(axis=1)
         colmax = np.maximum(np.abs(opB.real), np.abs(opB.imag)).max(axis=0)
-        bound = 2 * K * 2.0 ** -48 * rowmax[:, None] * colmax[None, :]
+        bound = 2 * K * 2.0 ** -52 * rowmax[:, None] * colmax[None, :]
         ratio = (np.abs(got - exact) / bound).max()
-        print(f"mode {mode} M={M} N={N} K={K}: worst error / (2K 2^-48 rowmax colmax) = {ratio:.3g}")
+        print(f"mode {mode} M={M} N={N} K={K}: worst error / (2K 2^-52 rowmax colmax) = {ratio:.3g}")
         assert np.isfinite(got).all()
         assert ratio <= 8.0
 
