@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_jacobi_persistent launch on the bulk
 # 512 x 512 split from the ncu capture of this kernel source summarised in
 # profiles/k_jacobi_persistent_split512.md (None once the kernel changes).
-JACOBI_TRAFFIC_BYTES = 4.334592e6 + 1.230848e6
+JACOBI_TRAFFIC_BYTES = 4.266752e6 + 1.186048e6
 JACOBI_TRAFFIC_NOTE = ("dram bytes per launch on the 512 x 512 bulk split (ncu, "
                        "profiles/k_jacobi_persistent_split512.md); the matrix is L2-resident, "
                        "the kernel is FP64-bound")
@@ -90,6 +90,13 @@ def parse():
     ap.add_argument("--lp-shape", default="all",
                     help="--only heff_lp: all, heisenberg512, heisenberg1024 or anderson512")
     ap.add_argument("--jobs", type=int, default=16, help="jobs in the batch sample")
+    ap.add_argument("--no-single", action="store_true", help="batch: skip the one-at-a-time arm")
+    ap.add_argument("--batch-ns", default="16,24,32,48,64", help="batch: chain lengths drawn from")
+    ap.add_argument("--grouping-mode", type=int, default=1, choices=[1, 2],
+                    help="batch: grouping mode of the grouped arm (1 continuous, 2 gather)")
+    ap.add_argument("--batch-chis", default="32,64,128,256", help="batch: bond caps drawn from")
+    ap.add_argument("--anderson-start", choices=["product", "saturated"], default="product",
+                    help="anderson: start from a product state or at the saturated chi")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-baths", default="9,19,29", help="serve: bath sizes drawn from")
     ap.add_argument("--serve-chis", default="16,32,64", help="serve: bond caps drawn from")
@@ -348,11 +355,11 @@ def heff_lp_rates(api, ctx, precisions=("mixed_bf16",), reps=10, shapes=LP_SHAPE
             api.k_heff_lp_prepare(ctx, H, i, L, R, prec)
             for _ in range(3):
                 api.k_heff_lp_apply(ctx, H, i, X, Y, 1.0, X, 0.5)
+            # back-to-back matvecs (one host synchronisation), as in a Krylov cycle
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(reps):
-                api.k_heff_lp_apply(ctx, H, i, X, Y, 1.0, X, 0.5)
+            api.k_heff_lp_apply_n(ctx, H, i, X, Y, 1.0, X, 0.5, reps=reps)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
@@ -623,21 +630,28 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_batch(args):
-    """Served execution of a bounded sample of the batched workload: Heisenberg
-    chains with N drawn from {16, 24, 32, 48, 64} and chi_max from {32, 64, 128}
-    (seed 4000; the chi = 256 draws of the full workload are left out of this
-    sample to bound its time), random product starts (seed 4000 + i), backward
-    Euler on the geometric grid 1e-2 -> 1e2 in --steps steps, tensor-core mode.
-    Runs the same jobs one at a time (1 slot) and side by side (--slots) and
-    prints one JSON line (not the benchmark line): tau-steps/s, p50/p99
-    latency, and the speed-up of serving over one-at-a-time."""
+    """Served execution of the batched workload: --jobs Heisenberg chains (64
+    at the full specification) with N drawn from {16, 24, 32, 48, 64} and
+    chi_max from {32, 64, 128, 256} (seed 4000), random product starts (seed
+    4000 + i), backward Euler on the geometric grid 1e-2 -> 1e2 in --steps steps
+    (30 at the full specification), shift = the current energy, in
+    --precision (mixed_bf16: bf16 contractions with fp32 accumulation, FP64
+    SVD and Krylov, local solves refined to 1e-10).  The same jobs run served
+    on --slots workers with the splits' Jacobi grouped across jobs, served
+    without grouping, and (unless --no-single) one at a time.  Prints one JSON
+    line (not the benchmark line): tau-steps/s, p50/p99 latency, the grouped
+    launches, and the speed-ups."""
     import torch
     from paper_2606_02930_gb300 import api, inputs
     torch.cuda.init()
     rng = np.random.default_rng(4000)
-    Ns = rng.choice([16, 24, 32, 48, 64], size=args.jobs)
-    chis = rng.choice([32, 64, 128], size=args.jobs)
-    opts = api.solver_opts(precision=args.precision)
+    Ns = rng.choice([int(x) for x in args.batch_ns.split(",")], size=args.jobs)
+    chis = rng.choice([int(x) for x in args.batch_chis.split(",")], size=args.jobs)
+    prec = args.precision
+    if prec.startswith("mixed"):
+        opts = api.solver_opts(precision=prec, refine_tol=1e-10, refine_max=20)
+    else:
+        opts = api.solver_opts(precision=prec)
 
     def make():
         return [api.Job("heisenberg", int(N), inputs.random_product_state(int(N), 2, 4000 + i),
@@ -646,15 +660,30 @@ def run_batch(args):
 
     api.evolve_batch(make()[:2], n_slots=2)          # warm-up: build caches, page in kernels
     out = {"workload": "batch", "metric": "tau-steps/s and p50/p99 latency of served jobs",
-           "jobs": int(args.jobs), "steps_per_job": args.steps, "precision": args.precision,
-           "sample": ("Heisenberg N in {16,24,32,48,64}, chi_max in {32,64,128} (seed 4000), "
-                      "BE 1e-2 -> 1e2")}
-    for slots in (1, args.slots):
-        res, st = api.evolve_batch(make(), n_slots=slots)
+           "jobs": int(args.jobs), "steps_per_job": args.steps, "precision": prec,
+           "sample": (f"Heisenberg N in {{{args.batch_ns}}}, chi_max in {{{args.batch_chis}}} "
+                      "(seed 4000), BE 1e-2 -> 1e2, shift = current energy"),
+           "chi_max_drawn": [int(c) for c in chis], "N_drawn": [int(n) for n in Ns]}
+    arms = [("grouped", args.slots, args.grouping_mode), ("ungrouped", args.slots, 0)]
+    if not args.no_single:
+        arms.append(("one_at_a_time", 1, 0))
+    energies = {}
+    for name, slots, grouping in arms:
+        jobs = make()
+        res, st = api.evolve_batch(jobs, n_slots=slots, grouping=grouping)
         assert all(r["status"] == 0 for r in res)
-        out[f"slots{slots}"] = {k: st[k] for k in ("tau_steps_per_s", "p50_latency_ms",
-                                                   "p99_latency_ms", "wall_ms", "peak_running")}
-    out["speedup"] = out[f"slots{args.slots}"]["tau_steps_per_s"] / out["slots1"]["tau_steps_per_s"]
+        energies[name] = [float(r["energy"]) for r in res]
+        out[name] = {"slots": slots, "grouping_mode": grouping,
+                     **{k: st[k] for k in ("tau_steps_per_s", "p50_latency_ms",
+                                                           "p99_latency_ms", "wall_ms",
+                                                           "peak_running", "group_launches",
+                                                           "group_items")}}
+    out["same_energies"] = all(energies[a] == energies["grouped"] for a in energies)
+    out["speedup_grouped_over_ungrouped"] = (out["grouped"]["tau_steps_per_s"]
+                                             / out["ungrouped"]["tau_steps_per_s"])
+    if "one_at_a_time" in out:
+        out["speedup_grouped_over_one_at_a_time"] = (out["grouped"]["tau_steps_per_s"]
+                                                     / out["one_at_a_time"]["tau_steps_per_s"])
     print(json.dumps(out), flush=True)
 
 
@@ -835,8 +864,13 @@ def run_anderson(args):
     eps, V = inputs.flat_band_bath(n_bath)
     ctx = api.ctx_create(0)
     H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
-    vecs = inputs.random_product_state(n_bath + 1, 4, 3000)
-    psi = api.mps_create_product(ctx, vecs, chi)
+    if args.anderson_start == "saturated":
+        # the bond dimension the evolution saturates at: random isometries with
+        # slowly decaying bond weights, chi = 512 in the bulk (seed 3000)
+        psi = api.mps_create(ctx, inputs.random_isometric_mps(n_bath + 1, 4, chi, 3000), chi)
+    else:
+        vecs = inputs.random_product_state(n_bath + 1, 4, 3000)
+        psi = api.mps_create_product(ctx, vecs, chi)
     nodes = api.grid_geometric(1e-2, 1e4, 50)
     opts = api.solver_opts(precision=args.precision)
     s = api.energy(ctx, H, psi)
@@ -867,7 +901,10 @@ def run_anderson(args):
                                "D=1, Gamma=0.05, U=0.3, eps_d=-U/2",
                       "chi_max": chi, "cutoff": cutoff, "scheme": "backward_euler",
                       "grid": "geometric 1e-2 -> 1e4, 50 steps", "shift": "current energy",
-                      "start": "random product state, seed 3000", "precision": args.precision},
+                      "start": ("saturated synthetic state (random isometries, chi = 512 in "
+                                "the bulk), seed 3000" if args.anderson_start == "saturated"
+                                else "random product state, seed 3000"),
+                      "precision": args.precision},
            "steps": steps,
            "tau_steps_per_s": len(steps) / (sum(x["ms"] for x in steps) * 1e-3)}
     if not args.no_cpu_baseline:
@@ -885,49 +922,40 @@ def run_anderson(args):
 
 def run_serve(args):
     """A Poisson stream of impurity evolutions through the server, after the
-    served workload's arrival process (mean rate --rate per second, seed 5000)
-    and parameter draws (U ~ U[0.05, 0.6], Gamma ~ U[0.02, 0.1], tau_max from
-    {1e2, 1e3, 1e4}, geometric grids from 1e-2 with ceil(10 log10(tau_max /
-    1e-2)) steps, random product starts), with the bath sizes and bond caps
-    scaled down to --serve-baths and --serve-chis so that the stream finishes
-    in minutes.  The same requests run served (--slots workers, mixed bf16)
-    and one at a time in plain FP64 (1 worker); both arms converge every local
-    solve (refinement / restarted GMRES to 1e-8), so they reach equal
-    accuracy.  Prints one JSON line (not the benchmark line)."""
+    served workload's arrival process and parameter draws
+    (inputs.serve_stream: mean rate --rate per second, seed 5000, U ~ U[0.05,
+    0.6], Gamma ~ U[0.02, 0.1], tau_max from {1e2, 1e3, 1e4}, geometric grids
+    from 1e-2 with ceil(10 log10(tau_max / 1e-2)) steps, random product
+    starts), with the bath sizes and bond caps scaled down to --serve-baths and
+    --serve-chis so that the stream finishes in minutes.  The same requests run
+    served (--slots workers, mixed bf16) and one at a time in plain FP64 (1
+    worker); both arms converge every local solve (refinement / restarted
+    GMRES to 1e-8), and each arm's final energies are compared with the
+    oracle's converged evolutions (tests/golden/serve_reference_energies.json,
+    when it holds this stream).  Prints one JSON line (not the benchmark
+    line)."""
     import torch
     from paper_2606_02930_gb300 import api, inputs
     torch.cuda.init()
-    rng = np.random.default_rng(5000)
     n = args.jobs
-    baths = [int(x) for x in args.serve_baths.split(",")]
-    chis = [int(x) for x in args.serve_chis.split(",")]
-    gaps = rng.exponential(1.0 / args.rate, size=n)
-    Us = rng.uniform(0.05, 0.6, n)
-    Gs = rng.uniform(0.02, 0.1, n)
-    nbs = rng.choice(baths, n)
-    cxs = rng.choice(chis, n)
-    tms = rng.choice([1e2, 1e3, 1e4], n)
+    baths = tuple(int(x) for x in args.serve_baths.split(","))
+    chis = tuple(int(x) for x in args.serve_chis.split(","))
+    reqs = inputs.serve_stream(n, args.rate, baths, chis)
 
     def make(prec):
         if prec == "fp64":
             o = api.solver_opts(precision="fp64", local_tol=1e-8, max_cycles=200)
         else:
             o = api.solver_opts(precision=prec, refine_tol=1e-8, refine_max=20)
-        jobs = []
-        for i in range(n):
-            eps, V = inputs.flat_band_bath(int(nbs[i]), gamma=float(Gs[i]))
-            K = int(np.ceil(10 * np.log10(tms[i] / 1e-2)))
-            jobs.append(api.Job("anderson", int(nbs[i]),
-                                inputs.random_product_state(int(nbs[i]) + 1, 4, 5000 + i),
-                                int(cxs[i]), 1e-14, 1e-2, float(tms[i]), K, scheme="be",
-                                U=float(Us[i]), eps_d=-0.5 * float(Us[i]), eps=eps, V=V, opts=o))
-        return jobs
+        return [api.Job("anderson", r["n_bath"], r["site_vecs"], r["chi_max"], 1e-14, 1e-2,
+                        r["tau_max"], r["n_steps"], scheme="be", U=r["U"], eps_d=r["eps_d"],
+                        eps=r["eps"], V=r["V"], opts=o) for r in reqs]
 
     def stream(jobs, slots):
         srv = api.Server(0, n_slots=slots)
         tickets = []
-        for j, g in zip(jobs, gaps):
-            time.sleep(float(g))
+        for j, r in zip(jobs, reqs):
+            time.sleep(r["gap_s"])
             tickets.append(srv.submit(j))
         res = [srv.wait(t) for t in tickets]
         st = srv.stats()
@@ -947,15 +975,26 @@ def run_serve(args):
     dE = max(abs(a - b) / abs(b) for a, b in zip(served["energies"], single["energies"]))
     out = {"workload": "serve", "metric": "p50/p99 latency and tau-steps/s of a served stream",
            "config": {"requests": n, "rate_per_s": args.rate, "seed": 5000,
-                      "bath_sites": baths, "chi_max": chis, "tau_max": [1e2, 1e3, 1e4],
-                      "U": [0.05, 0.6], "Gamma": [0.02, 0.1], "cutoff": 1e-14,
+                      "bath_sites": list(baths), "chi_max": list(chis),
+                      "tau_max": [1e2, 1e3, 1e4], "U": [0.05, 0.6], "Gamma": [0.02, 0.1],
+                      "cutoff": 1e-14,
                       "scaled": "bath sizes and bond caps scaled down from the served "
                                 "workload's {49,99,199} and {128,...,1024}"},
            "served_mixed_bf16": {k: v for k, v in served.items() if k != "energies"},
            "one_at_a_time_fp64": {k: v for k, v in single.items() if k != "energies"},
-           "max_rel_energy_diff": dE,
+           "max_rel_energy_diff_between_arms": dE,
            "throughput_ratio": served["tau_steps_per_s"] / single["tau_steps_per_s"],
            "p99_ratio": single["p99_latency_ms"] / served["p99_latency_ms"]}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "serve_reference_energies.json")) as f:
+            ref = json.load(f)
+        if ref["n"] == n and tuple(ref["baths"]) == baths and tuple(ref["chis"]) == chis:
+            e = ref["energies"]
+            for name, arm in (("served_mixed_bf16", served), ("one_at_a_time_fp64", single)):
+                out[name]["max_rel_energy_error_vs_oracle"] = max(
+                    abs(a - b) / abs(b) for a, b in zip(arm["energies"], e))
+    except (OSError, ValueError, KeyError):
+        pass
     print(json.dumps(out), flush=True)
 
 

@@ -48,6 +48,15 @@ ite_status ite_k_heff_lp_prepare(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int
 ite_status ite_k_heff_lp_apply(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
                                int chr_ket, int chr_bra, const double* X, double* Y,
                                const double alpha[2], const double* Z, const double gamma[2]);
+/* The same matvec `reps` times back to back on the context stream, with one
+ * host synchronisation at the end, as the matvecs of a Krylov cycle run (App.
+ * B's local solve issues them without host round trips); Y ends as one apply
+ * leaves it.  For timing the matvec as the solve sees it.  ITE_EINVAL for
+ * reps < 1 or Y equal to X or Z. */
+ite_status ite_k_heff_lp_apply_n(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                                 int chr_ket, int chr_bra, const double* X, double* Y,
+                                 const double alpha[2], const double* Z, const double gamma[2],
+                                 int reps);
 
 /* Two-site effective Hamiltonian on sites (i, i+1) of the MPO (the dominant
  * operation of the local solves, App. B):

@@ -109,6 +109,8 @@ typedef struct {
   double wall_ms;             /* first submission -> last completion                 */
   double tau_steps;           /* steps completed over all jobs                       */
   double tau_steps_per_s;     /* tau_steps / wall                                    */
+  long long group_launches;   /* grouped Jacobi launches (see ite_server_set_grouping) */
+  long long group_items;      /* splits those launches carried                       */
 } ite_server_stats;
 
 typedef struct ite_server_s* ite_server;
@@ -126,6 +128,23 @@ ite_status ite_server_create(int device, int n_slots, size_t mem_budget, ite_ser
 ite_status ite_server_submit(ite_server s, const ite_job* job, long long* ticket);
 /* ITE_OK and *out when the job has finished, ITE_PENDING before. */
 ite_status ite_server_poll(ite_server s, long long ticket, ite_job_result* out);
+/* Grouped launches across jobs.  The one-sided Jacobi of a truncated split
+ * (the SVD that follows every two-site solve, App. B) is a chain of dependent
+ * rounds that leaves most of the GPU idle, and two large ones already take
+ * every block the SMs hold at once.  With grouping, a running job posts the
+ * Jacobi of each split to the server instead of launching it, and posts go to
+ * the device together as one cooperative launch (k_jacobi_grouped).
+ *   mode 0: off (each job launches its own Jacobi);
+ *   mode 1 (default): continuous batching: a post goes out at once if it fits
+ *     next to the grouped launches still running, else as soon as every
+ *     running job outside a running launch has posted, a running launch has
+ *     made room, or the first post has waited window_ms (default 20);
+ *   mode 2: gather: posts wait for every running job's post, or window_ms.
+ * A post waits on the host only, never on the GPU.  Each split ends bit for
+ * bit as it would alone, so results do not depend on the mode.  Applies to
+ * jobs that start after the call.  ITE_EINVAL for a mode outside 0..2 or
+ * window_ms outside [0, 1e4]. */
+ite_status ite_server_set_grouping(ite_server s, int mode, double window_ms);
 /* Block until the job has finished. */
 ite_status ite_server_wait(ite_server s, long long ticket, ite_job_result* out);
 /* Block until every submitted job has finished. */
@@ -138,6 +157,11 @@ void ite_server_destroy(ite_server s);
  * out[n] receives the results in job order; stats may be NULL. */
 ite_status ite_evolve_batch(int device, int n_slots, size_t mem_budget, int n, const ite_job* jobs,
                             ite_job_result* out, ite_server_stats* stats);
+/* The same with the grouping mode and window of ite_server_set_grouping
+ * (ite_evolve_batch uses mode 1, window 20 ms). */
+ite_status ite_evolve_batch_grouped(int device, int n_slots, size_t mem_budget, int grouping,
+                                    double window_ms, int n, const ite_job* jobs,
+                                    ite_job_result* out, ite_server_stats* stats);
 
 #ifdef __cplusplus
 }

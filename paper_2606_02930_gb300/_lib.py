@@ -70,7 +70,8 @@ class ite_server_stats(C.Structure):
                 ("failed", C.c_longlong), ("peak_running", C.c_int),
                 ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
                 ("wall_ms", C.c_double), ("tau_steps", C.c_double),
-                ("tau_steps_per_s", C.c_double)]
+                ("tau_steps_per_s", C.c_double), ("group_launches", C.c_longlong),
+                ("group_items", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -131,6 +132,7 @@ SIGNATURES = {
                            C.c_longlong, C.c_longlong, _vp, C.c_longlong, C.c_longlong,
                            C.c_longlong, _i, _i, _i, _i]),
     "ite_k_heff_lp_apply": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _pd, _vp, _pd]),
+    "ite_k_heff_lp_apply_n": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _pd, _vp, _pd, _i]),
     "ite_k_local_solve": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _d, _d, _i, _d, _pi, _pd]),
     "ite_k_gemm_bf16": (_i, [_vp, _i, _i, _i, _vp, C.c_longlong, _vp, C.c_longlong, _vp,
                              C.c_longlong, _i]),
@@ -154,6 +156,9 @@ SIGNATURES = {
     "ite_server_destroy": (None, [_vp]),
     "ite_evolve_batch": (_i, [_i, _i, _sz, _i, C.POINTER(ite_job), C.POINTER(ite_job_result),
                               C.POINTER(ite_server_stats)]),
+    "ite_evolve_batch_grouped": (_i, [_i, _i, _sz, _i, C.c_double, _i, C.POINTER(ite_job),
+                                      C.POINTER(ite_job_result), C.POINTER(ite_server_stats)]),
+    "ite_server_set_grouping": (_i, [_vp, _i, C.c_double]),
 }
 
 

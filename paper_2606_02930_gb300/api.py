@@ -391,6 +391,15 @@ def k_heff_lp_apply(ctx, H, i, X, Y, alpha=1.0, Z=None, gamma=0.0):
                                   _dptr(_cpair(gamma))), ctx.h)
 
 
+def k_heff_lp_apply_n(ctx, H, i, X, Y, alpha=1.0, Z=None, gamma=0.0, reps=1):
+    """k_heff_lp_apply reps times back to back, one synchronisation at the end."""
+    chlK, chrK = X.shape[0], X.shape[3]
+    chlB, chrB = Y.shape[0], Y.shape[3]
+    check(lib.ite_k_heff_lp_apply_n(ctx.h, H.h, i, chlB, chlK, chrK, chrB, _p(X), _p(Y),
+                                    _dptr(_cpair(alpha)), _p(Z) if Z is not None else None,
+                                    _dptr(_cpair(gamma)), int(reps)), ctx.h)
+
+
 def k_env_left(ctx, H, i, Lin, bra, ket, Lout):
     check(lib.ite_k_env_left(ctx.h, H.h, i, bra.shape[0], ket.shape[0], bra.shape[2], ket.shape[2],
                              _p(Lin), _p(bra), _p(ket), _p(Lout)), ctx.h)
@@ -620,11 +629,16 @@ class MettsJob:
 class Server:
     """Independent evolutions side by side on one GPU (ite_server.h)."""
 
-    def __init__(self, device=0, n_slots=4, mem_budget=0):
+    def __init__(self, device=0, n_slots=4, mem_budget=0, grouping=1, window_ms=20.0):
         h = C.c_void_p()
         check(lib.ite_server_create(device, n_slots, mem_budget, C.byref(h)))
         self.h = h
         self.jobs = {}
+        self.set_grouping(grouping, window_ms)
+
+    def set_grouping(self, mode=1, window_ms=20.0):
+        """mode 0 off, 1 continuous batching, 2 gather (True means 1)."""
+        check(lib.ite_server_set_grouping(self.h, int(mode), float(window_ms)))
 
     def submit(self, job):
         t = C.c_longlong()
@@ -665,11 +679,12 @@ class Server:
             pass
 
 
-def evolve_batch(jobs, n_slots=4, mem_budget=0, device=0):
+def evolve_batch(jobs, n_slots=4, mem_budget=0, device=0, grouping=1, window_ms=20.0):
     """Run Job objects through a temporary server; returns (results, stats)."""
     n = len(jobs)
     arr = (L.ite_job * n)(*[j.c for j in jobs])
     res = (L.ite_job_result * n)()
     st = L.ite_server_stats()
-    check(lib.ite_evolve_batch(device, n_slots, mem_budget, n, arr, res, C.byref(st)))
+    check(lib.ite_evolve_batch_grouped(device, n_slots, mem_budget, int(grouping),
+                                       float(window_ms), n, arr, res, C.byref(st)))
     return [r.as_dict() for r in res], st.as_dict()

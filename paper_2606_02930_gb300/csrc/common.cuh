@@ -224,6 +224,45 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
                         const double* anorm2, double skip_rel, int keep_rank,
                         unsigned int* dev_state, int* stamps, double* wts, double* nref,
                         cudaStream_t st);
+// Several jacobi_rows problems in one cooperative launch (the truncated
+// splits of concurrent evolutions).  Each item is one matrix with its own
+// dev_state, stamps, wts and nref as jacobi_rows takes them, cleared
+// beforehand by jacobi_prepare on the item's stream; every item ends exactly as
+// jacobi_rows would leave it.  Items need at least 3 rows; n <= kJacobiGroupMax.
+// group_state (24 device words) holds the group's grid barrier.
+struct JacobiItem {
+  cplx* A;
+  const double* anorm2;
+  unsigned int* st;
+  int* stamps;
+  double* wts;
+  double* nref;
+  double tol, skip_rel;
+  int rows, len, max_sweeps, keep_rank;
+};
+constexpr int kJacobiGroupMax = 32;
+struct JacobiGroup {
+  int n;
+  JacobiItem it[kJacobiGroupMax];
+};
+cudaError_t jacobi_prepare(int rows, unsigned int* dev_state, int* stamps, cudaStream_t st);
+cudaError_t jacobi_rows_grouped(const JacobiItem* items, int n, unsigned int* group_state,
+                                cudaStream_t st);
+// blocks the grouped kernel can hold co-resident on the current device, and
+// the blocks jacobi_rows_grouped launches for these items
+cudaError_t jacobi_grouped_capacity(int* blocks);
+int jacobi_grouped_blocks(const JacobiItem* items, int n);
+// Grouped Jacobi launches across concurrent evolutions (group.cu): members
+// post their split's Jacobi with group_jacobi; posts collected within the
+// window, or once `expected` members have posted, run as one launch.
+struct SplitGroup;
+cudaError_t group_create(int device, double window_ms, SplitGroup** out);
+void group_destroy(SplitGroup* g);
+void group_set_expected(SplitGroup* g, int expected);
+void group_set_policy(SplitGroup* g, int mode, double window_ms);
+void group_stats(SplitGroup* g, long long* launches, long long* items);
+cudaError_t group_jacobi(SplitGroup* g, const JacobiItem& item, cudaEvent_t ready, cudaEvent_t done,
+                         unsigned int* gstate, cudaStream_t st);
 // one cooperative launch of `blocks` blocks meeting at the grid barrier, the
 // first `absent` of them never arriving; word 4 of dev_state ends nonzero
 // when the wait ran out (blocks must be co-resident: at most the SM count)

@@ -119,6 +119,11 @@ struct ite_ctx_s {
   // (the Gauss-Legendre step's shifted solves)
   std::vector<ite_ctx> children;
   std::vector<cudaStream_t> child_streams;
+  // grouped Jacobi launches with other contexts (served runtime), and the
+  // events that order this context's stream around them
+  SplitGroup* group = nullptr;
+  cudaEvent_t group_ready = nullptr, group_done = nullptr;
+  unsigned int* group_state = nullptr;     // 24 words: barrier of a grouped launch it leads
 };
 
 struct ite_mpo_s {
@@ -485,8 +490,18 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   // 3. one-sided Jacobi on the k rows (length p) of R
   {
     Scope jacobi_scope(ctx, P_JACOBI);
-    CK(jacobi_rows(R, k, p, kJacobiSweeps, std::max(1e-15, p * kEps), anorm2, skip_weight(cutoff),
-                   chi_max, jstate, stamps, wts, nref, ctx->stream));
+    const double tol = std::max(1e-15, p * kEps);
+    if (ctx->group && k >= 3) {
+      // the same Jacobi, launched together with other contexts' splits
+      CK(jacobi_prepare(k, jstate, stamps, ctx->stream));
+      const JacobiItem item{R, anorm2, jstate, stamps, wts, nref, tol, skip_weight(cutoff),
+                            k, p, kJacobiSweeps, chi_max};
+      CK(group_jacobi(ctx->group, item, ctx->group_ready, ctx->group_done, ctx->group_state,
+                      ctx->stream));
+    } else {
+      CK(jacobi_rows(R, k, p, kJacobiSweeps, tol, anorm2, skip_weight(cutoff), chi_max, jstate,
+                     stamps, wts, nref, ctx->stream));
+    }
   }
   // 4. singular values, order and rank
   int* rank_dev = reinterpret_cast<int*>(ctx->dscal + 6);
@@ -1278,6 +1293,9 @@ void ite_ctx_destroy(ite_ctx ctx) {
   dev_free(ctx, ctx->dcounter, 64 * sizeof(int));
   if (ctx->hr) cudaFreeHost(ctx->hr);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  if (ctx->group_state) dev_free(ctx, ctx->group_state, 24 * sizeof(unsigned int));
+  if (ctx->group_ready) cudaEventDestroy(ctx->group_ready);
+  if (ctx->group_done) cudaEventDestroy(ctx->group_done);
   delete ctx;
 }
 
@@ -2306,6 +2324,26 @@ ite_status ite_k_heff_lp_apply(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int c
   return kernel_finish(ctx);
 }
 
+ite_status ite_k_heff_lp_apply_n(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket,
+                                 int chr_ket, int chr_bra, const double* X, double* Y,
+                                 const double alpha[2], const double* Z, const double gamma[2],
+                                 int reps) {
+  if (!ctx || !H || !X || !Y || !alpha || i < 0 || i + 1 >= H->N || chl_bra < 1 || chl_ket < 1 ||
+      chr_ket < 1 || chr_bra < 1 || reps < 1 || Y == X || Y == Z)
+    return ITE_EINVAL;
+  CK(cudaMemsetAsync(reinterpret_cast<int*>(ctx->dcounter) + 10, 0, sizeof(int), ctx->stream));
+  struct LevelGuard {
+    ite_ctx c;
+    ~LevelGuard() { c->lp_level = -1; }
+  } guard{ctx};
+  ctx->lp_level = ctx->lp_prep.level;
+  const cplx g = gamma ? C(gamma[0], gamma[1]) : C(0);
+  for (int r = 0; r < reps; ++r)
+    CS(heff_lp(ctx, H, i, chl_bra, chl_ket, chr_ket, chr_bra, (const cplx*)X, (cplx*)Y,
+               C(alpha[0], alpha[1]), (const cplx*)Z, g));
+  return kernel_finish(ctx);
+}
+
 ite_status ite_k_heff(ite_ctx ctx, ite_mpo H, int i, int chl_bra, int chl_ket, int chr_ket,
                       int chr_bra, const double* L, const double* R, const double* X, double* Y,
                       const double alpha[2], const double* Z, const double gamma[2]) {
@@ -2505,6 +2543,20 @@ bool internal_bond_info(ite_mpo H, int i, int* d, int* D0, int* D1, int* D2, con
 }
 
 ite_status internal_fail(ite_ctx ctx, ite_status st, const char* msg) { return fail(ctx, st, msg); }
+
+// Attaches ctx to a group of grouped Jacobi launches (nullptr detaches).
+ite_status internal_set_group(ite_ctx ctx, SplitGroup* g) {
+  if (g && !ctx->group_ready) {
+    CK(cudaEventCreateWithFlags(&ctx->group_ready, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->group_done, cudaEventDisableTiming));
+  }
+  if (g && !ctx->group_state) {
+    ctx->group_state = static_cast<unsigned int*>(dev_alloc(ctx, 24 * sizeof(unsigned int)));
+    if (!ctx->group_state) return fail(ctx, ITE_ENOMEM, "group state allocation failed");
+  }
+  ctx->group = g;
+  return ITE_OK;
+}
 
 // Frees the context's reusable workspaces (they grow again on demand), so
 // that a long-lived context holds only its small fixed state between jobs.

@@ -131,13 +131,15 @@ __global__ void k_lp_xt(const cplx* __restrict__ X, int rows, long long n_cols,
 // column indices) beside them; then thread (pair p, group g) forms the
 // outputs k = g, g + groups, ... of the two values b' = b0 + 2p, b0 + 2p + 1
 // (paired loads and stores halve the instructions per output).
-constexpr int MIX_B = 64;           // values of b' per block
-constexpr int MIX_P = MIX_B / 2;    // threads per group
-template <bool TF32>
+// MIX_B (64, 128 or 256 values of b' per block) is chosen per shape so that a
+// block stages about 24 KB: enough bytes in flight per SM to stream the
+// L2-resident intermediates at a high rate.
+template <bool TF32, int MIX_B>
 __global__ void __launch_bounds__(256)
 k_lp_mix(MixPlan pl, const __nv_bfloat16* __restrict__ T1, int chlB, int chrK, int d, int D0,
          int D2, long long N1, typename Lp<TF32>::T* __restrict__ T2, long long ld2) {
   typedef typename Lp<TF32>::T T;
+  constexpr int MIX_P = MIX_B / 2;    // threads per group
   extern __shared__ uint4 smem_u4[];
   const int dd = d * d;
   const int ncol = D0 * dd;                              // (w, s t)
@@ -448,25 +450,35 @@ cudaError_t heff_lp_apply(const void* ops, const MixPlan& plan2, int d, int D0, 
   }
   // 2. mix into the K-major complex-interleaved T2
   {
-    dim3 grid((unsigned)((chrK + MIX_B - 1) / MIX_B), (unsigned)chlB);
-    const size_t smem = (size_t)2 * D0 * d * d * MIX_B * 2 +
+    const int stage_row = 4 * D0 * d * d;        // bytes staged per value of b'
+    const int mixb = stage_row * 256 <= 24 * 1024 ? 256 : (stage_row * 128 <= 24 * 1024 ? 128 : 64);
+    dim3 grid((unsigned)((chrK + mixb - 1) / mixb), (unsigned)chlB);
+    const size_t smem = (size_t)stage_row * mixb +
                         (size_t)plan2.nnz * (sizeof(float2) + sizeof(int)) +
                         (size_t)(plan2.nrows + 1) * sizeof(int) + 16 +
                         (size_t)D0 * d * d * sizeof(long long);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const void* fn = tf32 ? (mixb == 256 ? (const void*)k_lp_mix<true, 256>
+                             : mixb == 128 ? (const void*)k_lp_mix<true, 128> : (const void*)k_lp_mix<true, 64>)
+                          : (mixb == 256 ? (const void*)k_lp_mix<false, 256>
+                             : mixb == 128 ? (const void*)k_lp_mix<false, 128> : (const void*)k_lp_mix<false, 64>);
     if (smem > 48 * 1024) {
-      cudaError_t ea = tf32 ? cudaFuncSetAttribute(k_lp_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(k_lp_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (ea != cudaSuccess) return ea;
     }
-    // thread groups per pair of b' values (two or more output rows per thread),
-    // at most 8 (256 threads)
+    // thread groups of mixb / 2 threads, each group taking every groups-th
+    // output row; at most 256 threads, and no more groups than row pairs
+    const int mixp = mixb / 2;
     int groups = plan2.nrows / 2;
-    groups = groups < 1 ? 1 : (groups > 8 ? 8 : groups);
+    groups = groups < 1 ? 1 : (groups > 256 / mixp ? 256 / mixp : groups);
     count_launches(1);
-    if (tf32) k_lp_mix<true><<<grid, MIX_P * groups, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (float*)T2, ld2);
-    else k_lp_mix<false><<<grid, MIX_P * groups, smem, st>>>(plan2, T1, chlB, chrK, d, D0, D2, N1, (__nv_bfloat16*)T2, ld2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    void* T2p = T2;
+    MixPlan pl = plan2;
+    int a_chlB = chlB, a_chrK = chrK, a_d = d, a_D0 = D0, a_D2 = D2;
+    long long a_N1 = N1, a_ld2 = ld2;
+    const __nv_bfloat16* T1c = T1;
+    void* args[] = {&pl, &T1c, &a_chlB, &a_chrK, &a_d, &a_D0, &a_D2, &a_N1, &T2p, &a_ld2};
+    if ((e = cudaLaunchKernel(fn, grid, dim3(mixp * groups), args, smem, st)) != cudaSuccess) return e;
   }
   // 3. Y32[sp] = T2 Remb^T: M3 x (2 chrB), K = 2 D2 chrK, split over K
   int splits = 1;

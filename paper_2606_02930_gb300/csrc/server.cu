@@ -17,16 +17,21 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
 #include "ite.h"
 #include "ite_server.h"
 
 namespace ite {
 void internal_release_workspace(ite_ctx ctx);
+ite_status internal_set_group(ite_ctx ctx, SplitGroup* g);
 }
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+// longest a posted Jacobi waits for the other running jobs' posts while the
+// device is busy with grouped launches
+constexpr double kDefaultGroupWindowMs = 20.0;
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
@@ -150,6 +155,9 @@ struct ite_server_s {
   std::vector<double> latencies;
   double tau_steps = 0.0;
   ite_status setup_status = ITE_OK;
+  // grouped Jacobi launches across the running jobs (on unless switched off)
+  ite::SplitGroup* group = nullptr;
+  bool grouping = true;
 
   void worker_main();
   void run_job(ite_ctx ctx, cudaStream_t st, Job& job);
@@ -248,6 +256,8 @@ void ite_server_s::worker_main() {
       ++running;
       peak_running = std::max(peak_running, running);
       job->t_start = Clock::now();
+      if (group) ite::group_set_expected(group, running);
+      if (ctx) ite::internal_set_group(ctx, grouping ? group : nullptr);
     }
     if (ctx) {
       run_job(ctx, st, *job);
@@ -265,6 +275,7 @@ void ite_server_s::worker_main() {
       job->done = true;
       reserved -= job->bytes;
       --running;
+      if (group) ite::group_set_expected(group, running);
       if (r.status == ITE_OK) {
         ++completed;
         latencies.push_back(r.latency_ms);
@@ -304,6 +315,10 @@ ite_status ite_server_create(int device, int n_slots, size_t mem_budget, ite_ser
   ite_server s = new ite_server_s;
   s->device = device;
   s->budget = mem_budget;
+  if (ite::group_create(device, kDefaultGroupWindowMs, &s->group) != cudaSuccess) {
+    delete s;
+    return ITE_ECUDA;
+  }
   for (int w = 0; w < n_slots; ++w) s->workers.emplace_back([s] { s->worker_main(); });
   *out = s;
   return ITE_OK;
@@ -400,6 +415,15 @@ ite_status ite_server_stats_get(ite_server s, ite_server_stats* out) {
   out->wall_ms = s->any_submitted && s->completed + s->failed > 0 ? ms_between(s->t_first, s->t_last) : 0.0;
   out->tau_steps = s->tau_steps;
   out->tau_steps_per_s = out->wall_ms > 0.0 ? s->tau_steps / (out->wall_ms * 1e-3) : 0.0;
+  if (s->group) ite::group_stats(s->group, &out->group_launches, &out->group_items);
+  return ITE_OK;
+}
+
+ite_status ite_server_set_grouping(ite_server s, int mode, double window_ms) {
+  if (!s || mode < 0 || mode > 2 || !(window_ms >= 0.0) || window_ms > 1e4) return ITE_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->grouping = mode != 0;
+  ite::group_set_policy(s->group, mode == 0 ? 1 : mode, window_ms);
   return ITE_OK;
 }
 
@@ -412,17 +436,30 @@ void ite_server_destroy(ite_server s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  ite::group_destroy(s->group);
   delete s;
 }
 
 ite_status ite_evolve_batch(int device, int n_slots, size_t mem_budget, int n, const ite_job* jobs,
                             ite_job_result* out, ite_server_stats* stats) {
+  return ite_evolve_batch_grouped(device, n_slots, mem_budget, 1, kDefaultGroupWindowMs, n, jobs,
+                                  out, stats);
+}
+
+ite_status ite_evolve_batch_grouped(int device, int n_slots, size_t mem_budget, int grouping,
+                                    double window_ms, int n, const ite_job* jobs,
+                                    ite_job_result* out, ite_server_stats* stats) {
   if (n < 0 || (n > 0 && (!jobs || !out))) return ITE_EINVAL;
   for (int i = 0; i < n; ++i)
     if (!job_valid(&jobs[i])) return ITE_EINVAL;
   ite_server s = nullptr;
   ite_status st = ite_server_create(device, n_slots, mem_budget, &s);
   if (st != ITE_OK) return st;
+  st = ite_server_set_grouping(s, grouping, window_ms);
+  if (st != ITE_OK) {
+    ite_server_destroy(s);
+    return st;
+  }
   std::vector<long long> tickets(n, 0);
   for (int i = 0; i < n && st == ITE_OK; ++i) st = ite_server_submit(s, &jobs[i], &tickets[i]);
   if (st == ITE_OK) {

@@ -443,15 +443,20 @@ __device__ __forceinline__ void pair_norms_out(int u, int v, int flags, double a
 }
 
 // One Jacobi rotation on rows u < v (length len <= TPP EPL) of A by the team,
-// the rows held in registers.
+// the rows held in registers.  With last >= 0 the pair is skipped (*skipped
+// set, nothing written) when neither row has been rotated since global round
+// `last` (stamps); the stamps are loaded together with the rows, so a round
+// costs one L2 round trip before the arithmetic instead of two.
 template <int EPL>
 __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double skip, double* wts,
-                             double* nref) {
+                             double* nref, const int* stamps, int last, bool* skipped) {
   const int tid = threadIdx.x;
   cplx* au = A + (long long)u * len;
   cplx* av = A + (long long)v * len;
   cplx x[EPL], y[EPL];
-  // rows and their norms come from other SMs' rotations: read through L2
+  // rows, norms and stamps come from other SMs' rotations: read through L2, so
+  // that every thread sees the same stamps and the block takes one branch
+  const int stu = last >= 0 ? __ldcg(stamps + u) : 0, stv = last >= 0 ? __ldcg(stamps + v) : 0;
   const double al = __ldcg(wts + u), be = __ldcg(wts + v);
   const double ru = __ldcg(nref + u), rv = __ldcg(nref + v);
 #pragma unroll
@@ -459,6 +464,14 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
     const int e = tid + TPP * i;
     x[i] = e < len ? __ldcg(au + e) : cmake(0.0, 0.0);
     y[i] = e < len ? __ldcg(av + e) : cmake(0.0, 0.0);
+  }
+  PairOut out;
+  if (last >= 0 && stu <= last && stv <= last) {
+    *skipped = true;
+    out.rotated = out.counted = false;
+    out.al = al;
+    out.be = be;
+    return out;
   }
   // independent partial sums keep the dependent FP64 chains short
   constexpr int NP = EPL < 4 ? EPL : 4;
@@ -477,7 +490,6 @@ __device__ PairOut pair_regs(cplx* A, int len, int u, int v, double tol, double 
     gr += pr[a];
     gi += pi[a];
   }
-  PairOut out;
   double c, sr, si, al2, be2;
   int flags;
   pair_decide(gr, gi, al, be, ru, rv, tol, skip, c, sr, si, flags, al2, be2);
@@ -547,13 +559,25 @@ __device__ PairOut pair_stream(cplx* A, int len, int u, int v, double tol, doubl
   return out;
 }
 
+// The pair (u, v) of A; with last >= 0 it is skipped (*skipped set) when
+// neither row has been rotated since global round `last`.
 __device__ __forceinline__ PairOut jacobi_pair(cplx* A, int len, int u, int v, double tol,
-                                               double skip, double* wts, double* nref) {
+                                               double skip, double* wts, double* nref,
+                                               const int* stamps, int last, bool* skipped) {
   if (u > v) { const int t = u; u = v; v = t; }
-  if (len <= 2 * TPP) return pair_regs<2>(A, len, u, v, tol, skip, wts, nref);
-  if (len <= 4 * TPP) return pair_regs<4>(A, len, u, v, tol, skip, wts, nref);
-  if (len <= 8 * TPP) return pair_regs<8>(A, len, u, v, tol, skip, wts, nref);
-  if (len <= 16 * TPP) return pair_regs<16>(A, len, u, v, tol, skip, wts, nref);
+  *skipped = false;
+  if (len <= 2 * TPP) return pair_regs<2>(A, len, u, v, tol, skip, wts, nref, stamps, last, skipped);
+  if (len <= 4 * TPP) return pair_regs<4>(A, len, u, v, tol, skip, wts, nref, stamps, last, skipped);
+  if (len <= 8 * TPP) return pair_regs<8>(A, len, u, v, tol, skip, wts, nref, stamps, last, skipped);
+  if (len <= 16 * TPP)
+    return pair_regs<16>(A, len, u, v, tol, skip, wts, nref, stamps, last, skipped);
+  if (last >= 0 && __ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) {
+    *skipped = true;
+    PairOut out;
+    out.rotated = out.counted = false;
+    out.al = out.be = 0.0;
+    return out;
+  }
   return pair_stream(A, len, u, v, tol, skip, wts, nref);
 }
 
@@ -579,7 +603,8 @@ k_jacobi_round(cplx* A, int len, double tol, const double* anorm2, double skip_r
   const double a2 = anorm2 ? *anorm2 : 0.0;
   team_row_norms(A, len, 0, 2, 1, wts, nref);
   __syncthreads();
-  const PairOut o = jacobi_pair(A, len, 0, 1, tol, skip_rel * a2, wts, nref);
+  bool skipped;
+  const PairOut o = jacobi_pair(A, len, 0, 1, tol, skip_rel * a2, wts, nref, nullptr, -1, &skipped);
   if (threadIdx.x == 0) {
     if (o.counted) atomicAdd(st + S_CNT, 1u);
     atomicAdd(st + S_EXAMINED, 1u);
@@ -638,13 +663,12 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
         int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
         if (u >= rows || v >= rows) continue;
         if (u > v) { const int t = u; u = v; v = t; }
-        if (sw > 0) {
-          // read through L2 so that every thread sees the same stamps and the
-          // block takes one branch
-          const int last = g - (pp - 1);
-          if (__ldcg(stamps + u) <= last && __ldcg(stamps + v) <= last) continue;
-        }
-        const PairOut o = jacobi_pair(A, len, u, v, tol, skip, wts, nref);
+        // from the second sweep on, a pair neither of whose rows has been
+        // rotated since it was last examined is skipped
+        bool skipped;
+        const PairOut o = jacobi_pair(A, len, u, v, tol, skip, wts, nref, stamps,
+                                      sw > 0 ? g - (pp - 1) : -1, &skipped);
+        if (skipped) continue;
         ++examined;
         if (o.rotated) {
           ++rotations_done;
@@ -679,6 +703,129 @@ k_jacobi_persistent(cplx* A, int rows, int len, int pp, double tol, const double
   if (tid == 0) {
     atomicAdd(st + S_EXAMINED, examined);
     atomicAdd(st + S_ROTATED, rotations_done);
+  }
+}
+
+// The same Jacobi for several independent matrices in one cooperative launch
+// (the splits of concurrent evolutions).  Every matrix runs its own
+// round-robin tournament from global round 0, one round per global round, so
+// that its round G is round G % (pp - 1) of sweep G / (pp - 1); the pairs of
+// all matrices still sweeping are spread over the blocks, and one grid
+// barrier follows every global round.  Each matrix's pairs, stamps, counters
+// and stopping rule are those of k_jacobi_persistent, and a pair's arithmetic
+// does not depend on the block that takes it, so each matrix ends bit for bit
+// as it would alone.  Matrices need pp >= 4 (at least 3 rows).  gst holds the
+// group's barrier (words 0, 1) and error flag (word 4); on a failed wait every
+// matrix's error word is set.
+__global__ void __launch_bounds__(TPP)
+k_jacobi_grouped(const __grid_constant__ JacobiGroup g, unsigned int* gst) {
+  const unsigned int nb = gridDim.x;
+  const int tid = threadIdx.x;
+  __shared__ unsigned int s_ex[kJacobiGroupMax], s_rot[kJacobiGroupMax];
+  __shared__ int s_done[kJacobiGroupMax], s_act[kJacobiGroupMax];
+  __shared__ double s_skip[kJacobiGroupMax];
+  const int n = g.n;
+  for (int j = tid; j < n; j += TPP) {
+    s_ex[j] = s_rot[j] = 0u;
+    s_done[j] = 0;
+    s_skip[j] = g.it[j].skip_rel * (g.it[j].anorm2 ? *g.it[j].anorm2 : 0.0);
+  }
+  __syncthreads();
+  // the tracked squared norms start from the rows themselves
+  int total_rows = 0;
+  for (int j = 0; j < n; ++j) total_rows += g.it[j].rows;
+  for (int f = blockIdx.x; f < total_rows; f += (int)nb) {
+    int j = 0, r = f;
+    while (r >= g.it[j].rows) r -= g.it[j++].rows;
+    team_row_norms(g.it[j].A, g.it[j].len, r, r + 1, 1, g.it[j].wts, g.it[j].nref);
+  }
+  bool ok = grid_barrier(gst, nb);
+  for (int G = 0; ok; ++G) {
+    // matrices still sweeping (every block decides alike)
+    int total = 0;
+    for (int j = 0; j < n; ++j) {
+      const int pp = g.it[j].rows + (g.it[j].rows & 1);
+      const bool act = !s_done[j] && G / (pp - 1) < g.it[j].max_sweeps;
+      if (tid == 0) s_act[j] = act;
+      if (act) total += pp / 2;
+    }
+    if (total == 0) break;
+    if (blockIdx.x == 0 && tid == 0) {
+      for (int j = 0; j < n; ++j) {
+        const int pp = g.it[j].rows + (g.it[j].rows & 1);
+        const int sw = G / (pp - 1);
+        if (s_act[j] && G % (pp - 1) == 1) {
+          reinterpret_cast<int*>(g.it[j].st + S_CNT)[(sw + 1) & 1] = 0;
+          reinterpret_cast<unsigned long long*>(g.it[j].st + S_MAXW)[(sw + 1) & 1] = 0ull;
+        }
+      }
+    }
+    __syncthreads();
+    for (int f = blockIdx.x; f < total; f += (int)nb) {
+      int j = 0, k = f;
+      for (;; ++j) {
+        if (!s_act[j]) continue;
+        const int half = (g.it[j].rows + (g.it[j].rows & 1)) / 2;
+        if (k < half) break;
+        k -= half;
+      }
+      const JacobiItem& it = g.it[j];
+      const int rows = it.rows, pp = rows + (rows & 1);
+      const int sw = G / (pp - 1), r = G % (pp - 1);
+      int u = player(k, r, pp), v = player(pp - 1 - k, r, pp);
+      if (u >= rows || v >= rows) continue;
+      if (u > v) { const int t = u; u = v; v = t; }
+      bool skipped;
+      const PairOut o = jacobi_pair(it.A, it.len, u, v, it.tol, s_skip[j], it.wts, it.nref,
+                                    it.stamps, sw > 0 ? G - (pp - 1) : -1, &skipped);
+      if (skipped) continue;
+      if (tid == 0) {
+        ++s_ex[j];
+        if (o.rotated) {
+          ++s_rot[j];
+          it.stamps[u] = G;
+          it.stamps[v] = G;
+          if (o.counted) {
+            atomicAdd(reinterpret_cast<int*>(it.st + S_CNT) + (sw & 1), 1);
+            atomicMax(reinterpret_cast<unsigned long long*>(it.st + S_MAXW) + (sw & 1),
+                      (unsigned long long)__double_as_longlong(fmax(o.al, o.be)));
+          }
+        }
+      }
+    }
+    ok = grid_barrier(gst, nb);
+    if (!ok) break;
+    // the matrices whose sweep ended with this round decide whether to go on
+    for (int j = 0; j < n; ++j) {
+      if (!s_act[j]) continue;
+      const JacobiItem& it = g.it[j];
+      const int rows = it.rows, pp = rows + (rows & 1);
+      if (G % (pp - 1) != pp - 2) continue;
+      const int sw = G / (pp - 1);
+      if (blockIdx.x == 0 && tid == 0) it.st[S_SWEEPS] = (unsigned int)(sw + 1);
+      bool stop = *((volatile int*)(reinterpret_cast<int*>(it.st + S_CNT) + (sw & 1))) == 0;
+      if (!stop && it.keep_rank < rows) {
+        const double thr = __longlong_as_double((long long)__ldcg(
+                               reinterpret_cast<unsigned long long*>(it.st + S_MAXW) + (sw & 1))) /
+                           kKeepMargin;
+        int heavy = 0;
+        for (int i0 = 0; i0 < rows; i0 += blockDim.x) {
+          const int i = i0 + tid;
+          heavy += __syncthreads_count(i < rows && __ldcg(it.wts + i) > thr);
+        }
+        stop = heavy >= it.keep_rank;
+      }
+      __syncthreads();
+      if (stop && tid == 0) s_done[j] = 1;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const bool failed = *((volatile unsigned int*)(gst + S_ERR)) != 0u;
+  for (int j = tid; j < n; j += TPP) {
+    atomicAdd(g.it[j].st + S_EXAMINED, s_ex[j]);
+    atomicAdd(g.it[j].st + S_ROTATED, s_rot[j]);
+    if (failed) atomicExch(g.it[j].st + S_ERR, 1u);
   }
 }
 
@@ -821,7 +968,7 @@ struct Coresident {
     return b > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
   }
 };
-Coresident g_lq_blocks, g_jacobi_blocks, g_formq_blocks;
+Coresident g_lq_blocks, g_jacobi_blocks, g_formq_blocks, g_jgroup_blocks;
 
 // The grid barrier of the cooperative kernels with `absent` blocks that never
 // arrive: the others wait until the barrier's iteration limit, set the error
@@ -933,6 +1080,63 @@ cudaError_t jacobi_rows(cplx* A, int rows, int len, int max_sweeps, double tol,
   count_launches(1);
   return cudaLaunchCooperativeKernel((void*)k_jacobi_persistent, dim3(nblk), dim3(TPP), args, 0,
                                      st);
+}
+
+cudaError_t jacobi_prepare(int rows, unsigned int* dev_state, int* stamps, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(dev_state, 0, S_WORDS * sizeof(unsigned int), st);
+  if (err != cudaSuccess || rows < 2) return err;
+  return cudaMemsetAsync(stamps, 0, sizeof(int) * rows, st);
+}
+
+namespace {
+// co-resident blocks of k_jacobi_grouped on the current device (cached)
+int g_jgroup_capacity[64] = {0};
+int jgroup_cap_cached() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return 0;
+  return g_jgroup_capacity[d & 63];
+}
+}  // namespace
+
+cudaError_t jacobi_grouped_capacity(int* blocks) {
+  int max_blocks = 0;
+  cudaError_t err = g_jgroup_blocks.get((const void*)k_jacobi_grouped, TPP, &max_blocks);
+  if (err != cudaSuccess) return err;
+  int d = 0;
+  err = cudaGetDevice(&d);
+  if (err != cudaSuccess) return err;
+  g_jgroup_capacity[d & 63] = max_blocks;
+  *blocks = max_blocks;
+  return cudaSuccess;
+}
+
+// one block per pair of a round, up to every block the SMs can hold at once
+int jacobi_grouped_blocks(const JacobiItem* items, int n) {
+  int total = 0;
+  for (int j = 0; j < n; ++j) total += (items[j].rows + (items[j].rows & 1)) / 2;
+  int cap = jgroup_cap_cached();
+  if (cap < 1) cap = 152;
+  return total < cap ? total : cap;
+}
+
+cudaError_t jacobi_rows_grouped(const JacobiItem* items, int n, unsigned int* group_state,
+                                cudaStream_t st) {
+  if (n < 1 || n > kJacobiGroupMax) return cudaErrorInvalidValue;
+  JacobiGroup g;
+  g.n = n;
+  for (int j = 0; j < n; ++j) {
+    if (items[j].rows < 3) return cudaErrorInvalidValue;
+    g.it[j] = items[j];
+  }
+  cudaError_t err = cudaMemsetAsync(group_state, 0, S_WORDS * sizeof(unsigned int), st);
+  if (err != cudaSuccess) return err;
+  int cap = 0;
+  err = jacobi_grouped_capacity(&cap);
+  if (err != cudaSuccess) return err;
+  const int nblk = jacobi_grouped_blocks(items, n);
+  void* args[] = {&g, &group_state};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel((void*)k_jacobi_grouped, dim3(nblk), dim3(TPP), args, 0, st);
 }
 
 cudaError_t svd_rank(const cplx* A, int p, int q, double* sigma, int* perm, double* sorted_sigma,

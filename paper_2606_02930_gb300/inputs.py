@@ -106,3 +106,31 @@ WORKLOADS = {
                           chi_max=512, cutoff=1e-14, tau0=1e-2, tau_max=1e4, K=50,
                           schemes=("tr",), seed=3000),
 }
+
+
+def serve_stream(n, rate=20.0, baths=(49, 99, 199), chis=(128, 256, 512, 1024), seed=5000):
+    """Requests of the served impurity stream, drawn in this order from one
+    seeded generator: Poisson inter-arrival gaps (mean 1/rate s), U ~ U[0.05,
+    0.6], Gamma ~ U[0.02, 0.1], bath sizes from `baths`, bond caps from `chis`,
+    tau_max from {1e2, 1e3, 1e4}.  Each request evolves on the geometric grid
+    1e-2 -> tau_max in K = ceil(10 log10(tau_max / 1e-2)) steps from a random
+    product state (seed + i), with eps_d = -U/2 and the flat-band bath.  Returns
+    a list of dicts (model parameters and layout only)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    Us = rng.uniform(0.05, 0.6, n)
+    Gs = rng.uniform(0.02, 0.1, n)
+    nbs = rng.choice(list(baths), n)
+    cxs = rng.choice(list(chis), n)
+    tms = rng.choice([1e2, 1e3, 1e4], n)
+    out = []
+    for i in range(n):
+        nb = int(nbs[i])
+        eps, V = flat_band_bath(nb, gamma=float(Gs[i]))
+        out.append({"gap_s": float(gaps[i]), "U": float(Us[i]), "eps_d": -0.5 * float(Us[i]),
+                    "Gamma": float(Gs[i]), "n_bath": nb, "chi_max": int(cxs[i]),
+                    "tau_max": float(tms[i]),
+                    "n_steps": int(np.ceil(10 * np.log10(tms[i] / 1e-2))),
+                    "eps": eps, "V": V,
+                    "site_vecs": random_product_state(nb + 1, 4, seed + i)})
+    return out

@@ -94,6 +94,10 @@ def test_lp_heff_matches_oracle(api, ctx, precision):
             got = to_host(Y)
             err = np.linalg.norm(got - want) / np.linalg.norm(want - gamma * Z)
             assert err <= 8 * U[precision], (dims, err)
+        # back-to-back matvecs leave Y as one matvec does
+        Y2 = torch.full(Z.shape, float("nan"), dtype=torch.complex128, device="cuda")
+        api.k_heff_lp_apply_n(ctx, H, i, to_dev(X), Y2, alpha, to_dev(Z), gamma, reps=3)
+        assert np.array_equal(to_host(Y2), got)
     # an apply for another shape than the prepared one is refused
     H = api.mpo_create(ctx, ompo.heisenberg_mpo(12))
     Y = torch.zeros((8, 2, 2, 8), dtype=torch.complex128, device="cuda")

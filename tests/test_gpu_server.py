@@ -151,3 +151,34 @@ def test_metts_and_panel_jobs_in_the_mix_equal_calls_alone(api):
     t_mix, t_alone = evo.tensors(), psi.tensors()
     ov = omps.overlap(t_alone, t_mix)
     assert 1.0 - abs(ov) / (omps.norm(t_alone) * omps.norm(t_mix)) <= 1e-12
+
+
+def _energies_and_states(api, specs, n_slots, grouping, window_ms):
+    jobs = [api.Job(want_state=True, **s) for s in specs]
+    results, st = api.evolve_batch(jobs, n_slots=n_slots, grouping=grouping, window_ms=window_ms)
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert all(r["status"] == 0 for r in results)
+    return jobs, results, st
+
+
+@pytest.mark.parametrize("which", ["same_shapes", "mixed_shapes"])
+def test_grouped_jacobi_launches_change_no_result(api, which):
+    # the splits of the running jobs go to the device as grouped launches
+    # (k_jacobi_grouped); every job ends bit for bit as with grouping off, and
+    # as the same evolution alone
+    if which == "same_shapes":
+        specs = [dict(model="heisenberg", n=12, site_vecs=inputs.random_product_state(12, 2, 90 + k),
+                      chi_max=32, cutoff=1e-10, tau0=1e-2, tau_max=1e1, n_steps=3, scheme="be",
+                      opts=api.solver_opts(precision="fp64"))
+                 for k in range(4)]
+    else:
+        specs = _jobs(api)
+    # mode 2 (gather) makes the grouping certain: every running job's post
+    g_jobs, g_res, g_st = _energies_and_states(api, specs, len(specs), 2, 200.0)
+    u_jobs, _, u_st = _energies_and_states(api, specs, len(specs), 0, 20.0)
+    assert u_st["group_launches"] == 0
+    assert g_st["group_items"] > g_st["group_launches"] > 0     # launches carried several splits
+    for gj, uj in zip(g_jobs, u_jobs):
+        assert np.array_equal(gj.energies, uj.energies)
+        assert all(np.array_equal(a, b) for a, b in zip(gj.tensors(), uj.tensors()))
+    _check_against_alone(api, g_jobs, g_res, specs)
