@@ -97,6 +97,7 @@ def parse():
     ap.add_argument("--batch-chis", default="32,64,128,256", help="batch: bond caps drawn from")
     ap.add_argument("--anderson-start", choices=["product", "saturated"], default="product",
                     help="anderson: start from a product state or at the saturated chi")
+    ap.add_argument("--anderson-bath", type=int, default=99, help="anderson: bath sites")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-baths", default="9,19,29", help="serve: bath sizes drawn from")
     ap.add_argument("--serve-chis", default="16,32,64", help="serve: bond caps drawn from")
@@ -860,7 +861,7 @@ def run_anderson(args):
     import torch
     from paper_2606_02930_gb300 import api, inputs
     torch.cuda.init()
-    n_bath, chi, cutoff = 99, 512, 1e-14
+    n_bath, chi, cutoff = args.anderson_bath, 512, 1e-14
     eps, V = inputs.flat_band_bath(n_bath)
     ctx = api.ctx_create(0)
     H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
@@ -897,8 +898,8 @@ def run_anderson(args):
                                        if kk != "step" and v["ms"] > 0},
                       "svd_sweeps_mean": svd["sweeps_mean"]})
     out = {"workload": "anderson", "metric": "tau-steps/s of the first steps, stage shares",
-           "config": {"model": "Anderson impurity + 99 bath sites (N=100, d=4, D=6), flat band "
-                               "D=1, Gamma=0.05, U=0.3, eps_d=-U/2",
+           "config": {"model": (f"Anderson impurity + {n_bath} bath sites (N={n_bath + 1}, d=4, "
+                                f"D=6), flat band D=1, Gamma=0.05, U=0.3, eps_d=-U/2"),
                       "chi_max": chi, "cutoff": cutoff, "scheme": "backward_euler",
                       "grid": "geometric 1e-2 -> 1e4, 50 steps", "shift": "current energy",
                       "start": ("saturated synthetic state (random isometries, chi = 512 in "
@@ -909,14 +910,17 @@ def run_anderson(args):
            "tau_steps_per_s": len(steps) / (sum(x["ms"] for x in steps) * 1e-3)}
     if not args.no_cpu_baseline:
         t64, eq64 = oracle_anderson_sample(64, 2)
+        t128, eq128 = oracle_anderson_sample(128, 2)
         out["cpu_baseline"] = {
             "kind": "oracle, extrapolated", "cores": os.cpu_count(),
-            "seconds_per_bulk_update_chi64": t64, "bulk_equivalent_updates": eq64,
-            "seconds_per_step_chi64": t64 * eq64,
-            "seconds_per_step_chi512_extrapolated": t64 * eq64 * (512 / 64) ** 3,
+            "seconds_per_bulk_update": {"chi64": t64, "chi128": t128},
+            "bulk_equivalent_updates": {"chi64": eq64, "chi128": eq128},
+            "seconds_per_step": {"chi64": t64 * eq64, "chi128": t128 * eq128},
+            "measured_exponent_64_to_128": float(np.log2(t128 / t64)),
+            "seconds_per_step_chi512_extrapolated": t128 * eq128 * (512 / 128) ** 3,
             "sample": ("the oracle's first two bulk two-site updates of a step at a saturated "
-                       "chi = 64 (random isometries, seed 3000), times the step's "
-                       "bulk-equivalent updates at chi = 64, then the chi^3 law to chi = 512")}
+                       "chi = 64 and chi = 128 (random isometries, seed 3000), times the step's "
+                       "bulk-equivalent updates, then the chi^3 law from chi = 128 to 512")}
     print(json.dumps(out), flush=True)
 
 

@@ -134,14 +134,16 @@ ite_status ite_server_poll(ite_server s, long long ticket, ite_job_result* out);
  * every block the SMs hold at once.  With grouping, a running job posts the
  * Jacobi of each split to the server instead of launching it, and posts go to
  * the device together as one cooperative launch (k_jacobi_grouped).
- *   mode 0: off (each job launches its own Jacobi);
- *   mode 1 (default): continuous batching: a post goes out at once if it fits
+ *   mode 0 (default): off (each job launches its own Jacobi on its stream);
+ *   mode 1: continuous batching: a post goes out at once if it fits
  *     next to the grouped launches still running, else as soon as every
  *     running job outside a running launch has posted, a running launch has
  *     made room, or the first post has waited window_ms (default 20);
  *   mode 2: gather: posts wait for every running job's post, or window_ms.
  * A post waits on the host only, never on the GPU.  Each split ends bit for
- * bit as it would alone, so results do not depend on the mode.  Applies to
+ * bit as it would alone, so results do not depend on the mode.  On GB300 the
+ * Jacobis of concurrent jobs already overlap from their own streams, and the
+ * grouped modes measured 2-4% below that, hence off by default.  Applies to
  * jobs that start after the call.  ITE_EINVAL for a mode outside 0..2 or
  * window_ms outside [0, 1e4]. */
 ite_status ite_server_set_grouping(ite_server s, int mode, double window_ms);
@@ -158,7 +160,7 @@ void ite_server_destroy(ite_server s);
 ite_status ite_evolve_batch(int device, int n_slots, size_t mem_budget, int n, const ite_job* jobs,
                             ite_job_result* out, ite_server_stats* stats);
 /* The same with the grouping mode and window of ite_server_set_grouping
- * (ite_evolve_batch uses mode 1, window 20 ms). */
+ * (ite_evolve_batch uses mode 0). */
 ite_status ite_evolve_batch_grouped(int device, int n_slots, size_t mem_budget, int grouping,
                                     double window_ms, int n, const ite_job* jobs,
                                     ite_job_result* out, ite_server_stats* stats);

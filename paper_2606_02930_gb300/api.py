@@ -629,15 +629,15 @@ class MettsJob:
 class Server:
     """Independent evolutions side by side on one GPU (ite_server.h)."""
 
-    def __init__(self, device=0, n_slots=4, mem_budget=0, grouping=1, window_ms=20.0):
+    def __init__(self, device=0, n_slots=4, mem_budget=0, grouping=0, window_ms=20.0):
         h = C.c_void_p()
         check(lib.ite_server_create(device, n_slots, mem_budget, C.byref(h)))
         self.h = h
         self.jobs = {}
         self.set_grouping(grouping, window_ms)
 
-    def set_grouping(self, mode=1, window_ms=20.0):
-        """mode 0 off, 1 continuous batching, 2 gather (True means 1)."""
+    def set_grouping(self, mode=0, window_ms=20.0):
+        """mode 0 off, 1 continuous batching, 2 gather (ite_server_set_grouping)."""
         check(lib.ite_server_set_grouping(self.h, int(mode), float(window_ms)))
 
     def submit(self, job):
@@ -679,7 +679,7 @@ class Server:
             pass
 
 
-def evolve_batch(jobs, n_slots=4, mem_budget=0, device=0, grouping=1, window_ms=20.0):
+def evolve_batch(jobs, n_slots=4, mem_budget=0, device=0, grouping=0, window_ms=20.0):
     """Run Job objects through a temporary server; returns (results, stats)."""
     n = len(jobs)
     arr = (L.ite_job * n)(*[j.c for j in jobs])

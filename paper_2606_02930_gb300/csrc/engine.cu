@@ -89,7 +89,7 @@ struct ite_ctx_s {
   size_t bytes = 0;
   // workspace
   Buf ws_X, ws_B, ws_X2, ws_V, ws_T1, ws_T2, ws_svdA, ws_svdQ, ws_left, ws_small, ws_env, ws_emu,
-      ws_ovm, ws_lpops, ws_lpscr, ws_R, ws_D;
+      ws_ovm, ws_lpops, ws_lpscr, ws_R, ws_D, ws_R2, ws_Xt;
   // mixed modes: precision of the inner matvecs while a refinement correction
   // runs (-1: none, 0: bf16, 1: tf32), and what the operand buffer holds
   int lp_level = -1;
@@ -966,9 +966,13 @@ ite_status local_solve_mixed(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   const int d = H->d;
   const long long n = (long long)chl * d * d * chr;
   CS(buf_ensure(ctx, ctx->ws_R, (size_t)n * sizeof(cplx)));
+  CS(buf_ensure(ctx, ctx->ws_R2, (size_t)n * sizeof(cplx)));
   CS(buf_ensure(ctx, ctx->ws_D, (size_t)n * sizeof(cplx)));
-  cplx* r = P<cplx>(ctx->ws_R);
+  CS(buf_ensure(ctx, ctx->ws_Xt, (size_t)n * sizeof(cplx)));
+  cplx* r = P<cplx>(ctx->ws_R);        // residual of X
+  cplx* rt = P<cplx>(ctx->ws_R2);      // residual of the trial X + D
   cplx* D = P<cplx>(ctx->ws_D);
+  cplx* Xt = P<cplx>(ctx->ws_Xt);
   struct LevelGuard {
     ite_ctx c;
     ~LevelGuard() { c->lp_level = -1; }
@@ -978,23 +982,31 @@ ite_status local_solve_mixed(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
   int level = precision == ITE_MIXED_TF32 ? 1 : 0;
   if (work < kEmuMinWork || chl < 16 || chr < 16) level = 2;
   int prepared = -1, total = 0;
-  double rho = 0.0, rho_prev = 0.0, bnorm = 0.0;
-  for (int it = 0;; ++it) {
-    // r = B - alpha X - c H_eff X (FP64-class)
+  // out = B - alpha Y - c H_eff Y (FP64-class); its squared norm to slot
+  auto residual = [&](const cplx* Y, cplx* out, int slot) -> ite_status {
     ctx->lp_level = -1;
-    CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, X, r, csub(C(0), c), X, csub(C(0), alpha)));
-    CK(vec_axpby(r, B, C(1), C(1), n, ctx->stream));
-    CK(vec_norm2(r, n, ctx->dscal + 3, ctx->dscal + 16, nullptr, ctx->stream));
-    if (it == 0) CK(vec_norm2(B, n, ctx->dscal + 4, ctx->dscal + 16, nullptr, ctx->stream));
-    CK(cudaMemcpyAsync(&ctx->hr->d[0], ctx->dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CS(sync(ctx));
-    rho = std::sqrt(ctx->hr->d[0]);
-    if (it == 0) bnorm = std::sqrt(ctx->hr->d[1]);
-    if (!std::isfinite(rho)) return fail(ctx, ITE_ESINGULAR, "non-finite residual in the refinement");
-    if (!(bnorm > 0.0) || rho <= refine_tol * bnorm || it >= refine_max) break;
-    if (it > 0 && rho > 0.5 * rho_prev && level < 2) ++level;
-    rho_prev = rho;
+    CS(heff(ctx, H, i, chl, chl, chr, chr, L, R, Y, out, csub(C(0), c), Y, csub(C(0), alpha)));
+    CK(vec_axpby(out, B, C(1), C(1), n, ctx->stream));
+    CK(vec_norm2(out, n, ctx->dscal + slot, ctx->dscal + 16, nullptr, ctx->stream));
+    return ITE_OK;
+  };
+  CS(residual(X, r, 3));
+  CK(vec_norm2(B, n, ctx->dscal + 4, ctx->dscal + 16, nullptr, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hr->d[0], ctx->dscal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CS(sync(ctx));
+  double rho = std::sqrt(ctx->hr->d[0]);
+  const double bnorm = std::sqrt(ctx->hr->d[1]);
+  if (!std::isfinite(rho) || !std::isfinite(bnorm))
+    return fail(ctx, ITE_ESINGULAR, "non-finite residual in the refinement");
+  // Each correction solves (alpha + c H_eff) D = r with the inner matvecs at
+  // the current level and is kept only if the FP64-class residual of X + D is
+  // smaller than that of X: a correction that went astray (an inner solve whose
+  // low-precision operator is too far from the true one) is dropped, and the
+  // inner matvecs move up one level, as they do when the residual falls by
+  // less than half.  At level 2 the inner and outer operators agree, so GMRES
+  // cannot raise the residual beyond rounding; a rejection there ends the loop.
+  for (int it = 0; it < refine_max && bnorm > 0.0 && rho > refine_tol * bnorm; ++it) {
     if (level < 2 && prepared != level) {
       CS(heff_lp_setup(ctx, H, i, chl, chl, chr, chr, L, R, level));
       prepared = level;
@@ -1007,7 +1019,22 @@ ite_status local_solve_mixed(ite_ctx ctx, ite_mpo H, int i, int chl, int chr, co
     ctx->lp_level = -1;
     total += k;
     ctx->refinements += 1;
-    CK(vec_axpby(X, D, C(1), C(1), n, ctx->stream));
+    CK(vec_copy(Xt, X, n, ctx->stream));
+    CK(vec_axpby(Xt, D, C(1), C(1), n, ctx->stream));
+    CS(residual(Xt, rt, 5));
+    CK(cudaMemcpyAsync(&ctx->hr->d[2], ctx->dscal + 5, sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CS(sync(ctx));
+    const double rho_t = std::sqrt(ctx->hr->d[2]);
+    if (!(rho_t < rho)) {
+      if (level == 2) break;
+      ++level;
+      continue;
+    }
+    if (rho_t > 0.5 * rho && level < 2) ++level;
+    CK(vec_copy(X, Xt, n, ctx->stream));
+    std::swap(r, rt);
+    rho = rho_t;
   }
   if (steps) *steps = total;
   if (res) *res = bnorm > 0.0 ? rho / bnorm : 0.0;
@@ -1284,7 +1311,7 @@ void ite_ctx_destroy(ite_ctx ctx) {
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
                  &ctx->ws_emu, &ctx->ws_ovm, &ctx->ws_lpops, &ctx->ws_lpscr, &ctx->ws_R,
-                 &ctx->ws_D};
+                 &ctx->ws_D, &ctx->ws_R2, &ctx->ws_Xt};
   for (Buf* b : bufs) buf_free(ctx, *b);
   dev_free(ctx, ctx->gm, sizeof(GmresState));
   dev_free(ctx, ctx->dscal, 64 * sizeof(double) + kPartialSlots * sizeof(double));
@@ -2566,7 +2593,7 @@ void internal_release_workspace(ite_ctx ctx) {
   Buf* bufs[] = {&ctx->ws_X, &ctx->ws_B, &ctx->ws_X2, &ctx->ws_V, &ctx->ws_T1, &ctx->ws_T2,
                  &ctx->ws_svdA, &ctx->ws_svdQ, &ctx->ws_left, &ctx->ws_small, &ctx->ws_env,
                  &ctx->ws_emu, &ctx->ws_ovm, &ctx->ws_lpops, &ctx->ws_lpscr, &ctx->ws_R,
-                 &ctx->ws_D};
+                 &ctx->ws_D, &ctx->ws_R2, &ctx->ws_Xt};
   for (Buf* b : bufs) buf_free(ctx, *b);
   ctx->lp_prep = ite_ctx_s::LpPrepared();
 }

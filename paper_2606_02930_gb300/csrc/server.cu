@@ -112,6 +112,10 @@ size_t estimate_bytes(const ite_job* j) {
   elems += q * mps + 2LL * (q + 1) * ovs;
   size_t bytes = (size_t)elems * 16;
   if (j->opts.precision == ITE_FP64_TC) bytes += (size_t)128 * D * nmax;   // slice scratch
+  if (j->opts.precision == ITE_MIXED_BF16 || j->opts.precision == ITE_MIXED_TF32)
+    // slice scratch of the FP64-class residuals, the refinement's four vectors,
+    // and the low-precision operands and intermediates
+    bytes += (size_t)(128 + 16) * D * nmax + (size_t)64 * nmax;
   return bytes + ((size_t)8 << 20);                                         // fixed state
 }
 
@@ -155,9 +159,9 @@ struct ite_server_s {
   std::vector<double> latencies;
   double tau_steps = 0.0;
   ite_status setup_status = ITE_OK;
-  // grouped Jacobi launches across the running jobs (on unless switched off)
+  // grouped Jacobi launches across the running jobs (off unless switched on)
   ite::SplitGroup* group = nullptr;
-  bool grouping = true;
+  bool grouping = false;
 
   void worker_main();
   void run_job(ite_ctx ctx, cudaStream_t st, Job& job);
@@ -442,7 +446,7 @@ void ite_server_destroy(ite_server s) {
 
 ite_status ite_evolve_batch(int device, int n_slots, size_t mem_budget, int n, const ite_job* jobs,
                             ite_job_result* out, ite_server_stats* stats) {
-  return ite_evolve_batch_grouped(device, n_slots, mem_budget, 1, kDefaultGroupWindowMs, n, jobs,
+  return ite_evolve_batch_grouped(device, n_slots, mem_budget, 0, kDefaultGroupWindowMs, n, jobs,
                                   out, stats);
 }
 

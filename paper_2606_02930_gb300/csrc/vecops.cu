@@ -81,13 +81,27 @@ __global__ void k_block_dot(const cplx* V, long long ldv, int nv, const cplx* w,
   }
 }
 
+// out[i] = sum over the nblk partial rows of column i: warp i takes column
+// i, its lanes sum rows lane, lane + 32, ... in order and a fixed shuffle tree
+// adds the lanes, so the order of the sum is fixed and each lane issues its
+// loads together (a single thread summing the rows one by one waited on each
+// L2 load in turn, tens of microseconds per call).
 __global__ void k_reduce_cplx(const cplx* partial, int nblk, int nv, cplx* out, const int* active) {
   if (active && *active == 0) return;
-  const int i = threadIdx.x;
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= nv) return;
-  cplx s = cmake(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(long long)b * nv + i]);
-  out[i] = s;
+  double sr = 0.0, si = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    const cplx v = partial[(long long)b * nv + i];
+    sr += v.x;
+    si += v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) out[i] = cmake(sr, si);
 }
 
 __global__ void k_block_axpy(const cplx* V, long long ldv, int nv, const int* nv_dev,
@@ -118,12 +132,17 @@ __global__ void k_norm2_partial(const cplx* x, long long n, double* partial, con
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// *out = sum of the nblk partials, by one warp in the fixed order of
+// k_reduce_cplx
 __global__ void k_reduce_real(const double* partial, int nblk, double* out, const int* active) {
   if (active && *active == 0) return;
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[b];
-  *out = s;
+  for (int b = lane; b < nblk; b += 32) s += partial[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) *out = s;
 }
 
 __global__ void k_scale_dev(cplx* y, const double* scale, long long n, const int* active) {
@@ -312,7 +331,7 @@ cudaError_t vec_block_dot(const cplx* V, long long ldv, int nv, const cplx* w, l
   count_launches(1);
   k_block_dot<<<g, VT, 0, st>>>(V, ldv, nv, w, n, partial, active);
   count_launches(1);
-  k_reduce_cplx<<<1, 32, 0, st>>>(partial, g, nv, out, active);
+  k_reduce_cplx<<<1, 32 * nv, 0, st>>>(partial, g, nv, out, active);
   return cudaGetLastError();
 }
 cudaError_t vec_block_axpy(const cplx* V, long long ldv, int nv, const int* nv_dev,

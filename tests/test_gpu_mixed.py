@@ -106,6 +106,41 @@ def test_lp_heff_matches_oracle(api, ctx, precision):
         api.k_heff_lp_apply(ctx, H, 4, X, Y)
 
 
+@pytest.mark.parametrize("model,chi", [("heisenberg", 512), ("heisenberg", 1024),
+                                       ("anderson", 512)])
+def test_heff_lp_at_the_quoted_shapes(api, ctx, model, chi):
+    # the bulk shapes whose H_eff rates the benchmark quotes: the low-precision
+    # matvec against the FP64-class matvec (held to the oracle elsewhere) on
+    # the same random environments, within 8u relative
+    import torch
+    from tests.gpu_util import crandn
+    rng = np.random.default_rng(21)
+    if model == "heisenberg":
+        H, d, D = api.mpo_create_heisenberg(ctx, 40), 2, 5
+    else:
+        eps, V = inputs.flat_band_bath(39)
+        H, d, D = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15), 4, 6
+
+    def dev(*shape):
+        return torch.from_numpy(crandn(rng, *shape) / np.sqrt(shape[-1])).to("cuda")
+    L, R, X, Z = dev(D, chi, chi), dev(D, chi, chi), dev(chi, d, d, chi), dev(chi, d, d, chi)
+    alpha, gamma = 0.9 + 0.2j, -0.3
+    Yref = torch.empty_like(X)
+    api.set_kernel_precision(ctx, "fp64_tc")
+    try:
+        api.k_heff(ctx, H, 20, L, R, X, Yref, alpha, Z, gamma)
+    finally:
+        api.set_kernel_precision(ctx, "fp64")
+    ref = Yref - gamma * Z
+    for precision in ("mixed_bf16", "mixed_tf32"):
+        api.k_heff_lp_prepare(ctx, H, 20, L, R, precision)
+        Y = torch.full_like(X, float("nan"))
+        api.k_heff_lp_apply_n(ctx, H, 20, X, Y, alpha, Z, gamma, reps=2)
+        err = (torch.linalg.vector_norm(Y - Yref) / torch.linalg.vector_norm(ref)).item()
+        assert err <= 8 * U[precision], (model, chi, precision, err)
+    del L, R, X, Z, Y, Yref
+
+
 @pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_tf32"])
 def test_refined_local_solve_matches_converged_gmres(api, ctx, precision):
     # a local problem of a saturated chi = 64 MPS: environments of the real
