@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_jacobi_persistent launch on the bulk
 # 512 x 512 split from the ncu capture of this kernel source summarised in
 # profiles/k_jacobi_persistent_split512.md (None once the kernel changes).
-JACOBI_TRAFFIC_BYTES = 4.266752e6 + 1.186048e6
+JACOBI_TRAFFIC_BYTES = 4.268544e6 + 1.094656e6
 JACOBI_TRAFFIC_NOTE = ("dram bytes per launch on the 512 x 512 bulk split (ncu, "
                        "profiles/k_jacobi_persistent_split512.md); the matrix is L2-resident, "
                        "the kernel is FP64-bound")
