@@ -524,9 +524,10 @@ ite_status split(ite_ctx ctx, const cplx* X, int m, int n, int chi_max, double c
   ctx->jacobi_sweeps_total += ctx->hr->pad;
   ctx->jacobi_splits += 1;
   ctx->jacobi_sweeps_max = std::max(ctx->jacobi_sweeps_max, ctx->hr->pad);
-  // algorithmic FP64 flops of the Jacobi: 16 per element and examined pair
-  // (three inner products), 20 per element and rotated pair (the rotation)
-  ctx->jacobi_flops += (16.0 * ctx->hr->pairs[0] + 20.0 * ctx->hr->pairs[1]) * p;
+  // FP64 flops of the Jacobi as the device ran it: 8 per element and examined
+  // pair (one inner product; the row norms are tracked), 20 per element and
+  // rotated pair (the rotation)
+  ctx->jacobi_flops += (8.0 * ctx->hr->pairs[0] + 20.0 * ctx->hr->pairs[1]) * p;
   ctx->svd_alg_flops += kSvdAlgFlopsPerPQK * (double)p * q * k;
   const int r = ctx->hr->rank;
   if (r < 1 || r > k) return fail(ctx, ITE_ESINGULAR, "invalid rank from SVD");

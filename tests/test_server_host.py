@@ -71,3 +71,25 @@ def test_metts_and_panel_job_validation():
     assert pj.device_bytes() > 0 and len(pj.energies) == 15
     pj.c.grid = 5
     assert pj.device_bytes() == 0
+
+
+def test_mixed_modes_estimate_their_refinement_buffers():
+    # the mixed modes hold the FP64-class slice scratch, the refinement's four
+    # vectors and the low-precision operands on top of the FP64 state
+    for prec in ("mixed_bf16", "mixed_tf32"):
+        assert _heis(64, 256, prec).device_bytes() > _heis(64, 256, "fp64_tc").device_bytes()
+
+
+def test_serve_stream_draws():
+    # the served stream's requests: fixed by the seed, parameters in their
+    # ranges, steps from the grid length rule, bath arrays of the drawn size
+    a = inputs.serve_stream(12, baths=(9, 19), chis=(16, 32))
+    b = inputs.serve_stream(12, baths=(9, 19), chis=(16, 32))
+    assert all(np.array_equal(x["site_vecs"], y["site_vecs"]) and x["U"] == y["U"] for x, y in zip(a, b))
+    for r in a:
+        assert 0.05 <= r["U"] <= 0.6 and 0.02 <= r["Gamma"] <= 0.1 and r["eps_d"] == -0.5 * r["U"]
+        assert r["n_bath"] in (9, 19) and r["chi_max"] in (16, 32) and r["gap_s"] >= 0.0
+        assert r["tau_max"] in (1e2, 1e3, 1e4)
+        assert r["n_steps"] == int(np.ceil(10 * np.log10(r["tau_max"] / 1e-2)))
+        assert r["eps"].shape == (r["n_bath"],) and r["V"].shape == (r["n_bath"],)
+        assert r["site_vecs"].shape == (r["n_bath"] + 1, 4)
