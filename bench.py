@@ -870,8 +870,21 @@ def run_anderson(args):
     H = api.mpo_create_anderson(ctx, eps, V, 0.3, -0.15)
     if args.anderson_start == "saturated":
         # the bond dimension the evolution saturates at: random isometries with
-        # slowly decaying bond weights, chi = 512 in the bulk (seed 3000)
-        psi = api.mps_create(ctx, inputs.random_isometric_mps(n_bath + 1, 4, chi, 3000), chi)
+        # slowly decaying bond weights, chi = 512 in the bulk (seed 3000).  The
+        # norm of such a state falls geometrically with N (about 1e-74 at N =
+        # 100 already at chi = 32), and squared norms of its partial
+        # contractions would underflow, so every site is scaled by the same
+        # factor that makes the norm 1 (transfer matrices on the host, each
+        # renormalised by its trace, the logarithms summed).
+        A = inputs.random_isometric_mps(n_bath + 1, 4, chi, 3000)
+        E, log_norm2 = np.ones((1, 1), complex), 0.0
+        for a in A:
+            E = np.tensordot(a.conj(), np.tensordot(E, a, axes=([1], [0])), axes=([0, 1], [0, 1]))
+            t = float(np.trace(E).real)
+            E /= t
+            log_norm2 += np.log(t)
+        f = np.exp(-0.5 * log_norm2 / len(A))
+        psi = api.mps_create(ctx, [a * f for a in A], chi)
     else:
         vecs = inputs.random_product_state(n_bath + 1, 4, 3000)
         psi = api.mps_create_product(ctx, vecs, chi)
